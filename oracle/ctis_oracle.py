@@ -1,0 +1,409 @@
+"""Plain FP64 CPU oracle for shift-invariant CTIS EM reconstruction.
+
+TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module. The GPU product path (the C-ABI library and its Python binding) never
+imports, links or calls it, and shares no code with it.
+
+It follows White, Bell and Haygood, "Accelerating computed tomographic imaging
+spectrometer reconstruction using a parallel algorithm exploiting spatial
+shift-invariance":
+
+* Eq. 1: the imaging model ``g = H f``.
+* Sec. 2: one calibration image per wavelength (point source at field-stop pixel
+  (0,0)) vectorised into a column of H; every other column of that wavelength is
+  the same image shifted by the field-stop offset (shift-invariance).
+* Eq. 2: the EM update ``f <- (f / h) * H^T (g / H f)`` with ``h_j = sum_i H_ij``.
+* Eqs. 3-7: ``H = (H_1 ... H_w)`` and ``H_i = C_i E`` with circulant ``C_i`` and
+  the 0/1 embedding ``E`` built from ``Q = [I_a; 0]`` (used by :func:`dense_H`).
+* Sec. 3 index map ``i = j - s l + (gamma - a) floor((j - s l)/a) + s n``
+  (:func:`index_map`).
+* Eq. 10 (forward) and Eq. 14 (back projection) in their FFT form
+  (:func:`fft_forward`, :func:`fft_adjoint`).
+
+Everything is float64. Inputs given as float32 (datacube, PSF values, counts)
+are promoted exactly. Readings of points the paper leaves open:
+
+* vectorisation: ``i = x + gamma*y`` on the FPA and ``j = s*a*alpha + r*a + p``
+  in the datacube (the index map pairs the fast FPA axis with the fast
+  field-stop axis);
+* boundary: every shifted nonzero must stay on the FPA (checked by
+  :func:`check_bounds`); then the circulant form of Eq. 7 and the 2-D shift agree;
+* ``u_i = 0`` where ``(Hf)_i = 0`` and ``f_j = 0`` where ``h_j = 0`` (Eq. 2 leaves
+  both divisions undefined);
+* duplicate PSF entries at one FPA position add up (H is a sum of responses);
+* ``k`` iterations means ``k`` EM updates from the initial guess.
+
+Pins (tests/test_oracle_*.py): every function here is checked against something
+other than itself - a dense H assembled literally from Eqs. 5-7, the FFT form of
+Eqs. 10/14 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
+for w = 1, brute-force Python loops on tiny inputs, hand-worked values in
+tests/golden/, the EM invariants (nonnegativity, flux, monotone likelihood) and
+finite differences of a dense H.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclasses.dataclass(frozen=True)
+class Geometry:
+    a: int        # field-stop columns (fast axis)
+    alpha: int    # field-stop rows
+    w: int        # wavelengths
+    gamma: int    # FPA columns (fast axis)
+    xi: int       # FPA rows
+
+    @property
+    def ell(self) -> int:
+        return self.a * self.alpha
+
+    @property
+    def m(self) -> int:
+        return self.a * self.alpha * self.w
+
+    @property
+    def n(self) -> int:
+        return self.gamma * self.xi
+
+
+@dataclasses.dataclass
+class Taps:
+    """Merged PSF nonzeros, sorted by (s, y, x); values in float64."""
+
+    s: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    v: np.ndarray
+    ptr: np.ndarray   # [w+1] start of each wavelength's taps
+
+    def of(self, s: int):
+        lo, hi = int(self.ptr[s]), int(self.ptr[s + 1])
+        return self.x[lo:hi], self.y[lo:hi], self.v[lo:hi]
+
+
+class OutOfBounds(ValueError):
+    pass
+
+
+def check_bounds(geom: Geometry, psf) -> None:
+    """Reject a PSF whose shifted copies would leave the FPA.
+
+    Column j = (p, r, s) of H holds the calibration image of wavelength s shifted
+    by (p, r) (Sec. 2). Every shifted nonzero must satisfy ``0 <= x + p < gamma``
+    and ``0 <= y + r < xi`` for all p < a, r < alpha; otherwise the 1-D circulant
+    of Eq. 7 would wrap it into another FPA row while a physical shift would
+    lose it, and the two readings differ.
+    """
+    ptr, x, y, _ = psf
+    if len(ptr) != geom.w + 1:
+        raise ValueError("psf_ptr must have w+1 entries")
+    x = np.asarray(x, dtype=np.int64)
+    y = np.asarray(y, dtype=np.int64)
+    if x.size and (x.min() < 0 or y.min() < 0 or
+                   x.max() + geom.a - 1 >= geom.gamma or
+                   y.max() + geom.alpha - 1 >= geom.xi):
+        raise OutOfBounds("PSF nonzero shifted off the FPA")
+
+
+def merge_psf(geom: Geometry, psf) -> Taps:
+    """Sort each wavelength's nonzeros by (y, x) and add up duplicates (float64)."""
+    check_bounds(geom, psf)
+    ptr, x, y, v = psf
+    ptr = np.asarray(ptr, dtype=np.int64)
+    S, X, Y, V, P = [], [], [], [], [0]
+    for s in range(geom.w):
+        lo, hi = ptr[s], ptr[s + 1]
+        xs = np.asarray(x[lo:hi], dtype=np.int64)
+        ys = np.asarray(y[lo:hi], dtype=np.int64)
+        vs = np.asarray(v[lo:hi], dtype=np.float64)
+        key = ys * geom.gamma + xs
+        uniq, inv = np.unique(key, return_inverse=True)
+        acc = np.zeros(uniq.size)
+        np.add.at(acc, inv, vs)
+        S.append(np.full(uniq.size, s, dtype=np.int64))
+        X.append(uniq % geom.gamma)
+        Y.append(uniq // geom.gamma)
+        V.append(acc)
+        P.append(P[-1] + uniq.size)
+    cat = lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt)
+    return Taps(cat(S, np.int64), cat(X, np.int64), cat(Y, np.int64),
+                cat(V, np.float64), np.asarray(P, dtype=np.int64))
+
+
+def index_map(geom: Geometry) -> np.ndarray:
+    """Zero-based position in ``v = (I_w kron E) f`` of each datacube entry j.
+
+    Sec. 3 (after Eq. 9): ``s = floor(j / l)`` and
+    ``i = j - s l + (gamma - a) floor((j - s l) / a) + s n``.
+    """
+    j = np.arange(geom.m, dtype=np.int64)
+    s = j // geom.ell
+    q = j - s * geom.ell
+    return q + (geom.gamma - geom.a) * (q // geom.a) + s * geom.n
+
+
+class BlockH:
+    """The system matrix kept as its wavelength blocks ``H = (H_1 ... H_w)`` (Eq. 3).
+
+    Each block ``H_s`` (n x l, CSR, float64) is built straight from Sec. 2:
+    column ``r*a + p`` is the calibration image of wavelength s shifted by
+    (p, r), i.e. nonzero ``(x_k, y_k, v_k)`` lands in row
+    ``(x_k + p) + gamma*(y_k + r)``.
+    """
+
+    def __init__(self, geom: Geometry, taps: Taps, wavelengths=None):
+        self.geom = geom
+        self.taps = taps
+        self.wavelengths = list(range(geom.w)) if wavelengths is None else list(wavelengths)
+        a, al, ga = geom.a, geom.alpha, geom.gamma
+        P, R = np.meshgrid(np.arange(a), np.arange(al))     # [alpha][a]
+        col = (R * a + P).ravel()
+        shift = (P + ga * R).ravel()
+        self.blocks = {}
+        for s in self.wavelengths:
+            xs, ys, vs = taps.of(s)
+            base = xs + ga * ys
+            rows = (base[:, None] + shift[None, :]).ravel()
+            cols = np.broadcast_to(col[None, :], (xs.size, col.size)).ravel()
+            vals = np.broadcast_to(vs[:, None], (xs.size, col.size)).ravel()
+            self.blocks[s] = sp.csr_matrix((vals, (rows, cols)), shape=(geom.n, geom.ell))
+
+    def forward(self, f: np.ndarray) -> np.ndarray:
+        """``H f = sum_s H_s f_s`` (Eq. 1 with the partition of Eq. 3)."""
+        f = np.asarray(f, dtype=np.float64).reshape(self.geom.w, -1)
+        out = np.zeros(self.geom.n)
+        for s in self.wavelengths:
+            out += self.blocks[s] @ f[s]
+        return out
+
+    def adjoint(self, r: np.ndarray) -> np.ndarray:
+        """``H^T r`` stacked over the wavelength blocks."""
+        r = np.asarray(r, dtype=np.float64).ravel()
+        out = np.zeros((self.geom.w, self.geom.ell))
+        for s in self.wavelengths:
+            out[s] = self.blocks[s].T @ r
+        return out.ravel()
+
+    def h(self) -> np.ndarray:
+        """``h_j = sum_i H_ij`` (the normaliser of Eq. 2)."""
+        out = np.zeros((self.geom.w, self.geom.ell))
+        for s in self.wavelengths:
+            out[s] = np.asarray(self.blocks[s].sum(axis=0)).ravel()
+        return out.ravel()
+
+    def as_csr(self) -> sp.csr_matrix:
+        return sp.hstack([self.blocks[s] for s in range(self.geom.w)]).tocsr()
+
+
+def build_H(geom: Geometry, psf, wavelengths=None) -> BlockH:
+    return BlockH(geom, merge_psf(geom, psf), wavelengths)
+
+
+def ratio(g: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """``u = g / q`` (Eq. 2), with ``u_i = 0`` where ``q_i = 0``."""
+    g = np.asarray(g, dtype=np.float64).ravel()
+    q = np.asarray(q, dtype=np.float64).ravel()
+    u = np.zeros_like(q)
+    nz = q != 0
+    u[nz] = g[nz] / q[nz]
+    return u
+
+
+def em_update(f: np.ndarray, z: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """``f * z / h`` (Eq. 2), with ``f_j = 0`` where ``h_j = 0``."""
+    f = np.asarray(f, dtype=np.float64).ravel()
+    out = np.zeros_like(f)
+    nz = h != 0
+    out[nz] = f[nz] * z[nz] / h[nz]
+    return out
+
+
+def stats(q: np.ndarray, g: np.ndarray) -> dict:
+    """Global sums of one forward pass, in float64.
+
+    ``loglik`` is the Poisson log-likelihood up to the constant ``-sum log g!``:
+    ``sum_i g_i log q_i - q_i``; a pixel with ``g_i = 0`` adds ``-q_i`` and a
+    pixel with ``g_i > 0 = q_i`` makes it ``-inf``.
+    """
+    q = np.asarray(q, dtype=np.float64).ravel()
+    g = np.asarray(g, dtype=np.float64).ravel()
+    pos = q > 0
+    ll = float(np.sum(g[pos] * np.log(q[pos])) - np.sum(q[pos]))
+    if np.any((g > 0) & ~pos):
+        ll = -np.inf
+    return {
+        "flux_hf": float(q.sum()),
+        "flux_g_covered": float(g[pos].sum()),
+        "loglik": ll,
+        "resid2": float(np.sum((g - q) ** 2)),
+        "sum_g": float(g.sum()),
+    }
+
+
+def mlem(H: BlockH, g: np.ndarray, k: int, f0: np.ndarray | None = None,
+         init: str = "ones"):
+    """k EM updates (Eq. 2), following the loop of Algorithm 1.
+
+    Starts from ``f0`` if given, else all ones (``init='ones'``) or ``H^T g``
+    (``init='htg'``). Returns ``(f, history)`` where ``history[t]`` holds
+    :func:`stats` of ``H f^(t)`` for t = 0..k (the last one for the final f).
+    """
+    g64 = np.asarray(g, dtype=np.float64).ravel()
+    if f0 is not None:
+        f = np.asarray(f0, dtype=np.float64).ravel().copy()
+    elif init == "ones":
+        f = np.ones(H.geom.m)
+    elif init == "htg":
+        f = H.adjoint(g64)
+    else:
+        raise ValueError(init)
+    h = H.h()
+    history = []
+    for _ in range(k):
+        q = H.forward(f)
+        history.append(stats(q, g64))
+        z = H.adjoint(ratio(g64, q))
+        f = em_update(f, z, h)
+    history.append(stats(H.forward(f), g64))
+    return f, history
+
+
+def em_step(H: BlockH, g: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """One EM update of Eq. 2 from the given iterate."""
+    g64 = np.asarray(g, dtype=np.float64).ravel()
+    q = H.forward(f)
+    return em_update(f, H.adjoint(ratio(g64, q)), H.h())
+
+
+# --- pointwise evaluation for full-size parity on sampled outputs -------------
+
+def forward_at(geom: Geometry, taps: Taps, f: np.ndarray, xs, ys) -> np.ndarray:
+    """``(H f)`` at FPA pixels (xs, ys): sum over every tap of every wavelength of
+    the datacube value that lands there (zero where the field-stop index is out
+    of range)."""
+    f = np.asarray(f, dtype=np.float64).reshape(geom.w, geom.alpha, geom.a)
+    xs = np.asarray(xs, dtype=np.int64)
+    ys = np.asarray(ys, dtype=np.int64)
+    out = np.zeros(xs.size)
+    for s in range(geom.w):
+        tx, ty, tv = taps.of(s)
+        p = xs[:, None] - tx[None, :]
+        r = ys[:, None] - ty[None, :]
+        ok = (p >= 0) & (p < geom.a) & (r >= 0) & (r < geom.alpha)
+        vals = np.where(ok, f[s][np.clip(r, 0, geom.alpha - 1), np.clip(p, 0, geom.a - 1)], 0.0)
+        out += vals @ tv
+    return out
+
+
+def adjoint_at(geom: Geometry, taps: Taps, u: np.ndarray, s_idx, ps, rs) -> np.ndarray:
+    """``(H^T u)`` at voxels (p, r, s): the calibration image of wavelength s
+    shifted by (p, r), dotted with u."""
+    u = np.asarray(u, dtype=np.float64).reshape(geom.xi, geom.gamma)
+    out = np.zeros(len(s_idx))
+    for t, (s, p, r) in enumerate(zip(s_idx, ps, rs)):
+        tx, ty, tv = taps.of(int(s))
+        out[t] = np.dot(u[ty + r, tx + p], tv)
+    return out
+
+
+# --- the paper's own formulations, used as independent cross-checks ------------
+
+def dense_H(geom: Geometry, psf) -> np.ndarray:
+    """H assembled literally from Eqs. 5-7: ``H_i = C_i E`` (tiny sizes only).
+
+    ``Q = [I_a; 0]`` (gamma x a), ``E = [I_alpha kron Q; 0]`` (n x a alpha) and
+    ``C_i`` the n x n circulant whose first column is the vectorised calibration
+    image of wavelength i (the response to field-stop pixel (0, 0)).
+    """
+    a, al, ga, n = geom.a, geom.alpha, geom.gamma, geom.n
+    Q = np.vstack([np.eye(a), np.zeros((ga - a, a))])
+    top = np.kron(np.eye(al), Q)
+    E = np.vstack([top, np.zeros((n - top.shape[0], a * al))])
+    ptr, x, y, v = psf
+    blocks = []
+    for s in range(geom.w):
+        c = np.zeros(n)
+        lo, hi = int(ptr[s]), int(ptr[s + 1])
+        for k in range(lo, hi):
+            c[int(x[k]) + ga * int(y[k])] += float(v[k])
+        # circulant: column t is c rolled down by t
+        C = np.empty((n, n))
+        for t in range(n):
+            C[:, t] = np.roll(c, t)
+        blocks.append(C @ E)
+    return np.hstack(blocks)
+
+
+def _calibration_column(geom: Geometry, taps: Taps, s: int) -> np.ndarray:
+    c = np.zeros(geom.n)
+    xs, ys, vs = taps.of(s)
+    np.add.at(c, xs + geom.gamma * ys, vs)
+    return c
+
+
+def fft_forward(geom: Geometry, psf, f: np.ndarray) -> np.ndarray:
+    """Eq. 10: ``g = F^-1 sum_i d_i * (F v_i)`` with ``d_i = F c_i`` and
+    ``v_i = E f_i`` placed by the Sec. 3 index map (real FFT of length n)."""
+    taps = merge_psf(geom, psf)
+    f = np.asarray(f, dtype=np.float64).ravel()
+    imap = index_map(geom)
+    v = np.zeros(geom.n * geom.w)
+    v[imap] = f
+    acc = np.zeros(geom.n // 2 + 1, dtype=np.complex128)
+    for s in range(geom.w):
+        d = np.fft.rfft(_calibration_column(geom, taps, s))
+        acc += d * np.fft.rfft(v[s * geom.n:(s + 1) * geom.n])
+    return np.fft.irfft(acc, n=geom.n)
+
+
+def fft_adjoint(geom: Geometry, psf, u: np.ndarray) -> np.ndarray:
+    """Eq. 14: ``C_i^T u = F^-1(conj(d_i) * F u)``, then the transposed index
+    map ``zeta = (I_w kron E)^T z`` gathers voxel values (Sec. 3)."""
+    taps = merge_psf(geom, psf)
+    U = np.fft.rfft(np.asarray(u, dtype=np.float64).ravel())
+    z = np.zeros(geom.n * geom.w)
+    for s in range(geom.w):
+        d = np.fft.rfft(_calibration_column(geom, taps, s))
+        z[s * geom.n:(s + 1) * geom.n] = np.fft.irfft(np.conj(d) * U, n=geom.n)
+    return z[index_map(geom)]
+
+
+# --- gradients (for the differentiable projector) ------------------------------
+
+def psf_value_grad(geom: Geometry, taps: Taps, f: np.ndarray, gy: np.ndarray) -> np.ndarray:
+    """``d <gy, H f> / d v_{s,k} = sum_{p,r} f_s(p, r) gy(x_k + p, y_k + r)``.
+
+    H is linear in each merged tap value, and tap (s, k) contributes
+    ``v_{s,k} f_s(p, r)`` to pixel ``(x_k + p, y_k + r)``. One value per merged
+    tap, in the order of ``taps``.
+    """
+    f = np.asarray(f, dtype=np.float64).reshape(geom.w, geom.alpha, geom.a)
+    gy = np.asarray(gy, dtype=np.float64).reshape(geom.xi, geom.gamma)
+    out = np.zeros(taps.v.size)
+    for t in range(taps.v.size):
+        s, x, y = int(taps.s[t]), int(taps.x[t]), int(taps.y[t])
+        out[t] = np.sum(f[s] * gy[y:y + geom.alpha, x:x + geom.a])
+    return out
+
+
+def poisson_nll(q: np.ndarray, g: np.ndarray) -> float:
+    """``sum_i q_i - g_i log q_i`` (negative Poisson log-likelihood, no constant)."""
+    return -stats(q, g)["loglik"]
+
+
+def with_values(taps: Taps, v: np.ndarray) -> Taps:
+    return Taps(taps.s, taps.x, taps.y, np.asarray(v, dtype=np.float64), taps.ptr)
+
+
+def unrolled_nll(geom: Geometry, taps: Taps, g: np.ndarray, f0: np.ndarray, k: int) -> float:
+    """Poisson NLL of g under ``H f^(k)`` after k EM updates from ``f0``, with H
+    (and hence h) built from the tap values in ``taps``."""
+    H = BlockH(geom, taps)
+    f = np.asarray(f0, dtype=np.float64).ravel()
+    for _ in range(k):
+        f = em_step(H, g, f)
+    return poisson_nll(H.forward(f), g)

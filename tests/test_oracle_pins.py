@@ -1,0 +1,347 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself (hand-worked values, a dense H assembled from Eqs. 5-7, the FFT form of
+Eqs. 10/14, SciPy's 2-D convolution, brute-force loops, EM invariants)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.signal
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _geom(a, al, w, ga, xi):
+    return O.Geometry(a, al, w, ga, xi)
+
+
+def _tiny_psf(geom, nnz, seed, dup=0):
+    return synth.random_sparse_psf(geom.w, nnz, geom.gamma - geom.a, geom.xi - geom.alpha,
+                                   seed, duplicates=dup)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# --- hand-worked values -------------------------------------------------------
+
+def test_golden_index_map():
+    gold = json.load(open(os.path.join(GOLDEN, "hand_worked_a2_alpha2_gamma4_xi3.json")))
+    g = gold["index_map"]["geometry"]
+    geom = _geom(g["a"], g["alpha"], g["w"], g["gamma"], g["xi"])
+    assert O.index_map(geom).tolist() == gold["index_map"]["i_of_j"]
+
+
+def test_golden_projector_and_em_step():
+    gold = json.load(open(os.path.join(GOLDEN, "hand_worked_a2_alpha2_gamma4_xi3.json")))["projector"]
+    g = gold["geometry"]
+    geom = _geom(g["a"], g["alpha"], g["w"], g["gamma"], g["xi"])
+    p = gold["psf"]
+    psf = (np.array(p["ptr"]), np.array(p["x"]), np.array(p["y"]), np.array(p["val"], np.float32))
+    H = O.build_H(geom, psf)
+    f = np.array(gold["f_r_p"]).ravel()
+    hf = H.forward(f)
+    assert np.array_equal(hf, np.array(gold["hf_y_x"]).ravel())
+    assert np.array_equal(H.adjoint(hf), np.array(gold["adjoint_of_hf_r_p"]).ravel())
+    assert np.all(H.h() == gold["h"])
+    em = gold["em_from_ones"]
+    assert np.array_equal(H.forward(np.ones(geom.m)), np.array(em["hf1_y_x"]).ravel())
+    f2, _ = O.mlem(H, hf, 1)
+    assert np.allclose(f2, np.array(em["f2_r_p"]).ravel(), rtol=0, atol=1e-15)
+
+
+# --- index map and E ------------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4, 3), (3, 2, 3, 5, 4), (4, 3, 2, 7, 6), (1, 1, 1, 1, 1)])
+def test_index_map_is_the_embedding_E(dims):
+    """Sec. 3 map equals the nonzero row of each column of I_w kron E (Eqs. 5-6)."""
+    geom = _geom(*dims)
+    a, al, ga, n = geom.a, geom.alpha, geom.gamma, geom.n
+    Q = np.vstack([np.eye(a), np.zeros((ga - a, a))])
+    top = np.kron(np.eye(al), Q)
+    E = np.vstack([top, np.zeros((n - top.shape[0], a * al))])
+    big = np.kron(np.eye(geom.w), E)
+    rows = np.argmax(big, axis=0)
+    assert np.all(big.sum(axis=0) == 1)
+    assert np.array_equal(rows, O.index_map(geom))
+
+
+# --- dense brute force (Eqs. 5-7) -------------------------------------------------
+
+@pytest.mark.parametrize("dims,nnz,dup,seed", [
+    ((3, 2, 2, 6, 5), 3, 0, 1),
+    ((4, 3, 3, 9, 7), 5, 2, 2),
+    ((2, 4, 2, 5, 9), 4, 1, 3),
+    ((5, 5, 1, 8, 8), 6, 0, 4),
+])
+def test_sparse_H_equals_dense_circulant_form(dims, nnz, dup, seed):
+    geom = _geom(*dims)
+    psf = _tiny_psf(geom, nnz, seed, dup)
+    D = O.dense_H(geom, psf)
+    S = O.build_H(geom, psf).as_csr().toarray()
+    assert D.shape == (geom.n, geom.m)
+    np.testing.assert_allclose(S, D, rtol=1e-15, atol=0)
+    assert np.array_equal(S != 0, D != 0)
+
+
+def test_dense_form_on_synthetic_grating_psf():
+    wl = synth.Workload("t", 4, 3, 3, 22, 20, 3, 6.0, 1.0, 3, 0.7, "mask_spectra", 100.0, 3)
+    psf = synth.make_psf(wl)
+    geom = _geom(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    np.testing.assert_allclose(O.build_H(geom, psf).as_csr().toarray(), O.dense_H(geom, psf),
+                               rtol=1e-15, atol=0)
+
+
+# --- FFT form of the paper (Eqs. 10 and 14) ----------------------------------------
+
+def test_fft_forms_match_sparse_projectors_tiny_workload():
+    wl = synth.TINY
+    geom = _geom(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    psf = synth.make_psf(wl)
+    H = O.build_H(geom, psf)
+    f = synth.make_scene(wl).ravel()
+    u = synth.random_positive(geom.n, seed=7)
+    assert _rel(O.fft_forward(geom, psf, f), H.forward(f)) < 1e-12
+    assert _rel(O.fft_adjoint(geom, psf, u), H.adjoint(u)) < 1e-12
+
+
+# --- adjoint identity --------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_adjoint_identity(seed):
+    geom = _geom(7, 5, 4, 19, 17)
+    psf = _tiny_psf(geom, 9, seed, dup=3)
+    H = O.build_H(geom, psf)
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal(geom.m)
+    r = rng.standard_normal(geom.n)
+    lhs = np.dot(H.forward(f), r)
+    rhs = np.dot(f, H.adjoint(r))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1)
+
+
+# --- special cases ---------------------------------------------------------------
+
+def test_single_wavelength_is_2d_convolution():
+    geom = _geom(6, 5, 1, 16, 14)
+    psf = _tiny_psf(geom, 7, 11)
+    H = O.build_H(geom, psf)
+    taps = O.merge_psf(geom, psf)
+    img = np.zeros((geom.xi, geom.gamma))
+    img[taps.y, taps.x] = taps.v
+    f = synth.random_positive((geom.alpha, geom.a), 3).astype(np.float64)
+    conv = scipy.signal.convolve2d(img, f, mode="full")[:geom.xi, :geom.gamma]
+    np.testing.assert_allclose(H.forward(f.ravel()).reshape(geom.xi, geom.gamma), conv,
+                               rtol=1e-13, atol=1e-13)
+    u = synth.random_positive((geom.xi, geom.gamma), 4).astype(np.float64)
+    # (H^T u)(p, r) = sum_k v_k u(x_k + p, y_k + r): correlate u with the PSF image
+    corr = scipy.signal.correlate2d(u, img, mode="full")
+    # full-mode index of lag (r, p) is (r + xi - 1, p + gamma - 1)
+    ref = corr[geom.xi - 1:geom.xi - 1 + geom.alpha, geom.gamma - 1:geom.gamma - 1 + geom.a]
+    np.testing.assert_allclose(H.adjoint(u.ravel()).reshape(geom.alpha, geom.a), ref,
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_delta_psf_paste_crop_and_exact_em_recovery():
+    geom = _geom(5, 4, 3, 12, 11)
+    x0 = [2, 0, 7]
+    y0 = [1, 6, 3]
+    psf = (np.arange(4, dtype=np.int32), np.array(x0, np.int32), np.array(y0, np.int32),
+           np.ones(3, np.float32))
+    H = O.build_H(geom, psf)
+    f = synth.random_positive(geom.m, 5).astype(np.float64)
+    hf = H.forward(f).reshape(geom.xi, geom.gamma)
+    expect = np.zeros_like(hf)
+    fr = f.reshape(geom.w, geom.alpha, geom.a)
+    for s in range(geom.w):
+        expect[y0[s]:y0[s] + geom.alpha, x0[s]:x0[s] + geom.a] += fr[s]
+    assert np.array_equal(hf, expect)
+    u = synth.random_positive(geom.n, 6).astype(np.float64).reshape(geom.xi, geom.gamma)
+    crop = np.stack([u[y0[s]:y0[s] + geom.alpha, x0[s]:x0[s] + geom.a] for s in range(geom.w)])
+    assert np.array_equal(H.adjoint(u.ravel()), crop.ravel())
+    # disjoint footprints: one EM step from ones on noiseless data gives f exactly
+    geom1 = _geom(5, 4, 1, 12, 11)
+    psf1 = (np.array([0, 1], np.int32), np.array([3], np.int32), np.array([2], np.int32),
+            np.ones(1, np.float32))
+    H1 = O.build_H(geom1, psf1)
+    f1 = synth.random_positive(geom1.m, 8).astype(np.float64)
+    f2, _ = O.mlem(H1, H1.forward(f1), 1)
+    np.testing.assert_allclose(f2, f1, rtol=1e-15, atol=0)
+
+
+# --- merging and bounds ---------------------------------------------------------------
+
+def test_merge_matches_bruteforce_dict():
+    geom = _geom(3, 3, 4, 10, 9)
+    psf = _tiny_psf(geom, 12, 21, dup=6)
+    taps = O.merge_psf(geom, psf)
+    ptr, x, y, v = psf
+    for s in range(geom.w):
+        d = {}
+        for k in range(ptr[s], ptr[s + 1]):
+            key = (int(y[k]), int(x[k]))
+            d[key] = d.get(key, 0.0) + float(v[k])
+        keys = sorted(d)
+        tx, ty, tv = taps.of(s)
+        assert [(int(b), int(a)) for a, b in zip(tx, ty)] == keys
+        np.testing.assert_allclose(tv, [d[k] for k in keys], rtol=1e-15)
+
+
+def test_bounds_rejects_off_fpa():
+    geom = _geom(4, 4, 1, 10, 10)
+    ok = (np.array([0, 1]), np.array([6]), np.array([6]), np.ones(1, np.float32))
+    O.check_bounds(geom, ok)
+    for x, y in [(7, 0), (0, 7), (-1, 0), (0, -1)]:
+        bad = (np.array([0, 1]), np.array([x]), np.array([y]), np.ones(1, np.float32))
+        with pytest.raises(O.OutOfBounds):
+            O.check_bounds(geom, bad)
+
+
+# --- pointwise evaluators ---------------------------------------------------------
+
+def test_pointwise_evaluators_match_full_projectors():
+    wl = synth.TINY
+    geom = _geom(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    psf = synth.make_psf(wl)
+    H = O.build_H(geom, psf)
+    taps = O.merge_psf(geom, psf)
+    f = synth.make_scene(wl).ravel()
+    u = synth.random_positive(geom.n, 9)
+    rng = np.random.default_rng(0)
+    xs = rng.integers(0, geom.gamma, 200)
+    ys = rng.integers(0, geom.xi, 200)
+    full = H.forward(f).reshape(geom.xi, geom.gamma)
+    np.testing.assert_allclose(O.forward_at(geom, taps, f, xs, ys), full[ys, xs], rtol=1e-13, atol=1e-13)
+    ss = rng.integers(0, geom.w, 100)
+    ps = rng.integers(0, geom.a, 100)
+    rs = rng.integers(0, geom.alpha, 100)
+    adj = H.adjoint(u).reshape(geom.w, geom.alpha, geom.a)
+    np.testing.assert_allclose(O.adjoint_at(geom, taps, u, ss, ps, rs), adj[ss, rs, ps], rtol=1e-13)
+
+
+# --- EM invariants ----------------------------------------------------------------
+
+def _tiny_problem(noisy=True):
+    wl = synth.TINY
+    geom = _geom(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    psf = synth.make_psf(wl)
+    H = O.build_H(geom, psf)
+    f_true = synth.make_scene(wl).ravel().astype(np.float64)
+    q = H.forward(f_true)
+    if noisy:
+        g, scale = synth.make_measurement(q, wl.peak, wl.seed)
+    else:
+        g, scale = q * (wl.peak / q.max()), wl.peak / q.max()
+    return geom, H, g.astype(np.float64), f_true * scale
+
+
+@pytest.mark.parametrize("noisy", [False, True])
+def test_em_invariants(noisy):
+    geom, H, g, _ = _tiny_problem(noisy)
+    f, hist = O.mlem(H, g, 20)
+    assert np.all(f >= 0)
+    h = H.h()
+    f_t = np.ones(geom.m)
+    for t in range(20):
+        q = H.forward(f_t)
+        f_t = O.em_update(f_t, H.adjoint(O.ratio(g, q)), h)
+        covered = g[q > 0].sum()
+        # flux: sum_i (H f')_i = sum_j h_j f'_j = <Hf, u> = sum_{q>0} g
+        assert abs(H.forward(f_t).sum() - covered) <= 1e-10 * covered
+    lls = [s["loglik"] for s in hist]
+    assert all(b >= a - 1e-9 * abs(a) for a, b in zip(lls, lls[1:]))
+
+
+def test_noiseless_loglik_rises_toward_its_maximum():
+    geom, H, g, _ = _tiny_problem(noisy=False)
+    _, hist = O.mlem(H, g, 40)
+    pos = g > 0
+    ll_max = float(np.sum(g[pos] * np.log(g[pos])) - g.sum())
+    lls = [s["loglik"] for s in hist]
+    assert lls[-1] <= ll_max + 1e-9 * abs(ll_max)
+    gap0, gap = ll_max - lls[0], ll_max - lls[-1]
+    assert gap < 0.05 * gap0
+
+
+def test_htg_initial_guess_is_adjoint_of_g():
+    geom, H, g, _ = _tiny_problem(noisy=True)
+    f, hist = O.mlem(H, g, 0, init="htg")
+    np.testing.assert_allclose(f, H.adjoint(g), rtol=0, atol=0)
+
+
+# --- gradients ------------------------------------------------------------------------
+
+def test_psf_value_grad_matches_finite_differences_of_dense_H():
+    geom = _geom(4, 3, 2, 9, 8)
+    psf = _tiny_psf(geom, 4, 31)
+    taps = O.merge_psf(geom, psf)
+    rng = np.random.default_rng(1)
+    f = rng.uniform(0.1, 1, geom.m)
+    gy = rng.standard_normal(geom.n)
+    grad = O.psf_value_grad(geom, taps, f, gy)
+    eps = 1e-6
+    for t in range(taps.v.size):
+        def loss(delta):
+            v = taps.v.copy()
+            v[t] += delta
+            p = (taps.ptr, taps.x, taps.y, v)
+            return gy @ (O.dense_H(geom, p) @ f)
+        fd = (loss(eps) - loss(-eps)) / (2 * eps)
+        assert abs(fd - grad[t]) <= 1e-7 * max(1.0, abs(grad[t]))
+
+
+def test_nll_gradient_wrt_f_is_Ht_of_one_minus_ratio():
+    """d/df sum(Hf - g log Hf) = H^T(1 - g/Hf): central differences on dense H."""
+    geom = _geom(3, 3, 2, 8, 7)
+    psf = _tiny_psf(geom, 4, 5)
+    D = O.dense_H(geom, psf)
+    H = O.build_H(geom, psf)
+    rng = np.random.default_rng(2)
+    f = rng.uniform(0.5, 1.5, geom.m)
+    g = rng.poisson(D @ f * 10) / 10.0
+    q = H.forward(f)
+    grad = H.adjoint(1.0 - O.ratio(g, q))
+    eps = 1e-6
+    for j in range(0, geom.m, 3):
+        e = np.zeros(geom.m)
+        e[j] = eps
+        fd = (O.poisson_nll(D @ (f + e), g) - O.poisson_nll(D @ (f - e), g)) / (2 * eps)
+        assert abs(fd - grad[j]) <= 1e-6 * max(1.0, abs(grad[j]))
+
+
+# --- planted mistakes: the pins above must catch plausible oracle bugs -----------
+
+def _mutant_forward(geom, taps, f, kind):
+    fr = f.reshape(geom.w, geom.alpha, geom.a)
+    out = np.zeros((geom.xi, geom.gamma))
+    for s in range(geom.w):
+        xs, ys, vs = taps.of(s)
+        for x, y, v in zip(xs, ys, vs):
+            if kind == "transposed_shift":
+                # wrong: field-stop row shifts the FPA column
+                for r in range(geom.alpha):
+                    for p in range(geom.a):
+                        xx, yy = x + r, y + p
+                        if xx < geom.gamma and yy < geom.xi:
+                            out[yy, xx] += v * fr[s, r, p]
+            elif kind == "flipped_psf":
+                out[y:y + geom.alpha, x:x + geom.a] += v * fr[s, ::-1, ::-1]
+            elif kind == "wrong_wavelength":
+                out[y:y + geom.alpha, x:x + geom.a] += v * fr[(s + 1) % geom.w]
+    return out.ravel()
+
+
+@pytest.mark.parametrize("kind", ["transposed_shift", "flipped_psf", "wrong_wavelength"])
+def test_planted_mistakes_are_caught_by_dense_pin(kind):
+    geom = _geom(4, 3, 2, 10, 9)
+    psf = _tiny_psf(geom, 5, 41)
+    taps = O.merge_psf(geom, psf)
+    f = synth.random_positive(geom.m, 12).astype(np.float64)
+    D = O.dense_H(geom, psf)
+    assert not np.allclose(_mutant_forward(geom, taps, f, kind), D @ f, rtol=1e-6)
