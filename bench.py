@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the CTIS EM reconstruction on GB300.
+
+One step = one full reconstruction of the workload (k EM iterations with the
+per-iteration float64 statistics) from resident device inputs, through the
+library's public API. Default workload: field stop 128x128, 64 wavelengths,
+1024x1024 FPA, 5x5 diffraction orders, 3x3 spots (225 nonzeros per
+calibration image), 100 iterations; synthetic seeded inputs.
+
+Prints one JSON line on rank 0. With --impl reference the FP64 CPU oracle is
+timed instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstruction iterations/s and voxel-updates/s vs plain FP32; % roofline"
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # 80.5 TFLOP/s
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="realistic_128x128x64_fpa1024")
+    ap.add_argument("--k", type=int, default=None, help="EM iterations per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_median": statistics.median(power), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- helpers
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("ctis_gather.cu", "ctis_internal.h"):
+        with open(os.path.join(ROOT, "paper_2006_01573_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, units_scale: float = 1.0):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel sources changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if data.get("source_hash") != kernel_source_hash():
+        return None
+    entry = data.get("kernels", {}).get(kernel)
+    return None if entry is None else entry["dram_bytes_per_launch"] * units_scale
+
+
+def problem(wl, seed):
+    import numpy as np  # noqa: F401
+    import synth
+    return synth.make_psf(wl), synth.make_scene(wl, seed)
+
+
+# --------------------------------------------------------------------------- oracle
+def oracle_sample(wl, g, budget_s: float, n_waves: int = 4):
+    """Time the FP64 oracle's EM iteration on the first `n_waves` wavelength
+    blocks of the workload (Eq. 3 partition) for about `budget_s` seconds.
+    Returns (full-size iterations/s, iterations run, seconds, description)."""
+    import numpy as np
+
+    import oracle as O
+    import synth
+    geom = O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    taps = O.merge_psf(geom, synth.make_psf(wl))
+    waves = list(range(min(n_waves, wl.w)))
+    H = O.BlockH(geom, taps, waves)
+    h = H.h()
+    g64 = np.asarray(g, dtype=np.float64).ravel()
+    f = np.ones(geom.m)
+    t0 = time.perf_counter()
+    iters = 0
+    while True:
+        q = H.forward(f)
+        z = H.adjoint(O.ratio(g64, q))
+        f = O.em_update(f, z, h)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    frac = len(waves) / wl.w
+    desc = (f"{wl.name}: EM iterations on wavelength blocks 0..{len(waves) - 1} of {wl.w} "
+            f"(scipy CSR float64, 1 thread), {iters} iterations in {el:.1f} s, "
+            f"scaled by {len(waves)}/{wl.w} to the full workload")
+    return iters * frac / el, iters, el, desc
+
+
+def run_reference(args, wl, k):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    import synth
+    geom = O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    psf = synth.make_psf(wl)
+    taps = O.merge_psf(geom, psf)
+    f_true = synth.make_scene(wl).ravel()
+    # noiseless image of the first wavelength blocks only: timing input
+    Hs = O.BlockH(geom, taps, range(min(4, wl.w)))
+    g, _ = synth.make_measurement(Hs.forward(f_true), wl.peak, wl.seed)
+    budget = max(2.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, g, budget / 4)
+    vals, secs, descs = [], [], []
+    for _ in range(args.steps):
+        v, iters, el, desc = oracle_sample(wl, g, budget)
+        vals.append(v)
+        secs.append(el)
+        descs.append(desc)
+    value = args.steps / sum(1.0 / v for v in vals)   # iterations-weighted mean rate
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * k / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": wl.name, "k": k, "a": wl.a, "alpha": wl.alpha, "w": wl.w,
+                   "gamma": wl.gamma, "xi": wl.xi, "nnz_per_image": wl.nnz_per_image},
+        "voxel_updates_per_s": value * wl.m,
+        "cpu_baseline": {"value": value, "unit": "it/s", "cores": 1, "kind": "oracle",
+                         "sample": descs[-1], "host_cpus": os.cpu_count()},
+        "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, wl, k):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2006_01573_gb300 import Plan
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    seed = wl.seed + rank
+    psf = synth.make_psf(wl)
+    f_true = synth.make_scene(wl, seed)
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+    info = plan.info()
+    hf = plan.forward(torch.from_numpy(f_true).to(dev))
+    g_host, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, seed)
+    g = torch.from_numpy(g_host).to(dev)
+    f = torch.empty((wl.w, wl.alpha, wl.a), device=dev, dtype=torch.float32)
+    stats = torch.empty((k + 1, 4), device=dev, dtype=torch.float64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    plan.set_profiling(True)
+
+    def step():
+        plan.reconstruct(g, k, f=f, init="ones", stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall0 = time.perf_counter()
+    step_ms, fwd_ms, adj_ms, n_fwd, n_adj = [], 0.0, 0.0, 0, 0
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict L2 between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kt = plan.kernel_times()
+        fwd_ms += kt["forward"][0]
+        n_fwd += kt["forward"][1]
+        adj_ms += kt["adjoint"][0]
+        n_adj += kt["adjoint"][1]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    plan.check()
+
+    # ---- end to end through the public API from pinned host buffers
+    g_pin = torch.from_numpy(g_host).pin_memory()
+    f_pin = torch.empty(f.shape, dtype=f.dtype).pin_memory()
+    st_pin = torch.empty(stats.shape, dtype=stats.dtype).pin_memory()
+    g_dev = torch.empty_like(g)
+    f_dev = torch.empty_like(f)
+
+    def e2e_step():
+        g_dev.copy_(g_pin, non_blocking=True)
+        plan.reconstruct(g_dev, k, f=f_dev, init="ones", stats=stats)
+        f_pin.copy_(f_dev, non_blocking=True)
+        st_pin.copy_(stats, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+
+    total_ms = sum(step_ms)
+    total_e2e = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([total_ms, total_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, total_e2e = float(t[0]), float(t[1])
+    iters = args.steps * k * world
+    value = iters / (total_ms / 1e3)
+    e2e_value = iters / (total_e2e / 1e3)
+
+    # ---- roofline of the dominant kernel (per-launch, from the timed steps)
+    nnz_h = info["nnz"] * wl.a * wl.alpha          # nonzeros of H = FMAs per projection
+    flops = 2.0 * nnz_h
+    kernels = {"forward": (fwd_ms, n_fwd), "adjoint": (adj_ms, n_adj)}
+    dom = max(kernels, key=lambda n: kernels[n][0])
+    avg_ms = kernels[dom][0] / max(1, kernels[dom][1])
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    per_kernel = {n: {"launches": c, "avg_us": 1e3 * t / max(1, c),
+                      "tflops": flops / (t / max(1, c) * 1e-3) / 1e12 if c else None,
+                      "share_of_step": t / total_ms if total_ms else None}
+                  for n, (t, c) in kernels.items()}
+    if world > 1:
+        per_kernel = {n: v for n, v in per_kernel.items()}   # rank 0's view
+
+    if rank != 0:
+        plan.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded PSF, scene, Poisson noise)",
+        "config": {"workload": wl.name, "k": k, "a": wl.a, "alpha": wl.alpha, "w": wl.w,
+                   "gamma": wl.gamma, "xi": wl.xi, "orders": f"{wl.orders}x{wl.orders}",
+                   "spot": f"{wl.spot}x{wl.spot}", "nnz_per_image": wl.nnz_per_image,
+                   "voxels": wl.m, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "stats": "float64 flux/loglik/resid per iteration"},
+        "voxel_updates_per_s": value * wl.m,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": ncu_traffic(dom),
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2070 MHz (max SM clock)",
+                     "algorithmic_flops_per_launch": flops},
+        "kernels": per_kernel,
+        "e2e": {"value": e2e_value, "unit": "it/s",
+                "h2d_bytes_per_step": g_pin.numel() * 4,
+                "d2h_bytes_per_step": f_pin.numel() * 4 + st_pin.numel() * 8},
+        "gpu_launches": args.steps * (2 * k + 2),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    plan.close()
+    if world == 1 and not args.no_cpu_baseline:
+        v, iters_cpu, el, desc = oracle_sample(wl, g_host, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "it/s", "cores": 1, "kind": "oracle",
+                                "sample": desc, "host_cpus": os.cpu_count()}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    import synth
+    wl = synth.WORKLOADS[args.workload]
+    k = args.k if args.k is not None else wl.k
+    if args.impl == "reference":
+        run_reference(args, wl, k)
+    else:
+        run_ours(args, wl, k)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * ctis.h - C ABI of the GB300 CTIS reconstruction library (libctis.so).
+ *
+ * The library implements the data-parallel hot path of shift-invariant CTIS
+ * reconstruction (White, Bell, Haygood): the forward projection H f, the back
+ * projection H^T r and the EM iteration of Eq. 2 built from them, as
+ * hand-written sm_103a CUDA kernels.
+ *
+ * Problem statement (Sec. 2): a field stop of a x alpha pixels is observed at
+ * w wavelengths on a gamma x xi focal-plane array (FPA). One calibration image
+ * per wavelength is the response to a point source at field-stop pixel (0,0);
+ * under shift-invariance, field-stop pixel (p, r) produces the same image
+ * shifted by (p, r). H therefore has n = gamma*xi rows and m = a*alpha*w
+ * columns, and H f = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k) (Eqs. 1, 8-9).
+ *
+ * Layouts (all dense, row-major, no padding in caller buffers):
+ *   datacube f   : f[s][r][p], element j = s*a*alpha + r*a + p (the zero-based
+ *                  j of the Sec. 3 index map), s < w, r < alpha, p < a.
+ *   FPA image g  : g[y][x], element i = x + gamma*y, x < gamma, y < xi.
+ *   PSF          : CSR over wavelengths: psf_ptr[w+1] (psf_ptr[0] = 0), then
+ *                  per nonzero k the FPA coordinates psf_x[k], psf_y[k] of the
+ *                  response to field-stop pixel (0,0) and its value psf_val[k].
+ *
+ * Conventions:
+ *   - Every function returns a ctis_status (0 = success). Errors detected on
+ *     the host return before anything is enqueued. Kernels report device-side
+ *     failures (a bounded wait that gave up) through ctis_plan_check().
+ *   - Device pointers are caller-owned (allocate them with any allocator; the
+ *     library never frees them). Host pointers are read during the call only.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *     asynchronous and stream-ordered unless stated otherwise.
+ *   - A plan owns device workspace, so calls on one plan must not overlap in
+ *     time: issue them on one stream (or synchronise between streams).
+ *   - A plan is bound to the CUDA device that was current at creation; calls
+ *     must be made with that device current.
+ */
+#ifndef CTIS_H
+#define CTIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctis_plan ctis_plan;
+
+typedef enum {
+    CTIS_OK = 0,
+    CTIS_ERR_INVALID_ARG = -1,   /* bad size, pointer, flag or PSF entry        */
+    CTIS_ERR_OUT_OF_BOUNDS = -2, /* a shifted PSF nonzero leaves the FPA         */
+    CTIS_ERR_NOMEM = -3,         /* device or host allocation failed             */
+    CTIS_ERR_CUDA = -4,          /* a CUDA runtime/driver call failed            */
+    CTIS_ERR_TIMEOUT = -5,       /* a kernel's bounded wait gave up              */
+    CTIS_ERR_UNSUPPORTED = -6    /* valid request this build cannot serve        */
+} ctis_status;
+
+/* Storage type of the datacube f and of the PSF values inside a plan. */
+enum { CTIS_F32 = 0, CTIS_BF16 = 1 };
+
+/* ctis_reconstruct flags. Without an INIT flag, f_dev holds the initial guess. */
+enum {
+    CTIS_INIT_ONES = 1,  /* f^(1) = 1 (Algorithm 1)                     */
+    CTIS_INIT_HTG = 2    /* f^(1) = H^T g (Sec. 2, alternative guess)   */
+};
+
+/* Per-forward-pass statistics (float64), CTIS_NSTATS values each, taken over
+ * the pixels where H f > 0 (the support of the model image):
+ *   [0] sum H f                       (model flux)
+ *   [1] sum g                         (measured flux on the support)
+ *   [2] sum g log(H f) - H f          (Poisson log-likelihood, no constant)
+ *   [3] sum (g - H f)^2               (squared residual norm)          */
+enum { CTIS_STAT_FLUX_HF = 0, CTIS_STAT_FLUX_G = 1, CTIS_STAT_LOGLIK = 2,
+       CTIS_STAT_RESID2 = 3, CTIS_NSTATS = 4 };
+
+/* Create a plan: validate and merge the calibration PSFs, check that every
+ * shifted nonzero stays on the FPA (0 <= x_k, x_k + a - 1 < gamma, same for y
+ * with alpha and xi; otherwise CTIS_ERR_OUT_OF_BOUNDS), group nonzeros into
+ * spot clusters, build the per-tile work lists of both projectors, compute
+ * h = H^T 1 (Eq. 2; per wavelength the sum of its PSF values) in float64 and
+ * upload everything. All PSF arrays are host memory, copied. Values must be
+ * finite and >= 0. Duplicate (x, y) entries of one wavelength add up.
+ * dtype is CTIS_F32 or CTIS_BF16 (BF16: f and PSF values are stored in
+ * bfloat16, arithmetic accumulates in float32). Blocks until the plan's device
+ * data is uploaded. On failure *out is set to NULL. */
+int ctis_plan_create(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
+                     const int32_t* psf_ptr, const int32_t* psf_x,
+                     const int32_t* psf_y, const float* psf_val, int dtype);
+
+/* Optional plan settings (zero-initialise, set struct_size). */
+typedef struct {
+    int struct_size;       /* sizeof(ctis_plan_options)                         */
+    int tasks_per_item;    /* cluster tasks per work item; 0 = chosen by the plan
+                              (the chunk size whose simulated longest-first
+                              schedule over the GPU's warps finishes first)     */
+    int reserved[6];       /* must be 0                                          */
+} ctis_plan_options;
+
+/* ctis_plan_create with options; opt may be NULL (all defaults). */
+int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
+                        const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
+                        const float* psf_val, int dtype, const ctis_plan_options* opt);
+
+/* Release the plan and its device memory (synchronises the device first).
+ * NULL is accepted. */
+int ctis_plan_destroy(ctis_plan* plan);
+
+/* Sizes and derived quantities of a plan (host call, no device work). */
+typedef struct {
+    int64_t a, alpha, w, gamma, xi, m, n;
+    int64_t nnz;                 /* merged PSF nonzeros, all wavelengths       */
+    int64_t clusters;            /* spot clusters after grouping               */
+    int64_t cluster_k;           /* cluster box side K (K x K taps)            */
+    int64_t fwd_tiles, fwd_tasks, fwd_items;
+    int64_t adj_tiles, adj_tasks, adj_items;
+    int64_t scratch_bytes;       /* device workspace owned by the plan         */
+    int64_t dtype;
+    int64_t fwd_warps, adj_warps;          /* persistent warps per launch        */
+    int64_t fwd_chunk, adj_chunk;          /* tasks per work item                */
+    int64_t fwd_load_milli, adj_load_milli;/* busiest warp's scheduled tasks x1000 */
+} ctis_plan_info;
+
+int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
+
+/* Copy the merged PSF table to host arrays: for each merged nonzero, sorted by
+ * (s, y, x), its wavelength, FPA coordinates and value (as stored: float32, or
+ * bfloat16 widened to float32), plus h[w] (float32 as used by the update).
+ * Arrays must hold info.nnz entries (h: w entries). Any pointer may be NULL. */
+int ctis_plan_export_taps(const ctis_plan* plan, int32_t* s, int32_t* x, int32_t* y,
+                          float* val, float* h);
+
+/* Device index map of the Sec. 3 embedding (I_w kron E): out_dev[j] = position
+ * in the stacked FPA vectors v = (v_1 .. v_w) of datacube element j,
+ * i = x + gamma*y + s*n for j = (p, r, s) with x = p, y = r. int64, m entries. */
+int ctis_index_map(const ctis_plan* plan, int64_t* out_dev, void* stream);
+
+/* hf_dev = H f_dev (Eqs. 1, 8). f_dev: m elements of the plan's dtype;
+ * hf_dev: n float32. */
+int ctis_forward(const ctis_plan* plan, const void* f_dev, float* hf_dev, void* stream);
+
+/* out_dev = H^T r_dev (Eq. 11). r_dev: n float32; out_dev: m float32. */
+int ctis_adjoint(const ctis_plan* plan, const float* r_dev, float* out_dev, void* stream);
+
+/* k EM updates (Eq. 2, Algorithm 1): per iteration u = g / (H f) (0 where
+ * H f = 0), then f <- f * (H^T u) / h (0 where h = 0).
+ * g_dev: n float32 counts. f_dev: m elements of the plan's dtype; read as the
+ * initial guess unless an INIT flag is given, overwritten with f^(k+1).
+ * stats_dev: NULL, or device float64[(k+1)*CTIS_NSTATS]: row t holds the
+ * statistics of H f^(t+1) for t < k (computed by the iteration's forward
+ * pass) and row k those of the returned f (one extra forward pass).
+ * The k iterations are replayed from a CUDA graph cached in the plan
+ * (re-captured when pointers, k, flags or the stream's capture state change). */
+int ctis_reconstruct(const ctis_plan* plan, const float* g_dev, void* f_dev, int k,
+                     int flags, double* stats_dev, void* stream);
+
+/* Kernel timing. When enabled, ctis_reconstruct records a CUDA event pair
+ * (as event-record nodes of its cached graph) around every projector launch.
+ * ctis_plan_kernel_times waits for those events and reports, for the most
+ * recent ctis_reconstruct, the summed device time in milliseconds and the
+ * number of forward and adjoint launches. Any output pointer may be NULL. */
+int ctis_plan_set_profiling(ctis_plan* plan, int enable);
+int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,
+                           int* n_adj);
+
+/* Wait for the plan's work on `stream`, then report (and clear) any device-side
+ * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
+int ctis_plan_check(const ctis_plan* plan, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* ctis_status_string(int status);
+
+/* Details of the last error on the calling thread (static thread-local string). */
+const char* ctis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTIS_H */

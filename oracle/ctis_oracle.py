@@ -223,24 +223,22 @@ def em_update(f: np.ndarray, z: np.ndarray, h: np.ndarray) -> np.ndarray:
 
 
 def stats(q: np.ndarray, g: np.ndarray) -> dict:
-    """Global sums of one forward pass, in float64.
+    """Global sums of one forward pass, in float64, over the support of H f.
 
-    ``loglik`` is the Poisson log-likelihood up to the constant ``-sum log g!``:
-    ``sum_i g_i log q_i - q_i``; a pixel with ``g_i = 0`` adds ``-q_i`` and a
-    pixel with ``g_i > 0 = q_i`` makes it ``-inf``.
+    Reading of Eq. 2's likelihood (Shepp-Vardi EM): the Poisson log-likelihood
+    up to the constant ``-sum log g!`` is ``sum_i g_i log q_i - q_i``. Pixels with
+    ``q_i = 0`` are left out of every sum here (they add ``-q_i = 0`` when
+    ``g_i = 0``; a pixel with ``g_i > 0 = q_i`` would make the full likelihood
+    ``-inf``, which no measurement generated by H can produce).
     """
     q = np.asarray(q, dtype=np.float64).ravel()
     g = np.asarray(g, dtype=np.float64).ravel()
     pos = q > 0
-    ll = float(np.sum(g[pos] * np.log(q[pos])) - np.sum(q[pos]))
-    if np.any((g > 0) & ~pos):
-        ll = -np.inf
     return {
-        "flux_hf": float(q.sum()),
+        "flux_hf": float(q[pos].sum()),
         "flux_g_covered": float(g[pos].sum()),
-        "loglik": ll,
-        "resid2": float(np.sum((g - q) ** 2)),
-        "sum_g": float(g.sum()),
+        "loglik": float(np.sum(g[pos] * np.log(q[pos])) - np.sum(q[pos])),
+        "resid2": float(np.sum((g[pos] - q[pos]) ** 2)),
     }
 
 

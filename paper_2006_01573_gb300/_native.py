@@ -1,0 +1,269 @@
+"""ctypes binding of libctis.so (argument marshalling only).
+
+Every computation happens in the library's CUDA kernels; this module checks
+tensor shapes, dtypes and devices, passes raw pointers and the current CUDA
+stream, and turns status codes into exceptions. There is no CPU fallback: if
+the library is missing, importing a Plan fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctis.so")
+
+CTIS_F32, CTIS_BF16 = 0, 1
+CTIS_INIT_ONES, CTIS_INIT_HTG = 1, 2
+NSTATS = 4
+STAT_NAMES = ("flux_hf", "flux_g", "loglik", "resid2")
+
+_lib = None
+
+# Every symbol include/ctis.h declares, for the ABI export test.
+EXPORTED = (
+    "ctis_plan_create", "ctis_plan_create_ex", "ctis_plan_destroy", "ctis_plan_get_info", "ctis_plan_export_taps",
+    "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
+    "ctis_plan_set_profiling", "ctis_plan_kernel_times",
+    "ctis_status_string", "ctis_last_error",
+)
+
+
+class CtisError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{message} [{code}]")
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "a", "alpha", "w", "gamma", "xi", "m", "n", "nnz", "clusters", "cluster_k",
+        "fwd_tiles", "fwd_tasks", "fwd_items", "adj_tiles", "adj_tasks", "adj_items",
+        "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
+        "fwd_load_milli", "adj_load_milli")]
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int), ("tasks_per_item", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libctis.so and declare its C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "or python -m paper_2006_01573_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    f32p = ctypes.POINTER(ctypes.c_float)
+    sig = {
+        "ctis_plan_create": (I, [ctypes.POINTER(P), I, I, I, I, I, i32p, i32p, i32p, f32p, I]),
+        "ctis_plan_create_ex": (I, [ctypes.POINTER(P), I, I, I, I, I, i32p, i32p, i32p, f32p, I,
+                                    ctypes.POINTER(PlanOptions)]),
+        "ctis_plan_destroy": (I, [P]),
+        "ctis_plan_get_info": (I, [P, ctypes.POINTER(PlanInfo)]),
+        "ctis_plan_export_taps": (I, [P, i32p, i32p, i32p, f32p, f32p]),
+        "ctis_index_map": (I, [P, VP, VP]),
+        "ctis_forward": (I, [P, VP, VP, VP]),
+        "ctis_adjoint": (I, [P, VP, VP, VP]),
+        "ctis_reconstruct": (I, [P, VP, VP, I, I, VP, VP]),
+        "ctis_plan_check": (I, [P, VP]),
+        "ctis_plan_set_profiling": (I, [P, I]),
+        "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
+        "ctis_status_string": (ctypes.c_char_p, [I]),
+        "ctis_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = load()
+        raise CtisError(rc, f"{lib.ctis_status_string(rc).decode()}: "
+                            f"{lib.ctis_last_error().decode()}")
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Plan:
+    """A CTIS reconstruction plan on the current CUDA device.
+
+    ``psf`` is ``(psf_ptr[w+1], psf_x, psf_y, psf_val)`` in host memory; see
+    include/ctis.h for layouts. Datacubes are torch tensors shaped
+    ``(w, alpha, a)`` (float32, or bfloat16 for ``dtype='bf16'``), FPA images
+    ``(xi, gamma)`` float32, all on the plan's device.
+    """
+
+    def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0):
+        lib = load()
+        ptr, _ = _arr(psf[0], np.int32)
+        x, _ = _arr(psf[1], np.int32)
+        y, _ = _arr(psf[2], np.int32)
+        v, _ = _arr(psf[3], np.float32)
+        if ptr.size != w + 1:
+            raise ValueError("psf_ptr must have w+1 entries")
+        self.dtype = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
+        handle = ctypes.c_void_p()
+        i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item))
+        _check(lib.ctis_plan_create_ex(ctypes.byref(handle), a, alpha, w, gamma, xi, i32(ptr),
+                                       i32(x), i32(y),
+                                       v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       self.dtype, ctypes.byref(opt)))
+        self._h = handle
+        self.a, self.alpha, self.w, self.gamma, self.xi = a, alpha, w, gamma, xi
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ctis_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- metadata ---------------------------------------------------------------
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().ctis_plan_get_info(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in PlanInfo._fields_}
+
+    def export_taps(self):
+        """Merged PSF table ``(s, x, y, val)`` sorted by (s, y, x), and ``h[w]``."""
+        nnz = self.info()["nnz"]
+        s = np.zeros(nnz, np.int32)
+        x = np.zeros(nnz, np.int32)
+        y = np.zeros(nnz, np.int32)
+        v = np.zeros(nnz, np.float32)
+        h = np.zeros(self.w, np.float32)
+        i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        f32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(load().ctis_plan_export_taps(self._h, i32(s), i32(x), i32(y), f32(v), f32(h)))
+        return s, x, y, v, h
+
+    # -- helpers ------------------------------------------------------------------
+    def _f_dtype(self):
+        import torch
+        return torch.bfloat16 if self.dtype == CTIS_BF16 else torch.float32
+
+    def _check_cube(self, f, dtype=None):
+        import torch
+        dtype = dtype or self._f_dtype()
+        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == dtype and
+                f.is_contiguous() and f.numel() == self.w * self.alpha * self.a):
+            raise ValueError(f"datacube must be a contiguous CUDA {dtype} tensor of "
+                             f"{self.w}x{self.alpha}x{self.a} elements")
+
+    def _check_fpa(self, g):
+        import torch
+        if not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.float32 and
+                g.is_contiguous() and g.numel() == self.xi * self.gamma):
+            raise ValueError(f"FPA image must be a contiguous CUDA float32 tensor of "
+                             f"{self.xi}x{self.gamma} elements")
+
+    # -- operations -----------------------------------------------------------------
+    def forward(self, f, out=None, stream=None):
+        """``H f`` as an ``(xi, gamma)`` float32 tensor."""
+        import torch
+        self._check_cube(f)
+        if out is None:
+            out = torch.empty((self.xi, self.gamma), device=f.device, dtype=torch.float32)
+        self._check_fpa(out)
+        _check(load().ctis_forward(self._h, ctypes.c_void_p(f.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def adjoint(self, r, out=None, stream=None):
+        """``H^T r`` as a ``(w, alpha, a)`` float32 tensor."""
+        import torch
+        self._check_fpa(r)
+        if out is None:
+            out = torch.empty((self.w, self.alpha, self.a), device=r.device, dtype=torch.float32)
+        self._check_cube(out, torch.float32)
+        _check(load().ctis_adjoint(self._h, ctypes.c_void_p(r.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def reconstruct(self, g, k: int, f=None, init: str | None = "ones", stats=False,
+                    stream=None):
+        """k EM updates (Eq. 2). Returns ``(f, stats)``. ``stats`` may be False,
+        True (allocate) or a float64 CUDA tensor of ``(k+1, 4)`` to fill: rows
+        0..k-1 describe ``H f^(t+1)`` of each iteration, row k the returned f.
+        Reusing the same f, g and stats tensors replays the plan's cached graph."""
+        import torch
+        self._check_fpa(g)
+        if f is None:
+            if init is None:
+                raise ValueError("init=None needs an initial f")
+            f = torch.empty((self.w, self.alpha, self.a), device=g.device, dtype=self._f_dtype())
+        self._check_cube(f)
+        flags = {"ones": CTIS_INIT_ONES, "htg": CTIS_INIT_HTG, None: 0}[init]
+        st = None
+        if isinstance(stats, torch.Tensor):
+            st = stats
+            if not (st.is_cuda and st.dtype == torch.float64 and st.is_contiguous() and
+                    st.numel() >= (k + 1) * NSTATS):
+                raise ValueError("stats must be a contiguous CUDA float64 tensor of (k+1)*4")
+        elif stats:
+            st = torch.empty((k + 1, NSTATS), device=g.device, dtype=torch.float64)
+        _check(load().ctis_reconstruct(self._h, ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(f.data_ptr()), k, flags,
+                                       ctypes.c_void_p(st.data_ptr() if st is not None else 0),
+                                       _stream(stream)))
+        return f, st
+
+    def index_map(self, stream=None):
+        import torch
+        out = torch.empty(self.w * self.alpha * self.a, device="cuda", dtype=torch.int64)
+        _check(load().ctis_index_map(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def set_profiling(self, enable: bool):
+        _check(load().ctis_plan_set_profiling(self._h, int(bool(enable))))
+
+    def kernel_times(self):
+        """``{'forward': (ms_total, launches), 'adjoint': (ms_total, launches)}`` of
+        the last reconstruct call made with profiling enabled (waits for it)."""
+        fm, am = ctypes.c_double(), ctypes.c_double()
+        fn, an = ctypes.c_int(), ctypes.c_int()
+        _check(load().ctis_plan_kernel_times(self._h, ctypes.byref(fm), ctypes.byref(fn),
+                                             ctypes.byref(am), ctypes.byref(an)))
+        return {"forward": (fm.value, fn.value), "adjoint": (am.value, an.value)}
+
+    def check(self, stream=None):
+        """Synchronise the stream and raise if a kernel reported a device-side failure."""
+        _check(load().ctis_plan_check(self._h, _stream(stream)))

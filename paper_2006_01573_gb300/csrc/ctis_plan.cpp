@@ -1,0 +1,1106 @@
+// Plan construction and the C-ABI entry points of libctis.
+//
+// A plan turns the calibration PSFs (Sec. 2: one image per wavelength, the
+// response to field-stop pixel (0,0)) into everything the gather kernels need:
+//   * merged nonzeros (duplicates added in float64, rounded once to the
+//     storage type) and h = H^T 1 (Eq. 2), which under the on-FPA bounds rule
+//     is, for every voxel of wavelength s, the sum of that wavelength's values;
+//   * spot clusters: 8-connected groups of nonzeros, each covered by K x K
+//     boxes (K the smallest supported side that fits the largest group);
+//   * work lists: for the forward projector every FPA tile lists the clusters
+//     whose footprint (a + K - 1) x (alpha + K - 1) meets it; for the adjoint
+//     every voxel tile of wavelength s lists the clusters of s. Long lists are
+//     split into chunks; items are ordered longest first.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ctis.h"
+#include "ctis_internal.h"
+#include "ctis_kernels.h"
+
+using namespace ctis;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CTIS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CTIS_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+// Round a float to bfloat16, round to nearest even (finite, nonnegative input).
+uint16_t to_bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return static_cast<uint16_t>(u >> 16);
+}
+
+float bf16_bits_to_float(uint16_t b) {
+    const uint32_t u = static_cast<uint32_t>(b) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+struct Cluster {
+    int s, X, Y;
+};
+
+struct ProjTables {
+    std::vector<TileDesc> tiles;
+    std::vector<ItemDesc> items;
+    std::vector<TaskDesc> tasks;
+    std::vector<int> warp_begin;   // [n_warps + 1]
+    std::vector<int> warp_items;   // item indices, grouped by warp
+    int64_t scratch_slots = 0;
+    int per_item = 0;              // chunk size chosen for this table
+    int n_warps = 0;
+    double max_warp_load = 0.0;    // LPT estimate of the busiest warp, task units
+    TileDesc* d_tiles = nullptr;
+    ItemDesc* d_items = nullptr;
+    TaskDesc* d_tasks = nullptr;
+    int* d_warp_begin = nullptr;
+    int* d_warp_items = nullptr;
+    void* d_weights = nullptr;
+    int blocks_per_sm = 0;
+};
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+struct GraphKey {
+    const void* g = nullptr;
+    const void* f = nullptr;
+    const void* stats = nullptr;
+    int k = -1, flags = 0;
+    bool profiling = false;
+    bool operator==(const GraphKey& o) const {
+        return g == o.g && f == o.f && stats == o.stats && k == o.k && flags == o.flags &&
+               profiling == o.profiling;
+    }
+};
+
+}  // namespace
+
+struct ctis_plan {
+    int a = 0, alpha = 0, w = 0, gamma = 0, xi = 0, dtype = 0;
+    int64_t m = 0, n = 0;
+    int device = 0, num_sms = 0, K = 1;
+    int f_epc = 4;        // datacube elements per 16 bytes
+    int a_pitch = 0;      // pitch of the internal datacube copy (elements)
+    int g_pitch = 0;      // pitch of the internal FPA buffer (elements)
+    std::vector<int32_t> tap_s, tap_x, tap_y;
+    std::vector<float> tap_v;   // stored values widened to float32
+    std::vector<float> h;       // [w]
+    std::vector<Cluster> clusters;
+    ProjTables fwd, adj;
+    float* d_h = nullptr;
+    float* d_u = nullptr;
+    void* d_fwork = nullptr;
+    float* d_scratch = nullptr;
+    int* d_tickets = nullptr;
+    int* d_counters = nullptr;
+    double* d_tile_stats = nullptr;
+    int64_t device_bytes = 0;
+    cudaStream_t cap_stream = nullptr;
+    GraphKey gkey;
+    cudaGraphExec_t gexec = nullptr;
+    bool profiling = false;
+    int forced_per_item = 0;          // 0: chosen by schedule()
+    std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
+    std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
+};
+
+namespace {
+
+int dmalloc(ctis_plan* P, void** ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CTIS_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    P->device_bytes += static_cast<int64_t>(bytes);
+    return CTIS_OK;
+}
+
+template <typename T>
+int upload(ctis_plan* P, T** dst, const std::vector<T>& src) {
+    int rc = dmalloc(P, reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+    if (rc) return rc;
+    if (!src.empty())
+        CTIS_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return CTIS_OK;
+}
+
+void free_tables(ProjTables& t) {
+    cudaFree(t.d_tiles);
+    cudaFree(t.d_items);
+    cudaFree(t.d_tasks);
+    cudaFree(t.d_weights);
+    cudaFree(t.d_warp_begin);
+    cudaFree(t.d_warp_items);
+    t.d_tiles = nullptr;
+    t.d_items = nullptr;
+    t.d_tasks = nullptr;
+    t.d_weights = nullptr;
+    t.d_warp_begin = nullptr;
+    t.d_warp_items = nullptr;
+}
+
+void destroy(ctis_plan* P) {
+    if (!P) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->device);
+    cudaDeviceSynchronize();
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    for (cudaEvent_t e : P->events) cudaEventDestroy(e);
+    free_tables(P->fwd);
+    free_tables(P->adj);
+    cudaFree(P->d_h);
+    cudaFree(P->d_u);
+    cudaFree(P->d_fwork);
+    cudaFree(P->d_scratch);
+    cudaFree(P->d_tickets);
+    cudaFree(P->d_counters);
+    cudaFree(P->d_tile_stats);
+    cudaSetDevice(cur);
+    delete P;
+}
+
+// Cost of an item in task units: its tasks, plus the partial-sum round trip
+// and ticket of a chunked tile, plus the epilogue.
+double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 1.0 : 0.0) + 0.25; }
+
+// Splits every tile's task range into chunks of at most `per_item` tasks and
+// fills the item list and the scratch slot bases.
+void make_items(ProjTables& T, const std::vector<int>& tile_task_begin, int per_item) {
+    T.items.clear();
+    T.scratch_slots = 0;
+    for (size_t t = 0; t < T.tiles.size(); ++t) {
+        const int b = tile_task_begin[t], e = tile_task_begin[t + 1];
+        const int cnt = e - b;
+        const int nch = std::max(1, (cnt + per_item - 1) / per_item);
+        T.tiles[t].nchunks = nch;
+        T.tiles[t].scratch_base = 0;
+        if (nch > 1) {
+            T.tiles[t].scratch_base = static_cast<int>(T.scratch_slots);
+            T.scratch_slots += nch;
+        }
+        for (int c = 0; c < nch; ++c) {
+            ItemDesc it;
+            it.tile = static_cast<int>(t);
+            it.chunk = c;
+            it.task_begin = b + static_cast<int>(static_cast<int64_t>(cnt) * c / nch);
+            it.task_end = b + static_cast<int>(static_cast<int64_t>(cnt) * (c + 1) / nch);
+            T.items.push_back(it);
+        }
+    }
+}
+
+// Longest-processing-time-first assignment of the items to n_warps warps.
+// Returns the load of the busiest warp; fills warp_begin / warp_items.
+double assign_warps(ProjTables& T, int n_warps) {
+    std::vector<int> order(T.items.size());
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int i) {
+        const ItemDesc& it = T.items[i];
+        return item_cost(it.task_end - it.task_begin, T.tiles[it.tile].nchunks > 1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    using Slot = std::pair<double, int>;   // (load, warp)
+    std::vector<Slot> heap;
+    heap.reserve(n_warps);
+    for (int w = 0; w < n_warps; ++w) heap.emplace_back(0.0, w);
+    auto cmp = [](const Slot& x, const Slot& y) {
+        return x.first != y.first ? x.first > y.first : x.second > y.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    std::vector<std::vector<int>> per_warp(n_warps);
+    double max_load = 0.0;
+    for (int i : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        Slot& sl = heap.back();
+        per_warp[sl.second].push_back(i);
+        sl.first += cost(i);
+        max_load = std::max(max_load, sl.first);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    T.warp_begin.assign(1, 0);
+    T.warp_items.clear();
+    for (int w = 0; w < n_warps; ++w) {
+        T.warp_items.insert(T.warp_items.end(), per_warp[w].begin(), per_warp[w].end());
+        T.warp_begin.push_back(static_cast<int>(T.warp_items.size()));
+    }
+    return max_load;
+}
+
+// Picks the chunk size that minimises the LPT estimate of the busiest warp
+// (ties: the larger chunk, i.e. fewer partial sums), or uses `forced` > 0.
+void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int forced) {
+    T.n_warps = n_warps;
+    std::vector<int> cands;
+    if (forced > 0) {
+        cands.push_back(forced);
+    } else {
+        for (int c : {64, 48, 32, 24, 16, 13, 12, 10, 9, 8, 7, 6, 5, 4}) cands.push_back(c);
+    }
+    int best = cands[0];
+    double best_load = -1.0;
+    for (int c : cands) {
+        make_items(T, begin, c);
+        const double load = assign_warps(T, n_warps);
+        if (best_load < 0 || load < best_load - 1e-9) {
+            best_load = load;
+            best = c;
+        }
+    }
+    make_items(T, begin, best);
+    T.max_warp_load = assign_warps(T, n_warps);
+    T.per_item = best;
+}
+
+// Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
+// every shifted copy of every nonzero must stay on the FPA).
+int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
+                 const int32_t* psf_x, const int32_t* psf_y, const float* psf_val) {
+    const int64_t nnz_in = psf_ptr[w];
+    for (int64_t k = 0; k < nnz_in; ++k) {
+        const float v = psf_val[k];
+        if (!std::isfinite(v) || v < 0.f)
+            return fail(CTIS_ERR_INVALID_ARG, "psf_val[%lld] = %g is not finite and >= 0",
+                        (long long)k, (double)v);
+        const int64_t x = psf_x[k], y = psf_y[k];
+        if (x < 0 || y < 0 || x + a - 1 >= ga || y + al - 1 >= xi)
+            return fail(CTIS_ERR_OUT_OF_BOUNDS,
+                        "PSF nonzero %lld at (%lld, %lld) leaves the %dx%d FPA when shifted "
+                        "across the %dx%d field stop",
+                        (long long)k, (long long)x, (long long)y, ga, xi, a, al);
+    }
+    return CTIS_OK;
+}
+
+int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
+          const float* psf_val) {
+    const int a = P->a, al = P->alpha, w = P->w, ga = P->gamma, xi = P->xi;
+
+    // ---- merge duplicates, sort by (s, y, x)
+    std::vector<double> merged_v;
+    std::vector<int64_t> order;
+    for (int s = 0; s < w; ++s) {
+        const int64_t b = psf_ptr[s], e = psf_ptr[s + 1];
+        order.resize(e - b);
+        std::iota(order.begin(), order.end(), b);
+        std::sort(order.begin(), order.end(), [&](int64_t i, int64_t j) {
+            return psf_y[i] != psf_y[j] ? psf_y[i] < psf_y[j] : psf_x[i] < psf_x[j];
+        });
+        for (size_t q = 0; q < order.size(); ++q) {
+            const int64_t k = order[q];
+            if (!P->tap_s.empty() && P->tap_s.back() == s && P->tap_x.back() == psf_x[k] &&
+                P->tap_y.back() == psf_y[k]) {
+                merged_v.back() += static_cast<double>(psf_val[k]);
+            } else {
+                P->tap_s.push_back(s);
+                P->tap_x.push_back(psf_x[k]);
+                P->tap_y.push_back(psf_y[k]);
+                merged_v.push_back(static_cast<double>(psf_val[k]));
+            }
+        }
+    }
+    const int64_t nnz = static_cast<int64_t>(merged_v.size());
+    std::vector<uint16_t> tap_bf16;
+    P->tap_v.resize(nnz);
+    for (int64_t k = 0; k < nnz; ++k) {
+        const float f = static_cast<float>(merged_v[k]);
+        if (P->dtype == kDtypeBF16) {
+            tap_bf16.push_back(to_bf16_bits(f));
+            P->tap_v[k] = bf16_bits_to_float(tap_bf16.back());
+        } else {
+            P->tap_v[k] = f;
+        }
+    }
+
+    // ---- h = H^T 1 per wavelength, float64 sum of the stored values
+    P->h.assign(w, 0.f);
+    {
+        std::vector<double> hs(w, 0.0);
+        for (int64_t k = 0; k < nnz; ++k) hs[P->tap_s[k]] += static_cast<double>(P->tap_v[k]);
+        for (int s = 0; s < w; ++s) P->h[s] = static_cast<float>(hs[s]);
+    }
+
+    // ---- clusters: 8-connected components, covered by K x K boxes
+    std::vector<int64_t> s_begin(w + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) s_begin[P->tap_s[k] + 1]++;
+    for (int s = 0; s < w; ++s) s_begin[s + 1] += s_begin[s];
+    std::vector<int64_t> parent(nnz);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int64_t i) {
+        while (parent[i] != i) i = parent[i] = parent[parent[i]];
+        return i;
+    };
+    for (int s = 0; s < w; ++s) {
+        std::unordered_map<int64_t, int64_t> at;
+        for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k)
+            at[static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
+        for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k) {
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int64_t x = P->tap_x[k] + dx, y = P->tap_y[k] + dy;
+                    if (x < 0 || y < 0 || x >= ga || y >= xi) continue;
+                    auto it = at.find(y * ga + x);
+                    if (it != at.end()) {
+                        const int64_t r1 = find(k), r2 = find(it->second);
+                        if (r1 != r2) parent[std::max(r1, r2)] = std::min(r1, r2);
+                    }
+                }
+        }
+    }
+    struct Box { int s, x0, y0, x1, y1; };
+    std::unordered_map<int64_t, Box> comp;
+    int max_side = 1;
+    for (int64_t k = 0; k < nnz; ++k) {
+        const int64_t r = find(k);
+        auto it = comp.find(r);
+        if (it == comp.end()) {
+            comp[r] = Box{P->tap_s[k], P->tap_x[k], P->tap_y[k], P->tap_x[k], P->tap_y[k]};
+        } else {
+            Box& b = it->second;
+            b.x0 = std::min(b.x0, P->tap_x[k]);
+            b.x1 = std::max(b.x1, P->tap_x[k]);
+            b.y0 = std::min(b.y0, P->tap_y[k]);
+            b.y1 = std::max(b.y1, P->tap_y[k]);
+        }
+    }
+    for (auto& kv : comp)
+        max_side = std::max(max_side, std::max(kv.second.x1 - kv.second.x0 + 1,
+                                               kv.second.y1 - kv.second.y0 + 1));
+    const int K = max_side <= 1 ? 1 : (max_side <= 3 ? 3 : 5);
+    P->K = K;
+    std::vector<Box> boxes;
+    for (auto& kv : comp) boxes.push_back(kv.second);
+    std::sort(boxes.begin(), boxes.end(), [](const Box& x, const Box& y) {
+        if (x.s != y.s) return x.s < y.s;
+        if (x.y0 != y.y0) return x.y0 < y.y0;
+        return x.x0 < y.x0;
+    });
+    // Cover every component with K x K boxes and fill their weights.
+    std::vector<float> wts;          // adjoint orientation, [cluster][dy][dx], float32 values
+    for (int s = 0; s < w; ++s) {
+        std::unordered_map<int64_t, int64_t> at;
+        for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k)
+            at[static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
+        for (const Box& b : boxes) {
+            if (b.s != s) continue;
+            for (int by = b.y0; by <= b.y1; by += K)
+                for (int bx = b.x0; bx <= b.x1; bx += K) {
+                    std::vector<float> wk(static_cast<size_t>(K) * K, 0.f);
+                    bool any = false;
+                    for (int dy = 0; dy < K; ++dy)
+                        for (int dx = 0; dx < K; ++dx) {
+                            const int64_t x = bx + dx, y = by + dy;
+                            if (x > b.x1 || y > b.y1) continue;
+                            auto it = at.find(y * ga + x);
+                            if (it == at.end()) continue;
+                            wk[dy * K + dx] = P->tap_v[it->second];
+                            any = true;
+                        }
+                    if (!any) continue;
+                    P->clusters.push_back(Cluster{s, bx, by});
+                    wts.insert(wts.end(), wk.begin(), wk.end());
+                }
+        }
+    }
+    // A box is filled from every tap of its wavelength inside it, so two boxes
+    // of one wavelength must never overlap: remove taps already claimed.
+    {
+        std::vector<char> claimed(nnz, 0);
+        std::vector<std::unordered_map<int64_t, int64_t>> at(w);
+        for (int64_t k = 0; k < nnz; ++k)
+            at[P->tap_s[k]][static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
+        for (size_t c = 0; c < P->clusters.size(); ++c) {
+            const Cluster& cl = P->clusters[c];
+            for (int dy = 0; dy < K; ++dy)
+                for (int dx = 0; dx < K; ++dx) {
+                    float& wv = wts[c * K * K + dy * K + dx];
+                    if (wv == 0.f) continue;
+                    auto it = at[cl.s].find(static_cast<int64_t>(cl.Y + dy) * ga + cl.X + dx);
+                    if (claimed[it->second]) wv = 0.f;   // owned by an earlier box
+                    claimed[it->second] = 1;
+                }
+        }
+        for (int64_t k = 0; k < nnz; ++k)
+            if (!claimed[k] && P->tap_v[k] != 0.f)
+                return fail(CTIS_ERR_INVALID_ARG, "internal: tap %lld not covered by a cluster",
+                            (long long)k);
+    }
+    const int64_t ncl = static_cast<int64_t>(P->clusters.size());
+
+    // weights in the plan's storage type, both orientations
+    std::vector<float> wf(wts.size());
+    for (int64_t c = 0; c < ncl; ++c)
+        for (int e = 0; e < K * K; ++e) wf[c * K * K + e] = wts[c * K * K + (K * K - 1 - e)];
+    auto store_weights = [&](ProjTables& T, const std::vector<float>& src) -> int {
+        if (P->dtype == kDtypeBF16) {
+            std::vector<uint16_t> b(src.size());
+            for (size_t i = 0; i < src.size(); ++i) b[i] = to_bf16_bits(src[i]);
+            uint16_t* d = nullptr;
+            int rc = upload(P, &d, b);
+            T.d_weights = d;
+            return rc;
+        }
+        float* d = nullptr;
+        int rc = upload(P, &d, src);
+        T.d_weights = d;
+        return rc;
+    };
+
+    const int TX = gather_tile_w(), TY = gather_tile_h();
+    CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
+    CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
+    const int warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta();
+    const int warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta();
+
+    // ---- forward work lists: FPA tiles x clusters whose footprint meets them
+    {
+        ProjTables& T = P->fwd;
+        const int ntx = (ga + TX - 1) / TX, nty = (xi + TY - 1) / TY;
+        const int fw = a + K - 1, fh = al + K - 1;   // footprint of one cluster
+        std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
+        for (int64_t c = 0; c < ncl; ++c) {
+            const Cluster& cl = P->clusters[c];
+            const int tx0 = cl.X / TX, tx1 = std::min(ntx - 1, (cl.X + fw - 1) / TX);
+            const int ty0 = cl.Y / TY, ty1 = std::min(nty - 1, (cl.Y + fh - 1) / TY);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx)
+                    per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));
+        }
+        std::vector<int> begin{0};
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                TileDesc td{};
+                td.x0 = tx * TX;
+                td.y0 = ty * TY;
+                td.plane = 0;
+                T.tiles.push_back(td);
+                std::vector<TaskDesc> tl;
+                for (int c : per_tile[static_cast<size_t>(ty) * ntx + tx]) {
+                    const Cluster& cl = P->clusters[c];
+                    const int64_t px = static_cast<int64_t>(td.x0) - cl.X - (K - 1);
+                    const int64_t py = static_cast<int64_t>(td.y0) - cl.Y - (K - 1);
+                    const int64_t wx = floor_div(px, P->f_epc) * P->f_epc;
+                    TaskDesc t;
+                    t.wx = static_cast<int>(wx);
+                    t.wy = static_cast<int>(py);
+                    t.plane = cl.s;
+                    t.wsel = (c << 3) | static_cast<int>(px - wx);
+                    tl.push_back(t);
+                }
+                std::stable_sort(tl.begin(), tl.end(), [](const TaskDesc& x, const TaskDesc& y) {
+                    return (x.wsel & 7) < (y.wsel & 7);
+                });
+                T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
+                begin.push_back(static_cast<int>(T.tasks.size()));
+            }
+        schedule(T, begin, warps_fwd, P->forced_per_item);
+        int rc = store_weights(T, wf);
+        if (rc) return rc;
+    }
+
+    // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
+    {
+        ProjTables& T = P->adj;
+        std::vector<int64_t> c_begin(w + 1, 0);
+        for (int64_t c = 0; c < ncl; ++c) c_begin[P->clusters[c].s + 1]++;
+        for (int s = 0; s < w; ++s) c_begin[s + 1] += c_begin[s];
+        std::vector<int> begin{0};
+        const int ntx = (a + TX - 1) / TX, nty = (al + TY - 1) / TY;
+        for (int s = 0; s < w; ++s)
+            for (int ty = 0; ty < nty; ++ty)
+                for (int tx = 0; tx < ntx; ++tx) {
+                    TileDesc td{};
+                    td.x0 = tx * TX;
+                    td.y0 = ty * TY;
+                    td.plane = s;
+                    T.tiles.push_back(td);
+                    std::vector<TaskDesc> tl;
+                    for (int64_t c = c_begin[s]; c < c_begin[s + 1]; ++c) {
+                        const Cluster& cl = P->clusters[c];
+                        const int64_t px = static_cast<int64_t>(cl.X) + td.x0;
+                        const int64_t py = static_cast<int64_t>(cl.Y) + td.y0;
+                        const int64_t wx = floor_div(px, 4) * 4;
+                        TaskDesc t;
+                        t.wx = static_cast<int>(wx);
+                        t.wy = static_cast<int>(py);
+                        t.plane = 0;
+                        t.wsel = static_cast<int>(c << 3) | static_cast<int>(px - wx);
+                        tl.push_back(t);
+                    }
+                    std::stable_sort(tl.begin(), tl.end(), [](const TaskDesc& x, const TaskDesc& y) {
+                        return (x.wsel & 7) < (y.wsel & 7);
+                    });
+                    T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
+                    begin.push_back(static_cast<int>(T.tasks.size()));
+                }
+        schedule(T, begin, warps_adj, P->forced_per_item);
+        int rc = store_weights(T, wts);
+        if (rc) return rc;
+    }
+
+    // ---- device buffers
+    for (ProjTables* T : {&P->fwd, &P->adj}) {
+        int rc = upload(P, &T->d_tiles, T->tiles);
+        if (!rc) rc = upload(P, &T->d_items, T->items);
+        if (!rc) rc = upload(P, &T->d_tasks, T->tasks);
+        if (!rc) rc = upload(P, &T->d_warp_begin, T->warp_begin);
+        if (!rc) rc = upload(P, &T->d_warp_items, T->warp_items);
+        if (rc) return rc;
+    }
+    int rc = upload(P, &P->d_h, P->h);
+    if (rc) return rc;
+    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+    rc = dmalloc(P, reinterpret_cast<void**>(&P->d_u), sizeof(float) * P->g_pitch * (size_t)xi);
+    if (!rc) rc = dmalloc(P, &P->d_fwork, es * P->a_pitch * (size_t)al * w);
+    const int64_t slots = std::max(P->fwd.scratch_slots, P->adj.scratch_slots);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch),
+                          sizeof(float) * static_cast<size_t>(slots) * TX * TY);
+    const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 8);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
+                          sizeof(double) * kNumStats * P->fwd.tiles.size());
+    if (rc) return rc;
+    CTIS_CUDA(cudaMemset(P->d_tickets, 0, sizeof(int) * ntiles));
+    CTIS_CUDA(cudaMemset(P->d_counters, 0, sizeof(int) * 8));
+    CTIS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+    CTIS_CUDA(cudaDeviceSynchronize());
+    return CTIS_OK;
+}
+
+int check_plan(const ctis_plan* P) {
+    if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
+    int cur = -1;
+    CTIS_CUDA(cudaGetDevice(&cur));
+    if (cur != P->device)
+        return fail(CTIS_ERR_INVALID_ARG, "plan belongs to device %d, current device is %d",
+                    P->device, cur);
+    return CTIS_OK;
+}
+
+int make_map(CUtensorMap* map, const void* base, int dtype, int width, int height, int depth,
+             int64_t pitch, int64_t plane, int box_w, int box_h) {
+    EncodeFn fn = encode_fn();
+    if (!fn) return fail(CTIS_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int64_t es = dtype == kDtypeBF16 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)depth};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(plane * es)};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map,
+                          dtype == kDtypeBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(CTIS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for %dx%dx%d box %dx%d",
+                    (int)r, width, height, depth, box_w, box_h);
+    return CTIS_OK;
+}
+
+GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
+    GatherParams p{};
+    p.items = T.d_items;
+    p.tiles = T.d_tiles;
+    p.tasks = T.d_tasks;
+    p.weights = T.d_weights;
+    p.warp_begin = T.d_warp_begin;
+    p.warp_items = T.d_warp_items;
+    p.n_warps = T.n_warps;
+    p.n_tiles = static_cast<int>(T.tiles.size());
+    p.scratch = P->d_scratch;
+    p.tickets = P->d_tickets;
+    p.counters = P->d_counters;
+    p.tile_stats = P->d_tile_stats;
+    p.h = P->d_h;
+    return p;
+}
+
+// Forward pass from a datacube laid out with row pitch `f_pitch` (elements).
+int enqueue_forward(const ctis_plan* P, const void* f, int f_pitch, GatherParams p,
+                    cudaStream_t st) {
+    CUtensorMap slab, halo;
+    const int bw = gather_box_w(P->K, P->dtype);
+    const int64_t plane = static_cast<int64_t>(f_pitch) * P->alpha;
+    int rc = make_map(&slab, f, P->dtype, P->a, P->alpha, P->w, f_pitch, plane, bw,
+                      gather_tile_h() / (32 / kShapeMain.LX));
+    if (rc) return rc;
+    halo = slab;
+    if (P->K > 1) {
+        rc = make_map(&halo, f, P->dtype, P->a, P->alpha, P->w, f_pitch, plane, bw, P->K - 1);
+        if (rc) return rc;
+    }
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, slab, halo, p, st));
+    return CTIS_OK;
+}
+
+// Adjoint pass from an FPA vector laid out with row pitch `r_pitch` (elements).
+int enqueue_adjoint(const ctis_plan* P, const float* r, int r_pitch, GatherParams p,
+                    cudaStream_t st) {
+    CUtensorMap slab, halo;
+    const int bw = gather_box_w_input_f32(P->K);
+    const int64_t plane = static_cast<int64_t>(r_pitch) * P->xi;
+    int rc = make_map(&slab, r, kDtypeF32, P->gamma, P->xi, 1, r_pitch, plane, bw,
+                      gather_tile_h() / (32 / kShapeMain.LX));
+    if (rc) return rc;
+    halo = slab;
+    if (P->K > 1) {
+        rc = make_map(&halo, r, kDtypeF32, P->gamma, P->xi, 1, r_pitch, plane, bw, P->K - 1);
+        if (rc) return rc;
+    }
+    CTIS_CUDA(gather_launch(false, P->K, P->dtype, slab, halo, p, st));
+    return CTIS_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Datacube usable by TMA in place: 16-byte aligned base and row pitch.
+bool f_in_place(const ctis_plan* P, const void* f) {
+    return aligned16(f) && (P->a % P->f_epc) == 0;
+}
+
+bool r_in_place(const ctis_plan* P, const void* r) {
+    return aligned16(r) && (P->gamma % 4) == 0;
+}
+
+// Records event `idx` of the plan's pool on `st` (an event-record node when
+// the stream is being captured).
+int record(ctis_plan* P, int idx, cudaStream_t st) {
+    CTIS_CUDA(cudaEventRecordWithFlags(P->events[idx], st, cudaEventRecordExternal));
+    return CTIS_OK;
+}
+
+// Enqueues the whole reconstruction on `st`.
+int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
+                        double* stats, cudaStream_t st) {
+    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+    const bool inplace = f_in_place(P, f);
+    void* fw = inplace ? f : P->d_fwork;
+    const int fp = inplace ? P->a : P->a_pitch;
+    const int64_t fplane = static_cast<int64_t>(fp) * P->alpha;
+    int rc;
+    if (flags & CTIS_INIT_ONES) {
+        CTIS_CUDA(launch_fill(P->dtype, fw, P->a, P->alpha * P->w, fp, 1.0f, st));
+    } else if (flags & CTIS_INIT_HTG) {
+        CTIS_CUDA(cudaMemcpy2DAsync(P->d_u, sizeof(float) * P->g_pitch, g,
+                                    sizeof(float) * P->gamma, sizeof(float) * P->gamma, P->xi,
+                                    cudaMemcpyDeviceToDevice, st));
+        GatherParams p = base_params(P, P->adj);
+        p.mode = kEpiSet;
+        p.out_w = P->a;
+        p.out_h = P->alpha;
+        p.f_out = fw;
+        p.f_pitch = fp;
+        p.f_plane_stride = fplane;
+        rc = enqueue_adjoint(P, P->d_u, P->g_pitch, p, st);
+        if (rc) return rc;
+    } else if (!inplace) {
+        CTIS_CUDA(cudaMemcpy2DAsync(fw, es * P->a_pitch, f, es * P->a, es * P->a,
+                                    static_cast<size_t>(P->alpha) * P->w,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    GatherParams pf = base_params(P, P->fwd);
+    pf.mode = kEpiRatio;
+    pf.out_w = P->gamma;
+    pf.out_h = P->xi;
+    pf.out_f32 = P->d_u;
+    pf.out_pitch = P->g_pitch;
+    pf.g = g;
+    pf.g_pitch = P->gamma;
+    GatherParams pa = base_params(P, P->adj);
+    pa.mode = kEpiUpdate;
+    pa.out_w = P->a;
+    pa.out_h = P->alpha;
+    pa.f_in = fw;
+    pa.f_out = fw;
+    pa.f_pitch = fp;
+    pa.f_plane_stride = fplane;
+    P->prof_fwd.clear();
+    P->prof_adj.clear();
+    int ev = 0;
+    if (P->profiling) {
+        const size_t need = 4 * static_cast<size_t>(k + 1);
+        while (P->events.size() < need) {
+            cudaEvent_t e;
+            CTIS_CUDA(cudaEventCreate(&e));
+            P->events.push_back(e);
+        }
+    }
+    auto timed = [&](std::vector<std::pair<int, int>>& log, auto&& body) -> int {
+        if (!P->profiling) return body();
+        int r = record(P, ev, st);
+        if (!r) r = body();
+        if (!r) r = record(P, ev + 1, st);
+        if (!r) log.emplace_back(ev, ev + 1);
+        ev += 2;
+        return r;
+    };
+    for (int it = 0; it <= k; ++it) {
+        if (it == k && !stats) break;
+        pf.with_stats = stats != nullptr;
+        pf.stats_out = stats ? stats + static_cast<int64_t>(it) * kNumStats : nullptr;
+        rc = timed(P->prof_fwd, [&] { return enqueue_forward(P, fw, fp, pf, st); });
+        if (rc) return rc;
+        if (it == k) break;
+        rc = timed(P->prof_adj, [&] { return enqueue_adjoint(P, P->d_u, P->g_pitch, pa, st); });
+        if (rc) return rc;
+    }
+    if (!inplace)
+        CTIS_CUDA(cudaMemcpy2DAsync(f, es * P->a, fw, es * P->a_pitch, es * P->a,
+                                    static_cast<size_t>(P->alpha) * P->w,
+                                    cudaMemcpyDeviceToDevice, st));
+    return CTIS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* ctis_status_string(int status) {
+    switch (status) {
+        case CTIS_OK: return "CTIS_OK";
+        case CTIS_ERR_INVALID_ARG: return "CTIS_ERR_INVALID_ARG";
+        case CTIS_ERR_OUT_OF_BOUNDS: return "CTIS_ERR_OUT_OF_BOUNDS";
+        case CTIS_ERR_NOMEM: return "CTIS_ERR_NOMEM";
+        case CTIS_ERR_CUDA: return "CTIS_ERR_CUDA";
+        case CTIS_ERR_TIMEOUT: return "CTIS_ERR_TIMEOUT";
+        case CTIS_ERR_UNSUPPORTED: return "CTIS_ERR_UNSUPPORTED";
+        default: return "CTIS_ERR_UNKNOWN";
+    }
+}
+
+const char* ctis_last_error(void) { return g_last_error.c_str(); }
+
+int ctis_plan_create(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
+                     const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
+                     const float* psf_val, int dtype) {
+    return ctis_plan_create_ex(out, a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val,
+                               dtype, nullptr);
+}
+
+int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
+                        const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
+                        const float* psf_val, int dtype, const ctis_plan_options* opt) {
+    if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
+    int forced_per_item = 0;
+    if (opt) {
+        if (opt->struct_size != static_cast<int>(sizeof(ctis_plan_options)))
+            return fail(CTIS_ERR_INVALID_ARG, "ctis_plan_options.struct_size mismatch");
+        for (int r : opt->reserved)
+            if (r != 0) return fail(CTIS_ERR_INVALID_ARG, "reserved option fields must be 0");
+        if (opt->tasks_per_item < 0 || opt->tasks_per_item > 1 << 20)
+            return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item out of range");
+        forced_per_item = opt->tasks_per_item;
+    }
+    *out = nullptr;
+    if (a < 1 || alpha < 1 || w < 1 || gamma < 1 || xi < 1)
+        return fail(CTIS_ERR_INVALID_ARG, "sizes must be >= 1 (a=%d alpha=%d w=%d gamma=%d xi=%d)",
+                    a, alpha, w, gamma, xi);
+    if (a > gamma || alpha > xi)
+        return fail(CTIS_ERR_OUT_OF_BOUNDS, "field stop %dx%d larger than FPA %dx%d", a, alpha,
+                    gamma, xi);
+    if ((int64_t)gamma * xi > (int64_t)1 << 31 || (int64_t)a * alpha * w > (int64_t)1 << 31)
+        return fail(CTIS_ERR_UNSUPPORTED, "problem larger than 2^31 elements");
+    if (dtype != CTIS_F32 && dtype != CTIS_BF16)
+        return fail(CTIS_ERR_INVALID_ARG, "dtype must be CTIS_F32 or CTIS_BF16");
+    if (!psf_ptr) return fail(CTIS_ERR_INVALID_ARG, "psf_ptr is NULL");
+    if (psf_ptr[0] != 0) return fail(CTIS_ERR_INVALID_ARG, "psf_ptr[0] must be 0");
+    for (int s = 0; s < w; ++s)
+        if (psf_ptr[s + 1] < psf_ptr[s])
+            return fail(CTIS_ERR_INVALID_ARG, "psf_ptr must be non-decreasing (at %d)", s);
+    if (psf_ptr[w] > 0 && (!psf_x || !psf_y || !psf_val))
+        return fail(CTIS_ERR_INVALID_ARG, "PSF arrays are NULL");
+    if ((int64_t)psf_ptr[w] * 8 > (int64_t)1 << 31)
+        return fail(CTIS_ERR_UNSUPPORTED, "too many PSF nonzeros");
+    {
+        const int rc = validate_psf(a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val);
+        if (rc) return rc;
+    }
+
+    ctis_plan* P = new (std::nothrow) ctis_plan();
+    if (!P) return fail(CTIS_ERR_NOMEM, "host allocation failed");
+    P->a = a;
+    P->alpha = alpha;
+    P->w = w;
+    P->gamma = gamma;
+    P->xi = xi;
+    P->dtype = dtype;
+    P->m = (int64_t)a * alpha * w;
+    P->n = (int64_t)gamma * xi;
+    P->f_epc = dtype == CTIS_BF16 ? 8 : 4;
+    P->forced_per_item = forced_per_item;
+    P->a_pitch = static_cast<int>(round_up(a, P->f_epc));
+    P->g_pitch = static_cast<int>(round_up(gamma, 4));
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "no usable CUDA device");
+    }
+    int rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
+    if (rc) {
+        destroy(P);
+        return rc;
+    }
+    *out = P;
+    return CTIS_OK;
+}
+
+int ctis_plan_destroy(ctis_plan* plan) {
+    destroy(plan);
+    return CTIS_OK;
+}
+
+int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
+    if (!P || !info) return fail(CTIS_ERR_INVALID_ARG, "NULL argument");
+    info->a = P->a;
+    info->alpha = P->alpha;
+    info->w = P->w;
+    info->gamma = P->gamma;
+    info->xi = P->xi;
+    info->m = P->m;
+    info->n = P->n;
+    info->nnz = static_cast<int64_t>(P->tap_v.size());
+    info->clusters = static_cast<int64_t>(P->clusters.size());
+    info->cluster_k = P->K;
+    info->fwd_tiles = static_cast<int64_t>(P->fwd.tiles.size());
+    info->fwd_tasks = static_cast<int64_t>(P->fwd.tasks.size());
+    info->fwd_items = static_cast<int64_t>(P->fwd.items.size());
+    info->adj_tiles = static_cast<int64_t>(P->adj.tiles.size());
+    info->adj_tasks = static_cast<int64_t>(P->adj.tasks.size());
+    info->adj_items = static_cast<int64_t>(P->adj.items.size());
+    info->scratch_bytes = P->device_bytes;
+    info->dtype = P->dtype;
+    info->fwd_warps = P->fwd.n_warps;
+    info->adj_warps = P->adj.n_warps;
+    info->fwd_chunk = P->fwd.per_item;
+    info->adj_chunk = P->adj.per_item;
+    info->fwd_load_milli = static_cast<int64_t>(P->fwd.max_warp_load * 1000.0);
+    info->adj_load_milli = static_cast<int64_t>(P->adj.max_warp_load * 1000.0);
+    return CTIS_OK;
+}
+
+int ctis_plan_export_taps(const ctis_plan* P, int32_t* s, int32_t* x, int32_t* y, float* val,
+                          float* h) {
+    if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
+    const size_t n = P->tap_v.size();
+    if (s) std::memcpy(s, P->tap_s.data(), n * sizeof(int32_t));
+    if (x) std::memcpy(x, P->tap_x.data(), n * sizeof(int32_t));
+    if (y) std::memcpy(y, P->tap_y.data(), n * sizeof(int32_t));
+    if (val) std::memcpy(val, P->tap_v.data(), n * sizeof(float));
+    if (h) std::memcpy(h, P->h.data(), P->h.size() * sizeof(float));
+    return CTIS_OK;
+}
+
+int ctis_index_map(const ctis_plan* P, int64_t* out_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!out_dev) return fail(CTIS_ERR_INVALID_ARG, "out_dev is NULL");
+    CTIS_CUDA(launch_index_map(reinterpret_cast<long long*>(out_dev), P->a, P->alpha, P->w,
+                               P->gamma, P->n, static_cast<cudaStream_t>(stream)));
+    return CTIS_OK;
+}
+
+int ctis_forward(const ctis_plan* P, const void* f_dev, float* hf_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!f_dev || !hf_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const void* f = f_dev;
+    int fp = P->a;
+    if (!f_in_place(P, f_dev)) {
+        const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+        CTIS_CUDA(cudaMemcpy2DAsync(P->d_fwork, es * P->a_pitch, f_dev, es * P->a, es * P->a,
+                                    static_cast<size_t>(P->alpha) * P->w,
+                                    cudaMemcpyDeviceToDevice, st));
+        f = P->d_fwork;
+        fp = P->a_pitch;
+    }
+    GatherParams p = base_params(P, P->fwd);
+    p.mode = kEpiRaw;
+    p.out_w = P->gamma;
+    p.out_h = P->xi;
+    p.out_f32 = hf_dev;
+    p.out_pitch = P->gamma;
+    p.out_plane_stride = 0;
+    return enqueue_forward(P, f, fp, p, st);
+}
+
+int ctis_adjoint(const ctis_plan* P, const float* r_dev, float* out_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!r_dev || !out_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float* r = r_dev;
+    int rp = P->gamma;
+    if (!r_in_place(P, r_dev)) {
+        CTIS_CUDA(cudaMemcpy2DAsync(P->d_u, sizeof(float) * P->g_pitch, r_dev,
+                                    sizeof(float) * P->gamma, sizeof(float) * P->gamma, P->xi,
+                                    cudaMemcpyDeviceToDevice, st));
+        r = P->d_u;
+        rp = P->g_pitch;
+    }
+    GatherParams p = base_params(P, P->adj);
+    p.mode = kEpiRaw;
+    p.out_w = P->a;
+    p.out_h = P->alpha;
+    p.out_f32 = out_dev;
+    p.out_pitch = P->a;
+    p.out_plane_stride = static_cast<long long>(P->a) * P->alpha;
+    return enqueue_adjoint(P, r, rp, p, st);
+}
+
+int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k, int flags,
+                     double* stats_dev, void* stream) {
+    int rc = check_plan(Pc);
+    if (rc) return rc;
+    ctis_plan* P = const_cast<ctis_plan*>(Pc);
+    if (!g_dev || !f_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    if (k < 0) return fail(CTIS_ERR_INVALID_ARG, "k must be >= 0");
+    if (flags & ~(CTIS_INIT_ONES | CTIS_INIT_HTG) ||
+        (flags & CTIS_INIT_ONES && flags & CTIS_INIT_HTG))
+        return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CTIS_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)   // caller is building its own graph
+        return enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, st);
+
+    GraphKey key;
+    key.g = g_dev;
+    key.f = f_dev;
+    key.stats = stats_dev;
+    key.k = k;
+    key.flags = flags;
+    key.profiling = P->profiling;
+    if (!(P->gexec && P->gkey == key)) {
+        if (P->gexec) {
+            cudaGraphExecDestroy(P->gexec);
+            P->gexec = nullptr;
+        }
+        CTIS_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, P->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&P->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            P->gexec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        P->gkey = key;
+    }
+    CTIS_CUDA(cudaGraphLaunch(P->gexec, st));
+    return CTIS_OK;
+}
+
+int ctis_plan_set_profiling(ctis_plan* P, int enable) {
+    if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
+    P->profiling = enable != 0;
+    return CTIS_OK;
+}
+
+int ctis_plan_kernel_times(const ctis_plan* P, double* fwd_ms, int* n_fwd, double* adj_ms,
+                           int* n_adj) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    auto sum = [&](const std::vector<std::pair<int, int>>& log, double* ms, int* n) -> int {
+        double t = 0.0;
+        for (const auto& pr : log) {
+            CTIS_CUDA(cudaEventSynchronize(P->events[pr.second]));
+            float x = 0.f;
+            CTIS_CUDA(cudaEventElapsedTime(&x, P->events[pr.first], P->events[pr.second]));
+            t += x;
+        }
+        if (ms) *ms = t;
+        if (n) *n = static_cast<int>(log.size());
+        return CTIS_OK;
+    };
+    rc = sum(P->prof_fwd, fwd_ms, n_fwd);
+    if (!rc) rc = sum(P->prof_adj, adj_ms, n_adj);
+    return rc;
+}
+
+int ctis_plan_check(const ctis_plan* P, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    CTIS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int flag = 0;
+    CTIS_CUDA(cudaMemcpy(&flag, P->d_counters + 3, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CTIS_CUDA(cudaMemset(P->d_counters + 3, 0, sizeof(int)));
+        return fail(CTIS_ERR_TIMEOUT, "a kernel's bounded wait gave up (flag %d)", flag);
+    }
+    return CTIS_OK;
+}
+
+}  // extern "C"

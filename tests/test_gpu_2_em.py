@@ -1,0 +1,154 @@
+"""GPU parity of the fused EM iteration (Eq. 2, Algorithm 1) against the FP64 oracle.
+
+Tolerances (max floored-relative error, floor 1e-6 * max):
+  * one iteration from the same float32 iterate: 1e-5 (two projections of
+    <= 1e-5 each feed a ratio and a product; measured errors are ~1e-6);
+  * k iterations: k * 1e-5, and relative L2 <= 1e-5 * sqrt(k);
+  * statistics: float64 reductions of float32 pixel terms, 1e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle as O
+import synth
+from paper_2006_01573_gb300 import Plan
+from tests.helpers import floored_rel, geometry, problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+STAT_KEYS = ("flux_hf", "flux_g_covered", "loglik", "resid2")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+RAGGED = synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7, "mask_spectra", 500.0, 6)
+K5 = synth.Workload("k5", 20, 24, 6, 120, 110, 3, 36.0, 1.2, 5, 1.2, "segmentation", 800.0, 6)
+
+
+@pytest.fixture(scope="module", params=[synth.TINY, RAGGED, K5], ids=lambda w: w.name)
+def prob(request):
+    return (request.param,) + problem(request.param)
+
+
+def _plan(wl, psf):
+    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+
+
+def test_single_iteration_from_float32_iterate(prob):
+    wl, geom, psf, H, f_true, g = prob
+    f5, _ = O.mlem(H, g, 5)
+    f5 = f5.astype(np.float32)
+    ref = O.em_step(H, g, f5.astype(np.float64))
+    with _plan(wl, psf) as plan:
+        f = torch.from_numpy(f5.reshape(wl.w, wl.alpha, wl.a)).cuda()
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        out, _ = plan.reconstruct(gt, k=1, f=f, init=None)
+        plan.check()
+    assert floored_rel(out.cpu().numpy(), ref) <= 1e-5
+
+
+def test_k_iterations_and_statistics(prob):
+    wl, geom, psf, H, f_true, g = prob
+    k = wl.k
+    ref, hist = O.mlem(H, g, k)
+    with _plan(wl, psf) as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        f, st = plan.reconstruct(gt, k=k, init="ones", stats=True)
+        plan.check()
+        f, st = f.cpu().numpy().ravel(), st.cpu().numpy()
+    assert floored_rel(f, ref) <= k * 1e-5
+    assert rel_l2(f, ref) <= 1e-5 * math.sqrt(k)
+    assert np.all(f >= 0)
+    for t in range(k + 1):
+        for q, key in enumerate(STAT_KEYS):
+            assert abs(st[t, q] - hist[t][key]) <= 1e-5 * abs(hist[t][key]), (t, key)
+    # EM invariants seen on the GPU: flux of iterate t+1 equals the measured
+    # flux on the support of iterate t; the likelihood does not decrease.
+    for t in range(k):
+        assert abs(st[t + 1, 0] - st[t, 1]) <= 2e-6 * st[t, 1]
+        assert st[t + 1, 2] >= st[t, 2] - 1e-6 * abs(st[t, 2])
+
+
+def test_htg_initial_guess(prob):
+    wl, geom, psf, H, f_true, g = prob
+    with _plan(wl, psf) as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        f, _ = plan.reconstruct(gt, k=0, init="htg")
+        f1, _ = plan.reconstruct(gt, k=1, init="htg")
+        plan.check()
+    assert floored_rel(f.cpu().numpy(), H.adjoint(g)) <= 1e-5
+    ref1 = O.em_step(H, g, H.adjoint(g))
+    assert floored_rel(f1.cpu().numpy(), ref1) <= 2e-5
+
+
+def test_graph_replay_is_bitwise_reproducible():
+    wl = synth.TINY
+    _, psf, H, _, g = problem(wl)
+    with _plan(wl, psf) as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        f = torch.empty((wl.w, wl.alpha, wl.a), device="cuda")
+        outs = []
+        for _ in range(3):   # same pointers: the cached graph is replayed
+            plan.reconstruct(gt, k=7, f=f, init="ones")
+            outs.append(f.clone())
+        f2, _ = plan.reconstruct(gt, k=7, init="ones")   # new pointer: recaptured
+        plan.check()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert torch.equal(outs[0], f2)
+
+
+def test_noiseless_single_delta_recovers_scene_exactly():
+    """A delta PSF per wavelength on disjoint footprints: one EM step from ones
+    on noiseless data returns the scene (u = f_true, h = 1)."""
+    a, al, w, ga, xi = 12, 8, 3, 60, 30
+    x0 = [0, 20, 40]
+    psf = (np.arange(w + 1, dtype=np.int32), np.array(x0, np.int32), np.array([3, 10, 20], np.int32),
+           np.ones(w, np.float32))
+    f_true = synth.random_positive((w, al, a), 4)
+    geom = O.Geometry(a, al, w, ga, xi)
+    g = O.build_H(geom, psf).forward(f_true.ravel()).astype(np.float32)
+    with Plan(a, al, w, ga, xi, psf) as plan:
+        f, _ = plan.reconstruct(torch.from_numpy(g.reshape(xi, ga)).cuda(), k=1)
+    assert np.array_equal(f.cpu().numpy(), f_true)
+
+
+def test_full_size_first_iteration_sampled():
+    """Realistic workload, one EM step from ones in the benchmark's launch
+    configuration; sampled voxels evaluated one by one by the oracle."""
+    wl = synth.REALISTIC
+    geom = geometry(wl)
+    psf = synth.make_psf(wl)
+    taps = O.merge_psf(geom, psf)
+    f_true = synth.make_scene(wl)
+    rng = np.random.default_rng(1)
+    with _plan(wl, psf) as plan:
+        hf_true = plan.forward(torch.from_numpy(f_true).cuda())
+        # noise on the host from the GPU's noiseless image: inputs only
+        g, _ = synth.make_measurement(hf_true.cpu().numpy(), wl.peak, wl.seed)
+        gt = torch.from_numpy(g).cuda()
+        f1, st = plan.reconstruct(gt, k=1, init="ones", stats=True)
+        plan.check()
+        f1 = f1.cpu().numpy()
+    ss = rng.integers(0, wl.w, 40)
+    ps = rng.integers(0, wl.a, 40)
+    rs = rng.integers(0, wl.alpha, 40)
+    ones = np.ones(geom.m)
+    got, ref = [], []
+    for s, p, r in zip(ss, ps, rs):
+        tx, ty, tv = taps.of(int(s))
+        xs, ys = tx + p, ty + r
+        q = O.forward_at(geom, taps, ones, xs, ys)
+        u = np.where(q > 0, g[ys, xs] / np.where(q > 0, q, 1), 0.0)
+        zeta = float(np.dot(tv, u))
+        h = float(tv.sum())
+        ref.append(zeta / h)
+        got.append(f1[s, r, p])
+    assert floored_rel(got, ref) <= 1e-5
