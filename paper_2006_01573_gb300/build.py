@@ -64,4 +64,6 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    # python -m paper_2006_01573_gb300.build [--force] [-DNAME=VALUE ...]
+    defines = [a for a in sys.argv[1:] if a.startswith("-D")]
+    build(force="--force" in sys.argv or bool(defines), verbose=True, extra=defines)

@@ -22,7 +22,7 @@ namespace ctis {
 
 constexpr int kNumStats = 4;   // flux_hf, flux_g, loglik, resid2 (see ctis.h)
 
-struct TileDesc {        // 32 bytes
+struct TileDesc {        // 32 bytes (host-side bookkeeping)
     int x0, y0;          // output origin: FPA (x, y) forward, voxel (p, r) adjoint
     int plane;           // output plane: 0 forward, wavelength s adjoint
     int nchunks;         // items covering this tile
@@ -30,51 +30,68 @@ struct TileDesc {        // 32 bytes
     int pad0, pad1, pad2;
 };
 
-struct ItemDesc {        // 16 bytes
+struct ItemDesc {        // 16 bytes (host-side bookkeeping)
     int tile;
     int chunk;           // 0 .. nchunks-1
     int task_begin;
     int task_end;
 };
 
+// One work item as a warp reads it: everything it needs in a single 32-byte
+// load, stored in the order the warp processes its items.
+struct WorkItem {
+    int tile, x0, y0, plane;
+    int chunk_info;      // nchunks | (chunk << 16)
+    int scratch_base;
+    int task_begin, task_end;
+};
+
+// Input planes are kept as NC x-shifted copies (NC = elements per 16 bytes:
+// 4 for float32, 8 for bfloat16): copy q holds plane[x - q] at x (rows are
+// NC - 1 elements wider than the plane; the rest is zero). A window whose
+// origin x0 is not 16-byte aligned is read from copy q = (-x0) mod NC at the
+// aligned x0 + q, so every TMA box and every shared-memory load is aligned
+// and the kernel has a single code path.
 struct TaskDesc {        // 16 bytes
-    int wx;              // window origin x, a multiple of the 16-byte element count
+    int wx;              // aligned window origin x inside the chosen copy
     int wy;              // window origin y (any integer; TMA zero-fills outside)
-    int plane;           // input plane (wavelength s forward, 0 adjoint)
-    int wsel;            // (weight set index << 3) | (x offset inside the first chunk)
+    int plane;           // TMA depth coordinate: copy * planes + plane
+    int cluster;         // weight set index
 };
 
 enum Epilogue : int {
     kEpiRaw = 0,     // out_f32 = value                      (ctis_forward / ctis_adjoint)
-    kEpiRatio = 1,   // u = g / value, 0 where value == 0   (forward inside EM)
-    kEpiUpdate = 2,  // f_out = f_in * value / h_s, 0 where h_s == 0 (adjoint inside EM)
-    kEpiSet = 3      // f_out = value in the plan's dtype    (H^T g initial guess)
+    kEpiRatio = 1,   // u copies = g / value, 0 where value == 0  (forward inside EM)
+    kEpiUpdate = 2,  // f copies = f_in * value / h_s, 0 where h_s == 0 (adjoint inside EM)
+    kEpiSet = 3      // f copies = value in the plan's dtype  (H^T g initial guess)
 };
 
 struct GatherParams {
-    const ItemDesc* items;
-    const TileDesc* tiles;
+    const WorkItem* items;     // grouped by warp, in processing order
+    const int* warp_begin;     // [n_warps + 1] range of each warp in items
     const TaskDesc* tasks;
-    const void* weights;       // [sets][K*K] in the plan's storage type
-    const int* warp_begin;     // [n_warps + 1] range of each warp in warp_items
-    const int* warp_items;     // item indices in processing order, per warp
+    const void* weights;       // [clusters][padded K*K] in the plan's storage type
     int n_warps;
     int n_tiles;
     int out_w, out_h;          // extent of one output plane
     int mode;                  // Epilogue
     int with_stats;
-    // kEpiRaw / kEpiRatio output (float32)
+    // kEpiRaw output, or the kEpiRatio u copies (float32)
     float* out_f32;
     long long out_plane_stride;
     int out_pitch;
+    long long out_copy_stride;   // kEpiRatio: elements between u copies
+    int out_copies;              // kEpiRatio: number of u copies
     // kEpiRatio
     const float* g;
     int g_pitch;
-    // kEpiUpdate / kEpiSet (datacube in the plan's dtype)
+    // kEpiUpdate / kEpiSet (datacube copies in the plan's dtype; f_in = copy 0)
     const void* f_in;
     void* f_out;
     int f_pitch;
     long long f_plane_stride;
+    long long f_copy_stride;
+    int f_copies;
     const float* h;            // [w]
     // workspace
     float* scratch;            // partial tiles, [slots][TX*TY]
@@ -93,6 +110,24 @@ struct GatherShape {
     int NS;   // TMA stages per warp
 };
 
-constexpr GatherShape kShapeMain{8, 8, 4, 1, 2};   // 32 x 64 output tile per warp
+// Shapes of the two projectors. The defaults can be overridden at build time
+// (-DCTIS_FWD_R=..., etc.) to sweep them.
+#ifndef CTIS_FWD_R
+#define CTIS_FWD_R 8
+#endif
+#ifndef CTIS_FWD_NS
+#define CTIS_FWD_NS 2
+#endif
+#ifndef CTIS_ADJ_R
+#define CTIS_ADJ_R 8
+#endif
+#ifndef CTIS_ADJ_NS
+#define CTIS_ADJ_NS 2
+#endif
+#ifndef CTIS_NW
+#define CTIS_NW 4
+#endif
+constexpr GatherShape kShapeFwd{4, CTIS_FWD_R, 8, CTIS_NW, CTIS_FWD_NS};   // 32 x 32 tile
+constexpr GatherShape kShapeAdj{4, CTIS_ADJ_R, 8, CTIS_NW, CTIS_ADJ_NS};   // 32 x 32 tile
 
 }  // namespace ctis

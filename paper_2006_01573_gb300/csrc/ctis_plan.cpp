@@ -74,6 +74,7 @@ float bf16_bits_to_float(uint16_t b) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+int64_t floor_mod(int64_t a, int64_t b) { return a - floor_div(a, b) * b; }
 
 struct Cluster {
     int s, X, Y;
@@ -85,6 +86,8 @@ struct ProjTables {
     std::vector<TaskDesc> tasks;
     std::vector<int> warp_begin;   // [n_warps + 1]
     std::vector<int> warp_items;   // item indices, grouped by warp
+    std::vector<WorkItem> witems;  // the items in warp order, as the kernel reads them
+    int tile_w = 0, tile_h = 0;
     int64_t scratch_slots = 0;
     int per_item = 0;              // chunk size chosen for this table
     int n_warps = 0;
@@ -93,7 +96,7 @@ struct ProjTables {
     ItemDesc* d_items = nullptr;
     TaskDesc* d_tasks = nullptr;
     int* d_warp_begin = nullptr;
-    int* d_warp_items = nullptr;
+    WorkItem* d_witems = nullptr;
     void* d_weights = nullptr;
     int blocks_per_sm = 0;
 };
@@ -135,17 +138,19 @@ struct ctis_plan {
     int a = 0, alpha = 0, w = 0, gamma = 0, xi = 0, dtype = 0;
     int64_t m = 0, n = 0;
     int device = 0, num_sms = 0, K = 1;
-    int f_epc = 4;        // datacube elements per 16 bytes
-    int a_pitch = 0;      // pitch of the internal datacube copy (elements)
-    int g_pitch = 0;      // pitch of the internal FPA buffer (elements)
+    int f_epc = 4;        // datacube elements per 16 bytes (= number of f copies)
+    int a_pitch = 0;      // row pitch of the internal datacube copies (elements)
+    int g_pitch = 0;      // row pitch of the internal FPA copies (elements)
+    int f_copies = 4, u_copies = 4;
+    int64_t f_copy_stride = 0, u_copy_stride = 0;   // elements between copies
     std::vector<int32_t> tap_s, tap_x, tap_y;
     std::vector<float> tap_v;   // stored values widened to float32
     std::vector<float> h;       // [w]
     std::vector<Cluster> clusters;
     ProjTables fwd, adj;
     float* d_h = nullptr;
-    float* d_u = nullptr;
-    void* d_fwork = nullptr;
+    float* d_u = nullptr;        // u_copies x-shifted copies of the FPA input of the adjoint
+    void* d_fwork = nullptr;     // f_copies x-shifted copies of the datacube (forward input)
     float* d_scratch = nullptr;
     int* d_tickets = nullptr;
     int* d_counters = nullptr;
@@ -188,13 +193,13 @@ void free_tables(ProjTables& t) {
     cudaFree(t.d_tasks);
     cudaFree(t.d_weights);
     cudaFree(t.d_warp_begin);
-    cudaFree(t.d_warp_items);
+    cudaFree(t.d_witems);
     t.d_tiles = nullptr;
     t.d_items = nullptr;
     t.d_tasks = nullptr;
     t.d_weights = nullptr;
     t.d_warp_begin = nullptr;
-    t.d_warp_items = nullptr;
+    t.d_witems = nullptr;
 }
 
 void destroy(ctis_plan* P) {
@@ -221,7 +226,7 @@ void destroy(ctis_plan* P) {
 
 // Cost of an item in task units: its tasks, plus the partial-sum round trip
 // and ticket of a chunked tile, plus the epilogue.
-double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 1.0 : 0.0) + 0.25; }
+double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 2.0 : 0.0) + 0.5; }
 
 // Splits every tile's task range into chunks of at most `per_item` tasks and
 // fills the item list and the scratch slot bases.
@@ -309,6 +314,21 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
     make_items(T, begin, best);
     T.max_warp_load = assign_warps(T, n_warps);
     T.per_item = best;
+    T.witems.clear();
+    for (int i : T.warp_items) {
+        const ItemDesc& it = T.items[i];
+        const TileDesc& td = T.tiles[it.tile];
+        WorkItem w;
+        w.tile = it.tile;
+        w.x0 = td.x0;
+        w.y0 = td.y0;
+        w.plane = td.plane;
+        w.chunk_info = td.nchunks | (it.chunk << 16);
+        w.scratch_base = td.scratch_base;
+        w.task_begin = it.task_begin;
+        w.task_end = it.task_end;
+        T.witems.push_back(w);
+    }
 }
 
 // Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
@@ -490,30 +510,44 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     std::vector<float> wf(wts.size());
     for (int64_t c = 0; c < ncl; ++c)
         for (int e = 0; e < K * K; ++e) wf[c * K * K + e] = wts[c * K * K + (K * K - 1 - e)];
-    auto store_weights = [&](ProjTables& T, const std::vector<float>& src) -> int {
+    // weights of each cluster as duplicated pairs (w, w), padded to the
+    // kernel's 16-byte weight slot
+    auto store_weights = [&](ProjTables& T, bool forward, const std::vector<float>& src) -> int {
+        const int pad = gather_weight_pad(forward, K, P->dtype);
+        const size_t kk = static_cast<size_t>(K) * K;
         if (P->dtype == kDtypeBF16) {
-            std::vector<uint16_t> b(src.size());
-            for (size_t i = 0; i < src.size(); ++i) b[i] = to_bf16_bits(src[i]);
-            uint16_t* d = nullptr;
+            std::vector<uint32_t> b(static_cast<size_t>(ncl) * pad, 0);
+            for (int64_t c = 0; c < ncl; ++c)
+                for (size_t e = 0; e < kk; ++e) {
+                    const uint32_t h = to_bf16_bits(src[c * kk + e]);
+                    b[c * pad + e] = h | (h << 16);
+                }
+            uint32_t* d = nullptr;
             int rc = upload(P, &d, b);
             T.d_weights = d;
             return rc;
         }
+        std::vector<float> f(static_cast<size_t>(ncl) * pad * 2, 0.f);
+        for (int64_t c = 0; c < ncl; ++c)
+            for (size_t e = 0; e < kk; ++e) {
+                f[(c * pad + e) * 2] = src[c * kk + e];
+                f[(c * pad + e) * 2 + 1] = src[c * kk + e];
+            }
         float* d = nullptr;
-        int rc = upload(P, &d, src);
+        int rc = upload(P, &d, f);
         T.d_weights = d;
         return rc;
     };
 
-    const int TX = gather_tile_w(), TY = gather_tile_h();
     CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
     CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
-    const int warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta();
-    const int warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta();
+    const int warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta(true);
+    const int warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta(false);
 
     // ---- forward work lists: FPA tiles x clusters whose footprint meets them
     {
         ProjTables& T = P->fwd;
+        const int TX = T.tile_w = gather_tile_w(true, P->dtype), TY = T.tile_h = gather_tile_h(true, P->dtype);
         const int ntx = (ga + TX - 1) / TX, nty = (xi + TY - 1) / TY;
         const int fw = a + K - 1, fh = al + K - 1;   // footprint of one cluster
         std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
@@ -538,28 +572,26 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                     const Cluster& cl = P->clusters[c];
                     const int64_t px = static_cast<int64_t>(td.x0) - cl.X - (K - 1);
                     const int64_t py = static_cast<int64_t>(td.y0) - cl.Y - (K - 1);
-                    const int64_t wx = floor_div(px, P->f_epc) * P->f_epc;
+                    const int64_t q = floor_mod(-px, P->f_copies);   // copy holding px aligned
                     TaskDesc t;
-                    t.wx = static_cast<int>(wx);
+                    t.wx = static_cast<int>(px + q);
                     t.wy = static_cast<int>(py);
-                    t.plane = cl.s;
-                    t.wsel = (c << 3) | static_cast<int>(px - wx);
+                    t.plane = static_cast<int>(q) * w + cl.s;   // copy * w + s
+                    t.cluster = c;
                     tl.push_back(t);
                 }
-                std::stable_sort(tl.begin(), tl.end(), [](const TaskDesc& x, const TaskDesc& y) {
-                    return (x.wsel & 7) < (y.wsel & 7);
-                });
                 T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
                 begin.push_back(static_cast<int>(T.tasks.size()));
             }
         schedule(T, begin, warps_fwd, P->forced_per_item);
-        int rc = store_weights(T, wf);
+        int rc = store_weights(T, true, wf);
         if (rc) return rc;
     }
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
     {
         ProjTables& T = P->adj;
+        const int TX = T.tile_w = gather_tile_w(false, P->dtype), TY = T.tile_h = gather_tile_h(false, P->dtype);
         std::vector<int64_t> c_begin(w + 1, 0);
         for (int64_t c = 0; c < ncl; ++c) c_begin[P->clusters[c].s + 1]++;
         for (int s = 0; s < w; ++s) c_begin[s + 1] += c_begin[s];
@@ -578,22 +610,19 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                         const Cluster& cl = P->clusters[c];
                         const int64_t px = static_cast<int64_t>(cl.X) + td.x0;
                         const int64_t py = static_cast<int64_t>(cl.Y) + td.y0;
-                        const int64_t wx = floor_div(px, 4) * 4;
+                        const int64_t q = floor_mod(-px, P->u_copies);
                         TaskDesc t;
-                        t.wx = static_cast<int>(wx);
+                        t.wx = static_cast<int>(px + q);
                         t.wy = static_cast<int>(py);
-                        t.plane = 0;
-                        t.wsel = static_cast<int>(c << 3) | static_cast<int>(px - wx);
+                        t.plane = static_cast<int>(q);   // copy index
+                        t.cluster = static_cast<int>(c);
                         tl.push_back(t);
                     }
-                    std::stable_sort(tl.begin(), tl.end(), [](const TaskDesc& x, const TaskDesc& y) {
-                        return (x.wsel & 7) < (y.wsel & 7);
-                    });
                     T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
                     begin.push_back(static_cast<int>(T.tasks.size()));
                 }
         schedule(T, begin, warps_adj, P->forced_per_item);
-        int rc = store_weights(T, wts);
+        int rc = store_weights(T, false, wts);
         if (rc) return rc;
     }
 
@@ -603,23 +632,32 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         if (!rc) rc = upload(P, &T->d_items, T->items);
         if (!rc) rc = upload(P, &T->d_tasks, T->tasks);
         if (!rc) rc = upload(P, &T->d_warp_begin, T->warp_begin);
-        if (!rc) rc = upload(P, &T->d_warp_items, T->warp_items);
+        if (!rc) rc = upload(P, &T->d_witems, T->witems);
         if (rc) return rc;
     }
     int rc = upload(P, &P->d_h, P->h);
     if (rc) return rc;
     const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
-    rc = dmalloc(P, reinterpret_cast<void**>(&P->d_u), sizeof(float) * P->g_pitch * (size_t)xi);
-    if (!rc) rc = dmalloc(P, &P->d_fwork, es * P->a_pitch * (size_t)al * w);
-    const int64_t slots = std::max(P->fwd.scratch_slots, P->adj.scratch_slots);
+    P->u_copy_stride = static_cast<int64_t>(P->g_pitch) * xi;
+    P->f_copy_stride = static_cast<int64_t>(P->a_pitch) * al * w;
+    rc = dmalloc(P, reinterpret_cast<void**>(&P->d_u),
+                 sizeof(float) * static_cast<size_t>(P->u_copy_stride) * P->u_copies);
+    if (!rc) rc = dmalloc(P, &P->d_fwork, es * static_cast<size_t>(P->f_copy_stride) * P->f_copies);
+    const int64_t scratch_elems =
+        std::max(P->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
+                 P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch),
-                          sizeof(float) * static_cast<size_t>(slots) * TX * TY);
+                          sizeof(float) * static_cast<size_t>(scratch_elems));
     const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 8);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
                           sizeof(double) * kNumStats * P->fwd.tiles.size());
     if (rc) return rc;
+    // copies start zeroed: the elements past each copy's shifted end are never
+    // written and must read as zero
+    CTIS_CUDA(cudaMemset(P->d_u, 0, sizeof(float) * static_cast<size_t>(P->u_copy_stride) * P->u_copies));
+    CTIS_CUDA(cudaMemset(P->d_fwork, 0, es * static_cast<size_t>(P->f_copy_stride) * P->f_copies));
     CTIS_CUDA(cudaMemset(P->d_tickets, 0, sizeof(int) * ntiles));
     CTIS_CUDA(cudaMemset(P->d_counters, 0, sizeof(int) * 8));
     CTIS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
@@ -660,12 +698,10 @@ int make_map(CUtensorMap* map, const void* base, int dtype, int width, int heigh
 
 GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     GatherParams p{};
-    p.items = T.d_items;
-    p.tiles = T.d_tiles;
+    p.items = T.d_witems;
+    p.warp_begin = T.d_warp_begin;
     p.tasks = T.d_tasks;
     p.weights = T.d_weights;
-    p.warp_begin = T.d_warp_begin;
-    p.warp_items = T.d_warp_items;
     p.n_warps = T.n_warps;
     p.n_tiles = static_cast<int>(T.tiles.size());
     p.scratch = P->d_scratch;
@@ -676,51 +712,55 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     return p;
 }
 
-// Forward pass from a datacube laid out with row pitch `f_pitch` (elements).
-int enqueue_forward(const ctis_plan* P, const void* f, int f_pitch, GatherParams p,
-                    cudaStream_t st) {
-    CUtensorMap slab, halo;
-    const int bw = gather_box_w(P->K, P->dtype);
-    const int64_t plane = static_cast<int64_t>(f_pitch) * P->alpha;
-    int rc = make_map(&slab, f, P->dtype, P->a, P->alpha, P->w, f_pitch, plane, bw,
-                      gather_tile_h() / (32 / kShapeMain.LX));
+// Forward pass from the plan's datacube copies.
+int enqueue_forward(const ctis_plan* P, GatherParams p, cudaStream_t st) {
+    CUtensorMap win;
+    const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
+    int rc = make_map(&win, P->d_fwork, P->dtype, P->a + P->f_copies - 1, P->alpha,
+                      P->w * P->f_copies, P->a_pitch, plane, gather_box_w(true, P->K, P->dtype),
+                      gather_window_rows(true, P->K, P->dtype));
     if (rc) return rc;
-    halo = slab;
-    if (P->K > 1) {
-        rc = make_map(&halo, f, P->dtype, P->a, P->alpha, P->w, f_pitch, plane, bw, P->K - 1);
-        if (rc) return rc;
-    }
-    CTIS_CUDA(gather_launch(true, P->K, P->dtype, slab, halo, p, st));
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
     return CTIS_OK;
 }
 
-// Adjoint pass from an FPA vector laid out with row pitch `r_pitch` (elements).
-int enqueue_adjoint(const ctis_plan* P, const float* r, int r_pitch, GatherParams p,
-                    cudaStream_t st) {
-    CUtensorMap slab, halo;
-    const int bw = gather_box_w_input_f32(P->K);
-    const int64_t plane = static_cast<int64_t>(r_pitch) * P->xi;
-    int rc = make_map(&slab, r, kDtypeF32, P->gamma, P->xi, 1, r_pitch, plane, bw,
-                      gather_tile_h() / (32 / kShapeMain.LX));
+// Adjoint pass from the plan's FPA copies.
+int enqueue_adjoint(const ctis_plan* P, GatherParams p, cudaStream_t st) {
+    CUtensorMap win;
+    int rc = make_map(&win, P->d_u, kDtypeF32, P->gamma + P->u_copies - 1, P->xi, P->u_copies,
+                      P->g_pitch, P->u_copy_stride, gather_box_w(false, P->K, P->dtype),
+                      gather_window_rows(false, P->K, P->dtype));
     if (rc) return rc;
-    halo = slab;
-    if (P->K > 1) {
-        rc = make_map(&halo, r, kDtypeF32, P->gamma, P->xi, 1, r_pitch, plane, bw, P->K - 1);
-        if (rc) return rc;
-    }
-    CTIS_CUDA(gather_launch(false, P->K, P->dtype, slab, halo, p, st));
+    CTIS_CUDA(gather_launch(false, P->K, P->dtype, win, p, st));
     return CTIS_OK;
 }
 
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-// Datacube usable by TMA in place: 16-byte aligned base and row pitch.
-bool f_in_place(const ctis_plan* P, const void* f) {
-    return aligned16(f) && (P->a % P->f_epc) == 0;
+// Fills the datacube copies from a dense caller datacube (src_dtype) or, when
+// src is null, with `value`.
+int scatter_f(const ctis_plan* P, const void* src, int src_dtype, float value, cudaStream_t st) {
+    CTIS_CUDA(launch_scatter_copies(P->dtype, P->d_fwork, P->f_copy_stride, P->f_copies,
+                                    P->a_pitch, static_cast<int64_t>(P->a_pitch) * P->alpha, src,
+                                    src_dtype, P->a, static_cast<int64_t>(P->a) * P->alpha, P->a,
+                                    P->alpha, P->w, value, st));
+    return CTIS_OK;
 }
 
-bool r_in_place(const ctis_plan* P, const void* r) {
-    return aligned16(r) && (P->gamma % 4) == 0;
+// Fills the FPA copies from a dense float32 caller image.
+int scatter_u(const ctis_plan* P, const float* src, cudaStream_t st) {
+    CTIS_CUDA(launch_scatter_copies(kDtypeF32, P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch,
+                                    P->u_copy_stride, src, kDtypeF32, P->gamma,
+                                    static_cast<int64_t>(P->gamma) * P->xi, P->gamma, P->xi, 1,
+                                    0.f, st));
+    return CTIS_OK;
+}
+
+void set_f_copies(const ctis_plan* P, GatherParams& p) {
+    p.f_in = P->d_fwork;
+    p.f_out = P->d_fwork;
+    p.f_pitch = P->a_pitch;
+    p.f_plane_stride = static_cast<int64_t>(P->a_pitch) * P->alpha;
+    p.f_copy_stride = P->f_copy_stride;
+    p.f_copies = P->f_copies;
 }
 
 // Records event `idx` of the plan's pool on `st` (an event-record node when
@@ -733,48 +773,37 @@ int record(ctis_plan* P, int idx, cudaStream_t st) {
 // Enqueues the whole reconstruction on `st`.
 int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
                         double* stats, cudaStream_t st) {
-    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
-    const bool inplace = f_in_place(P, f);
-    void* fw = inplace ? f : P->d_fwork;
-    const int fp = inplace ? P->a : P->a_pitch;
-    const int64_t fplane = static_cast<int64_t>(fp) * P->alpha;
     int rc;
     if (flags & CTIS_INIT_ONES) {
-        CTIS_CUDA(launch_fill(P->dtype, fw, P->a, P->alpha * P->w, fp, 1.0f, st));
+        rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
     } else if (flags & CTIS_INIT_HTG) {
-        CTIS_CUDA(cudaMemcpy2DAsync(P->d_u, sizeof(float) * P->g_pitch, g,
-                                    sizeof(float) * P->gamma, sizeof(float) * P->gamma, P->xi,
-                                    cudaMemcpyDeviceToDevice, st));
+        rc = scatter_u(P, g, st);
+        if (rc) return rc;
         GatherParams p = base_params(P, P->adj);
         p.mode = kEpiSet;
         p.out_w = P->a;
         p.out_h = P->alpha;
-        p.f_out = fw;
-        p.f_pitch = fp;
-        p.f_plane_stride = fplane;
-        rc = enqueue_adjoint(P, P->d_u, P->g_pitch, p, st);
-        if (rc) return rc;
-    } else if (!inplace) {
-        CTIS_CUDA(cudaMemcpy2DAsync(fw, es * P->a_pitch, f, es * P->a, es * P->a,
-                                    static_cast<size_t>(P->alpha) * P->w,
-                                    cudaMemcpyDeviceToDevice, st));
+        set_f_copies(P, p);
+        rc = enqueue_adjoint(P, p, st);
+    } else {
+        rc = scatter_f(P, f, P->dtype, 0.f, st);
     }
+    if (rc) return rc;
     GatherParams pf = base_params(P, P->fwd);
     pf.mode = kEpiRatio;
     pf.out_w = P->gamma;
     pf.out_h = P->xi;
     pf.out_f32 = P->d_u;
     pf.out_pitch = P->g_pitch;
+    pf.out_copy_stride = P->u_copy_stride;
+    pf.out_copies = P->u_copies;
     pf.g = g;
     pf.g_pitch = P->gamma;
     GatherParams pa = base_params(P, P->adj);
     pa.mode = kEpiUpdate;
     pa.out_w = P->a;
     pa.out_h = P->alpha;
-    pa.f_in = fw;
-    pa.f_out = fw;
-    pa.f_pitch = fp;
-    pa.f_plane_stride = fplane;
+    set_f_copies(P, pa);
     P->prof_fwd.clear();
     P->prof_adj.clear();
     int ev = 0;
@@ -799,16 +828,15 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
         if (it == k && !stats) break;
         pf.with_stats = stats != nullptr;
         pf.stats_out = stats ? stats + static_cast<int64_t>(it) * kNumStats : nullptr;
-        rc = timed(P->prof_fwd, [&] { return enqueue_forward(P, fw, fp, pf, st); });
+        rc = timed(P->prof_fwd, [&] { return enqueue_forward(P, pf, st); });
         if (rc) return rc;
         if (it == k) break;
-        rc = timed(P->prof_adj, [&] { return enqueue_adjoint(P, P->d_u, P->g_pitch, pa, st); });
+        rc = timed(P->prof_adj, [&] { return enqueue_adjoint(P, pa, st); });
         if (rc) return rc;
     }
-    if (!inplace)
-        CTIS_CUDA(cudaMemcpy2DAsync(f, es * P->a, fw, es * P->a_pitch, es * P->a,
-                                    static_cast<size_t>(P->alpha) * P->w,
-                                    cudaMemcpyDeviceToDevice, st));
+    CTIS_CUDA(launch_gather_copy0(P->dtype, f, P->d_fwork, P->a_pitch,
+                                  static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
+                                  P->w, st));
     return CTIS_OK;
 }
 
@@ -891,9 +919,12 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     P->m = (int64_t)a * alpha * w;
     P->n = (int64_t)gamma * xi;
     P->f_epc = dtype == CTIS_BF16 ? 8 : 4;
+    P->f_copies = gather_input_copies(true, dtype);
+    P->u_copies = gather_input_copies(false, dtype);
     P->forced_per_item = forced_per_item;
-    P->a_pitch = static_cast<int>(round_up(a, P->f_epc));
-    P->g_pitch = static_cast<int>(round_up(gamma, 4));
+    // copies are NC - 1 elements wider than the plane (see TaskDesc)
+    P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
+    P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
@@ -970,16 +1001,8 @@ int ctis_forward(const ctis_plan* P, const void* f_dev, float* hf_dev, void* str
     if (rc) return rc;
     if (!f_dev || !hf_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const void* f = f_dev;
-    int fp = P->a;
-    if (!f_in_place(P, f_dev)) {
-        const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
-        CTIS_CUDA(cudaMemcpy2DAsync(P->d_fwork, es * P->a_pitch, f_dev, es * P->a, es * P->a,
-                                    static_cast<size_t>(P->alpha) * P->w,
-                                    cudaMemcpyDeviceToDevice, st));
-        f = P->d_fwork;
-        fp = P->a_pitch;
-    }
+    rc = scatter_f(P, f_dev, P->dtype, 0.f, st);
+    if (rc) return rc;
     GatherParams p = base_params(P, P->fwd);
     p.mode = kEpiRaw;
     p.out_w = P->gamma;
@@ -987,7 +1010,7 @@ int ctis_forward(const ctis_plan* P, const void* f_dev, float* hf_dev, void* str
     p.out_f32 = hf_dev;
     p.out_pitch = P->gamma;
     p.out_plane_stride = 0;
-    return enqueue_forward(P, f, fp, p, st);
+    return enqueue_forward(P, p, st);
 }
 
 int ctis_adjoint(const ctis_plan* P, const float* r_dev, float* out_dev, void* stream) {
@@ -995,15 +1018,8 @@ int ctis_adjoint(const ctis_plan* P, const float* r_dev, float* out_dev, void* s
     if (rc) return rc;
     if (!r_dev || !out_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const float* r = r_dev;
-    int rp = P->gamma;
-    if (!r_in_place(P, r_dev)) {
-        CTIS_CUDA(cudaMemcpy2DAsync(P->d_u, sizeof(float) * P->g_pitch, r_dev,
-                                    sizeof(float) * P->gamma, sizeof(float) * P->gamma, P->xi,
-                                    cudaMemcpyDeviceToDevice, st));
-        r = P->d_u;
-        rp = P->g_pitch;
-    }
+    rc = scatter_u(P, r_dev, st);
+    if (rc) return rc;
     GatherParams p = base_params(P, P->adj);
     p.mode = kEpiRaw;
     p.out_w = P->a;
@@ -1011,8 +1027,25 @@ int ctis_adjoint(const ctis_plan* P, const float* r_dev, float* out_dev, void* s
     p.out_f32 = out_dev;
     p.out_pitch = P->a;
     p.out_plane_stride = static_cast<long long>(P->a) * P->alpha;
-    return enqueue_adjoint(P, r, rp, p, st);
+    return enqueue_adjoint(P, p, st);
 }
+
+#ifdef CTIS_DEBUG_BOUNDS
+// Debug builds: register the buffers of a call for the epilogue range checks.
+int ctis_debug_arm(const ctis_plan* P, const void* user0, size_t bytes0, const void* user1,
+                   size_t bytes1, unsigned long long* log_dev) {
+    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+    const void* lo[6] = {P->d_u, P->d_fwork, P->d_scratch, user0, user1, nullptr};
+    const size_t bytes[6] = {sizeof(float) * static_cast<size_t>(P->u_copy_stride) * P->u_copies,
+                             es * static_cast<size_t>(P->f_copy_stride) * P->f_copies,
+                             sizeof(float) * static_cast<size_t>(std::max(
+                                 P->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
+                                 P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h)),
+                             bytes0, bytes1, 0};
+    CTIS_CUDA(debug_arm(lo, bytes, log_dev));
+    return CTIS_OK;
+}
+#endif
 
 int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k, int flags,
                      double* stats_dev, void* stream) {
