@@ -163,6 +163,31 @@ int ctis_plan_set_profiling(ctis_plan* plan, int enable);
 int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,
                            int* n_adj);
 
+/* H f like ctis_forward, but with the projection's scratch (the x-shifted
+ * copies of f, chunk partial sums, tile tickets and counters) taken from a
+ * fixed array inside the library instead of the plan's workspace. The paper
+ * has no counterpart; this exists for callers that cannot call cudaMalloc
+ * when they project (allocation-free real-time loops, code whose device
+ * memory all belongs to its own pool, or code running under a stream capture
+ * that rejects allocation). The call allocates nothing and calls no
+ * allocating routine.
+ *   - The array holds CTIS_STATIC_SCRATCH_BYTES (64 MiB) per GPU from the
+ *     moment the library is loaded on that GPU until the process exits.
+ *     Plans whose forward needs more return CTIS_ERR_UNSUPPORTED (the
+ *     realistic 128x128x64 -> 1024^2 workload needs about 35 MiB; the
+ *     256x256x128 -> 2048^2 one does not fit).
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, and it keeps the last
+ *     call's contents (each call clears what must start at zero). Calls whose
+ *     executions overlap on the GPU (other streams, other threads, other
+ *     plans) race on it: serialise them.
+ *   - A device-side wait that gives up is not reported by ctis_plan_check
+ *     for this call. */
+#define CTIS_STATIC_SCRATCH_BYTES (64u << 20)
+int ctis_forward_static_scratch(const ctis_plan* plan, const void* f_dev, float* hf_dev,
+                                void* stream);
+
 /* Wait for the plan's work on `stream`, then report (and clear) any device-side
  * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
 int ctis_plan_check(const ctis_plan* plan, void* stream);

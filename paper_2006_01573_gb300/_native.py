@@ -25,7 +25,7 @@ _lib = None
 EXPORTED = (
     "ctis_plan_create", "ctis_plan_create_ex", "ctis_plan_destroy", "ctis_plan_get_info", "ctis_plan_export_taps",
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
-    "ctis_plan_set_profiling", "ctis_plan_kernel_times",
+    "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "ctis_adjoint": (I, [P, VP, VP, VP]),
         "ctis_reconstruct": (I, [P, VP, VP, I, I, VP, VP]),
         "ctis_plan_check": (I, [P, VP]),
+        "ctis_forward_static_scratch": (I, [P, VP, VP, VP]),
         "ctis_plan_set_profiling": (I, [P, I]),
         "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),

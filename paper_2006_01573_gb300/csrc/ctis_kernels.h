@@ -45,6 +45,10 @@ cudaError_t launch_gather_copy0(int dtype, void* dst, const void* src, int src_p
 // Registers the buffers epilogue accesses may touch (debug builds only).
 cudaError_t debug_arm(const void* const lo[6], const size_t bytes[6], unsigned long long* log);
 #endif
+// Fixed scratch array of ctis_forward_static_scratch (ctis_static_scratch.cu).
+size_t static_scratch_bytes();
+cudaError_t static_scratch_ptr(void** out);   // device address on the current device
+
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream);
 

@@ -1123,6 +1123,65 @@ int ctis_plan_kernel_times(const ctis_plan* P, double* fwd_ms, int* n_fwd, doubl
     return rc;
 }
 
+int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf_dev,
+                                void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!f_dev || !hf_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    // Pieces of the static array, each 256-byte aligned: counters, tile
+    // tickets, chunk partial sums, the x-shifted copies of f.
+    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = static_cast<size_t>(round_up(static_cast<int64_t>(off + bytes), 256));
+        return o;
+    };
+    const size_t o_counters = take(8 * sizeof(int));
+    const size_t o_tickets = take(P->fwd.tiles.size() * sizeof(int));
+    const size_t o_partials = take(sizeof(float) * static_cast<size_t>(P->fwd.scratch_slots) *
+                                   P->fwd.tile_w * P->fwd.tile_h);
+    const size_t copies_bytes = es * static_cast<size_t>(P->f_copy_stride) * P->f_copies;
+    const size_t o_copies = take(copies_bytes);
+    if (off > static_scratch_bytes())
+        return fail(CTIS_ERR_UNSUPPORTED,
+                    "this plan's forward projection needs %zu bytes of scratch; the static "
+                    "scratch array holds %zu bytes (use ctis_forward)",
+                    off, static_scratch_bytes());
+    void* base_v = nullptr;
+    CTIS_CUDA(static_scratch_ptr(&base_v));
+    unsigned char* base = static_cast<unsigned char*>(base_v);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The array keeps the previous call's contents: counters and tickets must
+    // start at zero, and so must the copies (their unwritten ends are read).
+    CTIS_CUDA(cudaMemsetAsync(base + o_counters, 0, o_partials - o_counters, st));
+    CTIS_CUDA(cudaMemsetAsync(base + o_copies, 0, copies_bytes, st));
+    void* copies = base + o_copies;
+    const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
+    CTIS_CUDA(launch_scatter_copies(P->dtype, copies, P->f_copy_stride, P->f_copies, P->a_pitch,
+                                    plane, f_dev, P->dtype, P->a,
+                                    static_cast<int64_t>(P->a) * P->alpha, P->a, P->alpha, P->w,
+                                    0.f, st));
+    CUtensorMap win;
+    rc = make_map(&win, copies, P->dtype, P->a + P->f_copies - 1, P->alpha, P->w * P->f_copies,
+                  P->a_pitch, plane, gather_box_w(true, P->K, P->dtype),
+                  gather_window_rows(true, P->K, P->dtype));
+    if (rc) return rc;
+    GatherParams p = base_params(P, P->fwd);
+    p.scratch = reinterpret_cast<float*>(base + o_partials);
+    p.tickets = reinterpret_cast<int*>(base + o_tickets);
+    p.counters = reinterpret_cast<int*>(base + o_counters);
+    p.tile_stats = nullptr;
+    p.mode = kEpiRaw;
+    p.out_w = P->gamma;
+    p.out_h = P->xi;
+    p.out_f32 = hf_dev;
+    p.out_pitch = P->gamma;
+    p.out_plane_stride = 0;
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
 int ctis_plan_check(const ctis_plan* P, void* stream) {
     int rc = check_plan(P);
     if (rc) return rc;
