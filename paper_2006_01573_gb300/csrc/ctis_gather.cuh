@@ -1,0 +1,790 @@
+// Windowed-gather device code for the shift-invariant CTIS projector pair,
+// shared by the forward and adjoint translation units.
+//
+// Forward (Eqs. 1, 8-9):  (H f)(x, y) = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k)
+// Adjoint (Eq. 11):     (H^T r)_s(p, r) = sum_k v_{s,k} r(x_k + p, y_k + r)
+//
+// The PSF nonzeros of each wavelength are grouped into K x K spot clusters.
+// Applying one cluster to an output tile is a K x K correlation of a window of
+// the input plane (forward: f_s, zero outside the field stop; adjoint: the FPA
+// vector) with the cluster's weights (flipped for the forward). Both
+// projectors are therefore gathers: every output element is owned by one
+// thread, no atomics touch data, and the summation order is fixed by the plan,
+// so results are bit-reproducible.
+//
+// GB300 mapping:
+//  * every warp is an independent persistent worker with a static list of
+//    work items (balanced longest-first on the host) whose tasks are stored
+//    contiguously: no work-fetch atomics, no block-wide barriers;
+//  * lane 0 stages the input window of each task with tensor TMA
+//    (cp.async.bulk.tensor) and the task's weights with a bulk copy into one
+//    of NS shared-memory stages completed on an mbarrier, NS tasks ahead of
+//    the compute loop, across item boundaries;
+//  * a window is one dense TMA box; the 8 lanes of a quarter warp read 8
+//    consecutive 16-byte chunks of a row (conflict-free); TMA fills
+//    coordinates outside the plane with zeros, which is exactly the zero
+//    padding of the forward projector;
+//  * each lane keeps an R x C block of outputs in registers and slides down
+//    the window one input row at a time, so every staged value feeds up to
+//    K*K packed FMAs;
+//  * epilogues are fused and selected at compile time: the EM ratio
+//    u = g / (H f) with float64 statistics, and the multiplicative update
+//    f <- f * (H^T u) / h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "ctis_internal.h"
+#include "ctis_kernels.h"
+
+namespace ctis {
+namespace {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier, TMA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM cycles (about a second), records the
+// failure in the plan's error flag and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) {
+            atomicOr(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// element conversion
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Elem;
+template <>
+struct Elem<float> {
+    static constexpr int kPerChunk = 4;   // elements per 16-byte chunk
+    __device__ static __forceinline__ void load_chunk(const float* p, float* out) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    }
+    __device__ static __forceinline__ float load(const float* p) { return *p; }
+    __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
+    // weight stored as a duplicated pair (w, w)
+    using WPair = float2;
+    __device__ static __forceinline__ float2 weight_pair(const WPair& w) { return w; }
+};
+template <>
+struct Elem<__nv_bfloat16> {
+    static constexpr int kPerChunk = 8;
+    __device__ static __forceinline__ void load_chunk(const __nv_bfloat16* p, float* out) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            out[2 * q] = __uint_as_float(w[q] << 16);
+            out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+        }
+    }
+    __device__ static __forceinline__ float load(const __nv_bfloat16* p) {
+        return __bfloat162float(*p);
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+    // weight stored as a duplicated pair of bfloat16 in one 32-bit word
+    using WPair = uint32_t;
+    __device__ static __forceinline__ float2 weight_pair(const WPair& w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// compile-time geometry of one instantiation
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one stage: the task's input window as ONE dense TMA
+// box of (TY + K - 1) rows x BXW elements (row pitch BXW), then the task's
+// weights. Lanes are laid out LX = 8 across a row: the 8 lanes of a quarter
+// warp read 8 consecutive 16-byte chunks of one row, which hit 8 different
+// bank groups whatever the pitch, so the window needs no padding or skew.
+template <int K_, int C_, int R_, int LX_, int NW_, int NS_, typename TIn, typename TF>
+struct Geo {
+    static constexpr int K = K_, C = C_, R = R_, LX = LX_, NW = NW_, NS = NS_;
+    static constexpr int LY = 32 / LX;
+    static constexpr int TX = LX * C, TY = LY * R;
+    static constexpr int ES = int(sizeof(TIn));
+    static constexpr int EPC = Elem<TIn>::kPerChunk;
+    static_assert(C % EPC == 0, "a lane's columns must be whole 16-byte chunks");
+    static_assert(LX >= 8, "a quarter warp must span 8 consecutive chunks of a row");
+    // window row: TX + K - 1 elements from a chunk-aligned origin
+    static constexpr int BXW = (TX + K - 1 + EPC - 1) / EPC * EPC;
+    static constexpr int ROWS = TY + K - 1;           // TMA box height
+    static_assert((BXW * ES) % 16 == 0 && BXW <= 256 && ROWS <= 256, "TMA box");
+    static constexpr int WINDOW_BYTES = ROWS * BXW * ES;
+    // per-cluster weights (duplicated pairs), padded to a 16-byte multiple,
+    // copied with the window
+    static constexpr int WES = int(sizeof(typename Elem<TF>::WPair));
+    static constexpr int WPAD = (K * K * WES + 15) / 16 * 16 / WES;
+    static constexpr int WBYTES = WPAD * WES;
+    static constexpr int WOFF = (WINDOW_BYTES + 15) / 16 * 16;   // bytes into the stage
+    static constexpr int STAGE_BYTES = (WOFF + WBYTES + 127) / 128 * 128;
+    static_assert(STAGE_BYTES % 128 == 0, "TMA destinations must be 128-byte aligned");
+    static constexpr uint32_t TX_BYTES = uint32_t(WINDOW_BYTES + WBYTES);
+    static constexpr int TILE = TX * TY;
+    static constexpr int THREADS = NW * 32;
+    static constexpr int STAGES_BYTES = NW * NS * STAGE_BYTES;
+    static constexpr int SMEM_BYTES = STAGES_BYTES + NW * NS * 8;
+};
+
+// ---------------------------------------------------------------------------
+// per-lane correlation of one staged window
+// ---------------------------------------------------------------------------
+// acc[o][c] += sum_{dy,dx} w[dy][dx] * win[o + dy][c + dx]
+// `win` points at this lane's first element (window row ty*R, column tx*C).
+// Windows are chunk-aligned (shifted copies), so each row is a few 16-byte
+// loads; the even-offset operand pairs of the packed FMAs come straight from
+// them and the odd-offset pairs are formed once per row.
+template <class G, typename TIn>
+__device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const TIn* win,
+                                          const float2 (&w2)[G::K * G::K]) {
+    constexpr int K = G::K, C = G::C, R = G::R, EPC = G::EPC;
+    constexpr int NE = C + K - 1;                 // elements used per row
+    constexpr int NCH = (NE + EPC - 1) / EPC;
+    constexpr int NP = NCH * EPC / 2;             // even-offset pairs loaded
+#pragma unroll
+    for (int i = 0; i < R + K - 1; ++i) {
+        const TIn* rowp = win + i * G::BXW;
+        float raw[NCH * EPC];
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) Elem<TIn>::load_chunk(rowp + q * EPC, raw + q * EPC);
+        float2 ev[NP], od[NP - 1];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
+#pragma unroll
+        for (int k = 0; k + 1 < NP; ++k) od[k] = make_float2(raw[2 * k + 1], raw[2 * k + 2]);
+#pragma unroll
+        for (int dx = 0; dx < K; ++dx) {
+#pragma unroll
+            for (int dy = 0; dy < K; ++dy) {
+                const int o = i - dy;
+                if (o >= 0 && o < R) {
+#pragma unroll
+                    for (int c2 = 0; c2 < C / 2; ++c2) {
+                        // outputs (2c2, 2c2+1) need elements 2c2+dx, 2c2+dx+1
+                        const float2 x2 = (dx & 1) ? od[c2 + dx / 2] : ev[c2 + dx / 2];
+                        acc[o][c2] = __ffma2_rn(x2, w2[dy * K + dx], acc[o][c2]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epilogues (per warp, straight from the lanes' register blocks)
+// ---------------------------------------------------------------------------
+// Lane (tx, ty) owns tile rows ty*R .. ty*R+R-1 and columns tx*C .. tx*C+C-1.
+template <class G>
+__device__ __forceinline__ int tile_elem(int tx, int ty, int o, int c) {
+    return (ty * G::R + o) * G::TX + tx * G::C + c;
+}
+
+// Optional self-check of every epilogue access against the buffer ranges the
+// host registered (compiled in with -DCTIS_DEBUG_BOUNDS only): a bad access
+// is counted, its address recorded, and the access still happens only when
+// it is in range.
+#ifdef CTIS_DEBUG_BOUNDS
+__device__ DbgRanges g_dbg;
+__device__ __forceinline__ bool dbg_ok(const void* ptr, int bytes) {
+    const char* p0 = static_cast<const char*>(ptr);
+    for (int i = 0; i < 6; ++i)
+        if (g_dbg.lo[i] && p0 >= g_dbg.lo[i] && p0 + bytes <= g_dbg.hi[i]) return true;
+    if (g_dbg.log) {
+        if (atomicAdd(g_dbg.log, 1ull) == 0) g_dbg.log[1] = reinterpret_cast<unsigned long long>(p0);
+    }
+    return false;
+}
+#define DBG_CHECK_RANGE(ptr, n) \
+    if (!dbg_ok((ptr), int(sizeof(*(ptr))) * (n))) continue
+#else
+#define DBG_CHECK_RANGE(ptr, n) ((void)0)
+#endif
+
+// Vector access to C consecutive elements (16 bytes of float32, or 8/16 bytes
+// of bfloat16) at an address aligned to that size.
+template <typename T, int C>
+struct Vec;
+template <>
+struct Vec<float, 4> {
+    __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Vec<float, 8> {
+    __device__ static __forceinline__ void load(const float* p, float (&v)[8]) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float4 b = reinterpret_cast<const float4*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+    __device__ static __forceinline__ void store(float* p, const float (&v)[8]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+__device__ __forceinline__ void unpack_bf16x2(uint32_t w, float& lo, float& hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+template <>
+struct Vec<__nv_bfloat16, 4> {
+    __device__ static __forceinline__ void load(const __nv_bfloat16* p, float (&v)[4]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        unpack_bf16x2(q.x, v[0], v[1]);
+        unpack_bf16x2(q.y, v[2], v[3]);
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16* p, const float (&v)[4]) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+    }
+};
+
+template <>
+struct Vec<__nv_bfloat16, 8> {
+    __device__ static __forceinline__ void load(const __nv_bfloat16* p, float (&v)[8]) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        unpack_bf16x2(q.x, v[0], v[1]);
+        unpack_bf16x2(q.y, v[2], v[3]);
+        unpack_bf16x2(q.z, v[4], v[5]);
+        unpack_bf16x2(q.w, v[6], v[7]);
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16* p, const float (&v)[8]) {
+        *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                  pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    }
+};
+
+// Reads this lane's C consecutive elements of a row starting at column x
+// (tile-relative column base; `n_valid` of them inside the plane). Uses one
+// vector load when the row is complete and aligned, element loads otherwise.
+template <typename T, int C>
+__device__ __forceinline__ void load_row(const T* p, int n_valid, bool aligned, float (&v)[C]) {
+#ifdef CTIS_DEBUG_BOUNDS
+    for (int c = 0; c < C; ++c) v[c] = 0.f;
+    for (int c = 0; c < C && c < n_valid; ++c) {
+        DBG_CHECK_RANGE(p + c, 1);
+        v[c] = Elem<T>::load(p + c);
+    }
+    return;
+#endif
+    if (n_valid >= C && aligned) {
+        Vec<T, C>::load(p, v);
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = c < n_valid ? Elem<T>::load(p + c) : 0.f;
+    }
+}
+
+// Stores this lane's row values v[0..C-1] (plane columns col0 + c, col0 =
+// tx*C inside the tile; `tile_cols` of the tile's columns lie inside the
+// plane) into the x-shifted copies: copy q holds plane column x at x + q.
+// `row` points at copy 0, tile column 0, of this row. For each copy the lane
+// writes the C-aligned group [col0, col0 + C) of that copy with one vector
+// store; the values come from this lane and its left neighbours (warp
+// shuffles, same lane row). Groups cut by the tile edge, and the q values
+// that spill past the tile's right edge, are written element by element.
+template <typename T, int C, int LX>
+__device__ __forceinline__ void store_copies(T* row, long long copy_stride, int ncopies, bool active,
+                                             int tx, int tile_cols, const float (&v)[C]) {
+    constexpr int NCMAX = 16 / int(sizeof(T));
+    const int col0 = tx * C;
+    // `ncopies` is the same for every lane of the launch, so all lanes run
+    // every shuffle; lanes of rows outside the plane (`active` false) store
+    // nothing.
+#pragma unroll
+    for (int q = 0; q < NCMAX; ++q) {
+        if (q >= ncopies) break;
+        float a[C];
+        bool full = active;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            // destination column col0 + j of copy q holds source column col0 + j - q
+            const int d = j >= q ? 0 : (q - j + C - 1) / C;     // lanes to the left
+            const int e = ((j - q) % C + C) % C;                // element in that lane
+            const float up = __shfl_up_sync(0xffffffffu, v[e], d);
+            a[j] = d == 0 ? v[e] : up;
+            const int src = col0 + j - q;
+            if (tx < d || src >= tile_cols) full = false;
+        }
+        if (!active) continue;
+        T* dst = row + q * copy_stride;
+        if (full) {
+            DBG_CHECK_RANGE(dst + col0, C);
+            Vec<T, C>::store(dst + col0, a);
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const int d = j >= q ? 0 : (q - j + C - 1) / C;
+                const int src = col0 + j - q;
+                if (tx >= d && src >= 0 && src < tile_cols) {
+                    DBG_CHECK_RANGE(dst + col0 + j, 1);
+                    Elem<T>::store(dst + col0 + j, a[j]);
+                }
+            }
+        }
+        // spill: own source columns whose copy-q position is past the tile
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int src = col0 + c;
+            if (src + q >= LX * C && src < tile_cols) {
+                DBG_CHECK_RANGE(dst + src + q, 1);
+                Elem<T>::store(dst + src + q, v[c]);
+            }
+        }
+    }
+}
+
+// Applies the epilogue MODE to the lane's outputs v[o][c] of the item's tile;
+// accumulates the forward statistics of the lane in stat[].
+template <class G, typename TF, int MODE>
+__device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& it, int tx,
+                                         int ty, const float (&v)[G::R][G::C],
+                                         float (&stat)[kNumStats]) {
+    constexpr int C = G::C;
+    const int tile_cols = min(G::TX, p.out_w - it.x0);
+    const int col0 = tx * C;
+    const int n_valid = tile_cols - col0;
+    float rh = 0.f;   // kEpiUpdate: 1 / h_s (0 where h_s == 0: f = 0 there)
+    if constexpr (MODE == kEpiUpdate) {
+        const float hs = p.h[it.plane];
+        rh = hs != 0.f ? 1.0f / hs : 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < G::R; ++o) {
+        const int y = it.y0 + ty * G::R + o;
+        const bool row_ok = y < p.out_h;      // warp-divergent only at the bottom edge
+        if constexpr (MODE == kEpiRaw) {
+            if (!row_ok || n_valid <= 0) continue;
+            float* dst = p.out_f32 + it.plane * p.out_plane_stride + (long long)y * p.out_pitch +
+                         it.x0 + col0;
+#ifdef CTIS_DEBUG_BOUNDS
+            for (int c = 0; c < C && c < n_valid; ++c) {
+                DBG_CHECK_RANGE(dst + c, 1);
+                dst[c] = v[o][c];
+            }
+            continue;
+#endif
+            if (n_valid >= C && (p.out_pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                Vec<float, C>::store(dst, v[o]);
+            } else {
+                for (int c = 0; c < C && c < n_valid; ++c) dst[c] = v[o][c];
+            }
+        } else if constexpr (MODE == kEpiRatio) {
+            float gv[C], u[C];
+            const float* gp = p.g + (long long)(row_ok ? y : 0) * p.g_pitch + it.x0 + col0;
+            load_row<float, C>(gp, row_ok ? n_valid : 0,
+                               (p.g_pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(gp) & 15) == 0, gv);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float val = v[o][c];
+                // u = g / Hf on the support of Hf (Eq. 12); the fast quotient
+                // (within 2 ulp) is used for normal Hf, the IEEE one below
+                u[c] = val >= 1.17549435e-38f ? __fdividef(gv[c], val) : (val > 0.f ? gv[c] / val : 0.f);
+            }
+            if (p.with_stats) {   // uniform; selects instead of branches per element
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float val = v[o][c];
+                    const bool on = val > 0.f && row_ok && c < n_valid;
+                    const float hv = on ? val : 0.f, gg = on ? gv[c] : 0.f;
+                    stat[0] += hv;
+                    stat[1] += gg;
+                    stat[2] += gg * __logf(on ? val : 1.f) - hv;
+                    const float dd = gg - hv;
+                    stat[3] += dd * dd;
+                }
+            }
+            // all lanes of the row take part in the shuffles; rows past the
+            // plane store nothing
+            float* row = p.out_f32 + (long long)(row_ok ? y : 0) * p.out_pitch + it.x0;
+            store_copies<float, C, G::LX>(row, p.out_copy_stride, p.out_copies, row_ok, tx,
+                                          tile_cols, u);
+        } else {   // kEpiUpdate, or kEpiSet when p.mode says so
+            const long long rowoff = it.plane * p.f_plane_stride +
+                                     (long long)(row_ok ? y : 0) * p.f_pitch + it.x0;
+            float fv[C];
+            if (p.mode == kEpiUpdate) {
+                float fi[C];
+                load_row<TF, C>(static_cast<const TF*>(p.f_in) + rowoff + col0,
+                                row_ok ? n_valid : 0, true, fi);
+#pragma unroll
+                for (int c = 0; c < C; ++c) fv[c] = fi[c] * v[o][c] * rh;
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) fv[c] = v[o][c];
+            }
+            store_copies<TF, C, G::LX>(static_cast<TF*>(p.f_out) + rowoff, p.f_copy_stride,
+                                       p.f_copies, row_ok, tx, tile_cols, fv);
+        }
+    }
+}
+
+// Fixed-order float64 warp sum (same tree on every run); lane 0 gets the total.
+__device__ __forceinline__ double warp_sum(double d) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+    return d;
+}
+
+// Statistics of one finished tile, reduced in a fixed two-level tree so that
+// no single warp walks all tiles: the warp that finishes the last tile of a
+// group of 32 tiles adds that group (one tile per lane), and the warp that
+// finishes the last group adds the groups into p.stats_out. Tile sums are
+// per-lane float32 sums of 32 elements widened to float64; everything above
+// them is float64 in a fixed order, so the result is reproducible.
+__device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumStats]) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(src));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(src) + 1);
+    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+}
+
+__device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx,
+                                             const float (&stat)[kNumStats], int lane) {
+    static_assert(kNumStats == 4, "statistics move as two double2");
+    const int n_groups = (p.n_tiles + kStatGroup - 1) / kStatGroup;
+    double* group_stats = p.tile_stats + (long long)p.n_tiles * kNumStats;
+    int* group_tickets = p.tickets + p.n_tiles;
+    double tot[kNumStats];
+#pragma unroll
+    for (int q = 0; q < kNumStats; ++q) tot[q] = warp_sum(static_cast<double>(stat[q]));
+    const int group = tile_idx / kStatGroup;
+    const int in_group = min(kStatGroup, p.n_tiles - group * kStatGroup);
+    int last = 0;
+    if (lane == 0) {
+        double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
+        __stcg(dst, make_double2(tot[0], tot[1]));
+        __stcg(dst + 1, make_double2(tot[2], tot[3]));
+        __threadfence();
+        last = atomicAdd(&group_tickets[group], 1) == in_group - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double d[kNumStats] = {0.0, 0.0, 0.0, 0.0};
+    if (lane < in_group)
+        load_stats(p.tile_stats + (long long)(group * kStatGroup + lane) * kNumStats, d);
+#pragma unroll
+    for (int q = 0; q < kNumStats; ++q) d[q] = warp_sum(d[q]);
+    last = 0;
+    if (lane == 0) {
+        double2* dst = reinterpret_cast<double2*>(group_stats + (long long)group * kNumStats);
+        __stcg(dst, make_double2(d[0], d[1]));
+        __stcg(dst + 1, make_double2(d[2], d[3]));
+        group_tickets[group] = 0;
+        __threadfence();
+        last = atomicAdd(&p.counters[2], 1) == n_groups - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
+    for (int g0 = 0; g0 < n_groups; g0 += 32) {   // all loads of a pass in flight at once
+        double e[kNumStats] = {0.0, 0.0, 0.0, 0.0};
+        if (g0 + lane < n_groups) load_stats(group_stats + (long long)(g0 + lane) * kNumStats, e);
+#pragma unroll
+        for (int q = 0; q < kNumStats; ++q) t[q] += e[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kNumStats; ++q) t[q] = warp_sum(t[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kNumStats; ++q) p.stats_out[q] = t[q];
+        p.counters[2] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel body (wrapped by forward_kernel / adjoint_kernel)
+// ---------------------------------------------------------------------------
+// Every warp owns a contiguous range of items (a static, longest-first
+// balanced list made on the host), and the tasks of those items are stored
+// contiguously in the same order, so the TMA issue cursor is a plain counter
+// over the warp's task range running NS tasks ahead of the compute loop,
+// across item boundaries. Only lane 0 reads task descriptors (it alone issues
+// the copies); it loads the next one right after each issue, so the load's
+// latency overlaps a task of compute.
+template <class G, typename TIn, typename TF, int MODE>
+__device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const GatherParams& p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + G::STAGES_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * G::NW + warp;
+    if (gw >= p.n_warps) return;
+    const int ib = p.warp_begin[gw], ie = p.warp_begin[gw + 1];
+    if (ib >= ie) return;   // nothing issued, nothing to drain
+    const int tx = lane % G::LX, ty = lane / G::LX;
+    unsigned char* my_stages = smem_raw + warp * G::NS * G::STAGE_BYTES;
+    uint64_t* my_bars = bars + warp * G::NS;
+    if (lane == 0) {
+        for (int s = 0; s < G::NS; ++s) mbar_init(&my_bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    const int lane_off = ty * G::R * G::BXW + tx * G::C;   // this lane's first element
+    WorkItem next_it = p.items[ib];
+    const int task_end = p.items[ie - 1].task_end;         // end of the warp's task range
+    int issue_task = next_it.task_begin;                    // next task to issue (uniform)
+    int issue_stage = 0;
+    int cons_stage = 0;
+    uint32_t cons_phase = 0;
+    int outstanding = 0;                                    // copies issued, not yet waited for
+    bool failed = false;                                    // warp-uniform
+    TaskDesc nxt{};                                         // lane 0: descriptor of issue_task
+    if (lane == 0 && issue_task < task_end) nxt = p.tasks[issue_task];
+
+    auto issue_next = [&]() {
+        if (issue_task >= task_end || failed) return;
+        if (lane == 0) {
+            unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
+            uint64_t* bar = &my_bars[issue_stage];
+            mbar_arrive_expect_tx(bar, G::TX_BYTES);
+            tma_load_3d(stage, &tm_win, nxt.wx, nxt.wy, nxt.plane, bar);
+            bulk_load(stage + G::WOFF,
+                      static_cast<const unsigned char*>(p.weights) + (long long)nxt.cluster * G::WBYTES,
+                      G::WBYTES, bar);
+            if (issue_task + 1 < task_end) nxt = p.tasks[issue_task + 1];
+        }
+        ++issue_task;
+        ++outstanding;
+        if (++issue_stage == G::NS) issue_stage = 0;
+    };
+#pragma unroll
+    for (int j = 0; j < G::NS; ++j) issue_next();
+
+    for (int ii = ib; ii < ie; ++ii) {
+        const WorkItem it = next_it;
+        if (ii + 1 < ie) next_it = p.items[ii + 1];   // prefetch; used next item
+        // pull the epilogue's inputs toward L1 while the item's tasks run
+        if constexpr (MODE == kEpiRatio || MODE == kEpiUpdate) {
+            if (MODE == kEpiRatio || p.mode == kEpiUpdate) {
+#pragma unroll
+                for (int o = 0; o < G::R; ++o) {
+                    const int y = it.y0 + ty * G::R + o;
+                    const int x = it.x0 + tx * G::C;
+                    if (y < p.out_h && x < p.out_w) {
+                        const void* src =
+                            MODE == kEpiRatio
+                                ? static_cast<const void*>(p.g + (long long)y * p.g_pitch + x)
+                                : static_cast<const void*>(static_cast<const TF*>(p.f_in) +
+                                                           it.plane * p.f_plane_stride +
+                                                           (long long)y * p.f_pitch + x);
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(src));
+                    }
+                }
+            }
+        }
+
+        float2 acc[G::R][G::C / 2];
+#pragma unroll
+        for (int o = 0; o < G::R; ++o)
+#pragma unroll
+            for (int c = 0; c < G::C / 2; ++c) acc[o][c] = make_float2(0.f, 0.f);
+
+        for (int t = it.task_begin; t < it.task_end; ++t) {
+            if (!failed) {
+                // fast path: one try_wait; the bounded spin runs only when the
+                // copies have not landed yet
+                if (!mbar_try_wait(&my_bars[cons_stage], cons_phase)) {
+                    const bool ok = mbar_wait_bounded(&my_bars[cons_stage], cons_phase, &p.counters[3]);
+                    failed = __any_sync(0xffffffffu, !ok);
+                }
+            }
+            if (!failed) {
+                const unsigned char* stage = my_stages + cons_stage * G::STAGE_BYTES;
+                using WP = typename Elem<TF>::WPair;
+                const WP* ws = reinterpret_cast<const WP*>(stage + G::WOFF);
+                float2 w2[G::K * G::K];
+#pragma unroll
+                for (int q = 0; q < G::K * G::K; ++q) w2[q] = Elem<TF>::weight_pair(ws[q]);
+                correlate<G, TIn>(acc, reinterpret_cast<const TIn*>(stage) + lane_off, w2);
+                // after a failed wait the stage and phase stay at the copy
+                // that did not land, where the final drain resumes
+                --outstanding;
+                if (++cons_stage == G::NS) {
+                    cons_stage = 0;
+                    cons_phase ^= 1u;
+                }
+            }
+            __syncwarp();   // every lane is done with the stage before it is refilled
+            issue_next();
+        }
+
+        float v[G::R][G::C];
+#pragma unroll
+        for (int o = 0; o < G::R; ++o)
+#pragma unroll
+            for (int c = 0; c < G::C / 2; ++c) {
+                v[o][2 * c] = acc[o][c].x;
+                v[o][2 * c + 1] = acc[o][c].y;
+            }
+
+        const int nchunks = it.chunk_info & 0xffff;
+        const int chunk = it.chunk_info >> 16;
+        bool finish = true;
+        if (nchunks > 1) {
+            float* slots = p.scratch + (long long)it.scratch_base * G::TILE;
+            float* mine = slots + (long long)chunk * G::TILE;
+#pragma unroll
+            for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                for (int c = 0; c < G::C; c += 4)
+                    __stcg(reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)),
+                           make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]));
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&p.tickets[it.tile], 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            finish = old == nchunks - 1;
+            if (finish) {
+                __threadfence();
+#pragma unroll
+                for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                    for (int c = 0; c < G::C; c += 4) {
+                        const int e = tile_elem<G>(tx, ty, o, c);
+                        float4 s4 = __ldcg(reinterpret_cast<const float4*>(slots + e));
+                        for (int ch = 1; ch < nchunks; ++ch) {
+                            const float4 q4 = __ldcg(
+                                reinterpret_cast<const float4*>(slots + (long long)ch * G::TILE + e));
+                            s4.x += q4.x; s4.y += q4.y; s4.z += q4.z; s4.w += q4.w;
+                        }
+                        v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
+                    }
+                if (lane == 0) p.tickets[it.tile] = 0;
+            }
+        }
+        if (finish) {
+            float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
+            epilogue<G, TF, MODE>(p, it, tx, ty, v, stat);
+            if constexpr (MODE == kEpiRatio) {
+                if (p.with_stats) finish_stats(p, it.tile, stat, lane);
+            }
+        }
+    }
+
+    // Copies still in flight exist only after a failed wait: give them a
+    // bounded chance to land before the warp's shared memory is released.
+    if (lane == 0) {
+        while (outstanding > 0) {
+            if (!mbar_wait_bounded(&my_bars[cons_stage], cons_phase, &p.counters[3])) break;
+            --outstanding;
+            if (++cons_stage == G::NS) {
+                cons_stage = 0;
+                cons_phase ^= 1u;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// A lane owns whole 16-byte chunks: C = 4 float32 or 8 bfloat16 columns; the
+// rows per lane shrink with the element size so a lane keeps the same number
+// of accumulators.
+template <bool FWD, typename TIn>
+constexpr GatherShape shape_of() {
+    GatherShape s = FWD ? kShapeFwd : kShapeAdj;
+    const int c = 16 / int(sizeof(TIn));
+    s.R = s.R * s.C / c;
+    s.C = c;
+    return s;
+}
+
+template <int K, typename TIn, typename TF, bool FWD>
+using GeoOf = Geo<K, shape_of<FWD, TIn>().C, shape_of<FWD, TIn>().R, shape_of<FWD, TIn>().LX,
+                  shape_of<FWD, TIn>().NW, shape_of<FWD, TIn>().NS, TIn, TF>;
+
+template <class G, class Kern>
+cudaError_t prepare_kernel(Kern kern, int* blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         G::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, G::THREADS,
+                                                      G::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return *blocks_per_sm >= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+template <class G, class Kern>
+cudaError_t launch_kernel(Kern kern, const CUtensorMap& win, const GatherParams& p,
+                          cudaStream_t stream) {
+    const int grid = (p.n_warps + G::NW - 1) / G::NW;
+    kern<<<grid, G::THREADS, G::SMEM_BYTES, stream>>>(win, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace ctis

@@ -21,6 +21,7 @@
 namespace ctis {
 
 constexpr int kNumStats = 4;   // flux_hf, flux_g, loglik, resid2 (see ctis.h)
+constexpr int kStatGroup = 32; // forward tiles per group of the statistics tree
 
 struct TileDesc {        // 32 bytes (host-side bookkeeping)
     int x0, y0;          // output origin: FPA (x, y) forward, voxel (p, r) adjoint
@@ -69,7 +70,7 @@ enum Epilogue : int {
 struct GatherParams {
     const WorkItem* items;     // grouped by warp, in processing order
     const int* warp_begin;     // [n_warps + 1] range of each warp in items
-    const TaskDesc* tasks;
+    const TaskDesc* tasks;     // in item order: each warp's tasks are contiguous
     const void* weights;       // [clusters][padded K*K] in the plan's storage type
     int n_warps;
     int n_tiles;
@@ -96,7 +97,7 @@ struct GatherParams {
     // workspace
     float* scratch;            // partial tiles, [slots][TX*TY]
     int* tickets;              // [n_tiles], zero between launches
-    int* counters;             // [2] stat tiles done, [3] error flag (others unused)
+    int* counters;             // [2] statistics groups done, [3] error flag (others unused)
     double* tile_stats;        // [n_tiles][kNumStats]
     double* stats_out;         // [kNumStats] or nullptr
 };
@@ -129,5 +130,10 @@ struct GatherShape {
 #endif
 constexpr GatherShape kShapeFwd{4, CTIS_FWD_R, 8, CTIS_NW, CTIS_FWD_NS};   // 32 x 32 tile
 constexpr GatherShape kShapeAdj{4, CTIS_ADJ_R, 8, CTIS_NW, CTIS_ADJ_NS};   // 32 x 32 tile
+
+#ifdef CTIS_DEBUG_BOUNDS
+// Buffers the epilogues may touch, registered by debug builds only.
+struct DbgRanges { const char* lo[6]; const char* hi[6]; unsigned long long* log; };
+#endif
 
 }  // namespace ctis

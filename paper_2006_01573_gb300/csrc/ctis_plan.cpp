@@ -92,8 +92,6 @@ struct ProjTables {
     int per_item = 0;              // chunk size chosen for this table
     int n_warps = 0;
     double max_warp_load = 0.0;    // LPT estimate of the busiest warp, task units
-    TileDesc* d_tiles = nullptr;
-    ItemDesc* d_items = nullptr;
     TaskDesc* d_tasks = nullptr;
     int* d_warp_begin = nullptr;
     WorkItem* d_witems = nullptr;
@@ -188,17 +186,13 @@ int upload(ctis_plan* P, T** dst, const std::vector<T>& src) {
 }
 
 void free_tables(ProjTables& t) {
-    cudaFree(t.d_tiles);
-    cudaFree(t.d_items);
     cudaFree(t.d_tasks);
-    cudaFree(t.d_weights);
     cudaFree(t.d_warp_begin);
+    cudaFree(t.d_weights);
     cudaFree(t.d_witems);
-    t.d_tiles = nullptr;
-    t.d_items = nullptr;
     t.d_tasks = nullptr;
-    t.d_weights = nullptr;
     t.d_warp_begin = nullptr;
+    t.d_weights = nullptr;
     t.d_witems = nullptr;
 }
 
@@ -314,7 +308,11 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
     make_items(T, begin, best);
     T.max_warp_load = assign_warps(T, n_warps);
     T.per_item = best;
+    // the kernel's view: items in warp order, and their tasks stored in the
+    // same order, so every warp's tasks form one contiguous range
     T.witems.clear();
+    std::vector<TaskDesc> wt;
+    wt.reserve(T.tasks.size());
     for (int i : T.warp_items) {
         const ItemDesc& it = T.items[i];
         const TileDesc& td = T.tiles[it.tile];
@@ -325,10 +323,12 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
         w.plane = td.plane;
         w.chunk_info = td.nchunks | (it.chunk << 16);
         w.scratch_base = td.scratch_base;
-        w.task_begin = it.task_begin;
-        w.task_end = it.task_end;
+        w.task_begin = static_cast<int>(wt.size());
+        wt.insert(wt.end(), T.tasks.begin() + it.task_begin, T.tasks.begin() + it.task_end);
+        w.task_end = static_cast<int>(wt.size());
         T.witems.push_back(w);
     }
+    T.tasks.swap(wt);
 }
 
 // Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
@@ -628,9 +628,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
 
     // ---- device buffers
     for (ProjTables* T : {&P->fwd, &P->adj}) {
-        int rc = upload(P, &T->d_tiles, T->tiles);
-        if (!rc) rc = upload(P, &T->d_items, T->items);
-        if (!rc) rc = upload(P, &T->d_tasks, T->tasks);
+        int rc = upload(P, &T->d_tasks, T->tasks);
         if (!rc) rc = upload(P, &T->d_warp_begin, T->warp_begin);
         if (!rc) rc = upload(P, &T->d_witems, T->witems);
         if (rc) return rc;
@@ -648,11 +646,15 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                  P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch),
                           sizeof(float) * static_cast<size_t>(scratch_elems));
-    const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
+    // tickets: one per tile (chunked tiles), then one per group of
+    // kStatGroup forward tiles (statistics); statistics: per forward tile,
+    // then per group
+    const size_t stat_groups = (P->fwd.tiles.size() + kStatGroup - 1) / kStatGroup;
+    const size_t ntiles = std::max(P->fwd.tiles.size() + stat_groups, P->adj.tiles.size());
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 8);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
-                          sizeof(double) * kNumStats * P->fwd.tiles.size());
+                          sizeof(double) * kNumStats * (P->fwd.tiles.size() + stat_groups));
     if (rc) return rc;
     // copies start zeroed: the elements past each copy's shifted end are never
     // written and must read as zero
@@ -699,9 +701,9 @@ int make_map(CUtensorMap* map, const void* base, int dtype, int width, int heigh
 GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     GatherParams p{};
     p.items = T.d_witems;
-    p.warp_begin = T.d_warp_begin;
     p.tasks = T.d_tasks;
     p.weights = T.d_weights;
+    p.warp_begin = T.d_warp_begin;
     p.n_warps = T.n_warps;
     p.n_tiles = static_cast<int>(T.tiles.size());
     p.scratch = P->d_scratch;
