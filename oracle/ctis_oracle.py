@@ -20,6 +20,9 @@ shift-invariance":
   (:func:`index_map`).
 * Eq. 10 (forward) and Eq. 14 (back projection) in their FFT form
   (:func:`fft_forward`, :func:`fft_adjoint`).
+* The bfloat16 storage form (datacube and PSF values kept in bfloat16, sums in
+  wider precision) is not in the paper; :func:`round_bf16` states the storage
+  rounding and :func:`em_step_stored` applies it to an EM step.
 
 Everything is float64. Inputs given as float32 (datacube, PSF values, counts)
 are promoted exactly. Readings of points the paper leaves open:
@@ -38,8 +41,9 @@ Pins (tests/test_oracle_*.py): every function here is checked against something
 other than itself - a dense H assembled literally from Eqs. 5-7, the FFT form of
 Eqs. 10/14 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
 for w = 1, brute-force Python loops on tiny inputs, hand-worked values in
-tests/golden/, the EM invariants (nonnegativity, flux, monotone likelihood) and
-finite differences of a dense H.
+tests/golden/, the EM invariants (nonnegativity, flux, monotone likelihood),
+finite differences of a dense H, and PyTorch's float32 -> bfloat16 conversion
+for :func:`round_bf16`.
 """
 from __future__ import annotations
 
@@ -368,6 +372,26 @@ def fft_adjoint(geom: Geometry, psf, u: np.ndarray) -> np.ndarray:
         d = np.fft.rfft(_calibration_column(geom, taps, s))
         z[s * geom.n:(s + 1) * geom.n] = np.fft.irfft(np.conj(d) * U, n=geom.n)
     return z[index_map(geom)]
+
+
+# --- bfloat16 storage form ------------------------------------------------------
+
+def round_bf16(x) -> np.ndarray:
+    """Rounds float32 values to the nearest bfloat16 (ties to even), returned as
+    float32: bfloat16 keeps the sign, the 8-bit exponent and the top 7 mantissa
+    bits of a float32, so rounding adds half of the dropped 16-bit field (plus
+    one when the kept last bit is odd, which breaks ties to even) and clears it.
+    Finite inputs only (the PSF values and datacubes it is used on)."""
+    bits = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32)
+
+
+def em_step_stored(H: BlockH, g: np.ndarray, f: np.ndarray, store) -> np.ndarray:
+    """One EM update (Eq. 2) computed in float64 from the stored iterate ``f``,
+    whose result is then stored through ``store`` (e.g. rounding to float32
+    then bfloat16, as a reduced-precision datacube keeps it)."""
+    return np.asarray(store(em_step(H, g, f)), dtype=np.float64)
 
 
 # --- gradients (for the differentiable projector) ------------------------------

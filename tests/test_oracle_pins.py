@@ -345,3 +345,39 @@ def test_planted_mistakes_are_caught_by_dense_pin(kind):
     f = synth.random_positive(geom.m, 12).astype(np.float64)
     D = O.dense_H(geom, psf)
     assert not np.allclose(_mutant_forward(geom, taps, f, kind), D @ f, rtol=1e-6)
+
+
+# --- bfloat16 storage rounding ---------------------------------------------------
+
+def test_round_bf16_matches_torch_conversion():
+    """round_bf16 against PyTorch's float32 -> bfloat16 cast (round to nearest
+    even) on random magnitudes, exact ties of both parities and values that
+    are already bfloat16."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    x = (rng.uniform(0, 1, 4000) * 10.0 ** rng.integers(-30, 30, 4000)).astype(np.float32)
+    # upper 16 bits below 0x7f80: finite, positive (exponent field < 255)
+    ties = (rng.integers(1, 0x7F80, 2000).astype(np.uint32) << 16 | 0x8000).view(np.float32)
+    exact = (rng.integers(1, 0x7F80, 500).astype(np.uint32) << 16).view(np.float32)
+    for v in (x, ties, exact):
+        want = torch.from_numpy(v.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+        assert np.array_equal(O.round_bf16(v).view(np.uint32), want.view(np.uint32))
+    assert np.array_equal(O.round_bf16(exact), exact)
+
+
+def test_round_bf16_ties_go_to_even():
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 (kept last bit even: down);
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6 (odd: up)
+    v = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20], np.float32)
+    assert O.round_bf16(v).tolist() == [1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7]
+
+
+def test_em_step_stored_with_exact_store_is_em_step():
+    geom = _geom(5, 4, 3, 14, 12)
+    psf = _tiny_psf(geom, 6, 44)
+    H = O.build_H(geom, psf)
+    f = synth.random_positive(geom.m, 45).astype(np.float64)
+    g = H.forward(synth.random_positive(geom.m, 46))
+    assert np.array_equal(O.em_step_stored(H, g, f, lambda z: z), O.em_step(H, g, f))
+    stored = O.em_step_stored(H, g, f, lambda z: O.round_bf16(z.astype(np.float32)))
+    assert np.array_equal(stored, O.round_bf16(O.em_step(H, g, f).astype(np.float32)))
