@@ -116,7 +116,8 @@ class ClockSampler:
 # --------------------------------------------------------------------------- helpers
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("ctis_gather.cu", "ctis_internal.h"):
+    for name in ("ctis_gather.cuh", "ctis_gather_fwd.cu", "ctis_gather_adj.cu", "ctis_gather.cu",
+                 "ctis_internal.h"):
         with open(os.path.join(ROOT, "paper_2006_01573_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -366,6 +367,7 @@ def run_ours(args, wl, k):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
+    line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value)}
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
         v, iters_cpu, el, desc = oracle_sample(wl, g_host, args.cpu_budget)
@@ -374,6 +376,39 @@ def run_ours(args, wl, k):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def bf16_form(args, wl, k, psf, g, f32_result, flush, stream, f32_value):
+    """The bfloat16 storage form (datacube and PSF values in bfloat16, float32
+    sums) on the same workload and g: its iterations/s, the ratio to the plain
+    float32 path, and the relative L2 distance of its reconstruction from the
+    float32 one after k iterations."""
+    import torch
+    from paper_2006_01573_gb300 import Plan
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16")
+    fb = torch.empty(f32_result.shape, device=g.device, dtype=torch.bfloat16)
+    stats = torch.empty((k + 1, 4), device=g.device, dtype=torch.float64)
+    for _ in range(max(1, args.warmup)):
+        plan.reconstruct(g, k, f=fb, init="ones", stats=stats)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    total = 0.0
+    for i in range(steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.reconstruct(g, k, f=fb, init="ones", stats=stats)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    plan.check()
+    value = steps * k / (total / 1e3)
+    a = fb.double()
+    b = f32_result.double()
+    err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    plan.close()
+    return {"value": value, "unit": "it/s", "steps": steps, "vs_f32": value / f32_value,
+            "rel_l2_vs_f32_after_k": err, "dtype": "bf16 storage, f32 accumulate"}
 
 
 def main():
