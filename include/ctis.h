@@ -188,6 +188,37 @@ int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, do
 int ctis_forward_static_scratch(const ctis_plan* plan, const void* f_dev, float* hf_dev,
                                 void* stream);
 
+/* ---- gradients (the differentiable form of the projector pair) ----------
+ * The PSF values are the parameters: tap t of wavelength s, at FPA offset
+ * (x_t, y_t) for field-stop pixel (0, 0), adds v_t f_s(p, r) to pixel
+ * (x_t + p, y_t + r) (Sec. 2), so H is linear in every v_t. Taps are
+ * indexed in ctis_plan_export_taps order (merged, sorted by (s, y, x)). */
+
+/* Replace the plan's tap values (host float32[nnz], finite and >= 0),
+ * rounded to the plan's dtype, and recompute h = H^T 1 (Eq. 2). Waits for all
+ * device work first (queued kernels may read the old tables); the plan's
+ * cached reconstruction graph stays valid and uses the new values. */
+int ctis_plan_set_values(ctis_plan* plan, const float* vals);
+
+/* dval_dev[t] = sum_{p,r} f_s(p, r) * r(x_t + p, y_t + r): the gradient of
+ * <r, H f> with respect to v_t (s = tap t's wavelength). f_dev: m elements of
+ * the plan's dtype; r_dev: n float32; dval_dev: nnz float32. Sums are float32
+ * in a fixed order (reproducible). */
+int ctis_psf_grad(const ctis_plan* plan, const void* f_dev, const float* r_dev,
+                  float* dval_dev, void* stream);
+
+/* The Poisson negative log-likelihood after k EM updates (Eq. 2) and its
+ * gradient through the updates:
+ *   f^(0) = f0 (or all ones when f0_dev is NULL), f^(t+1) = EM(f^(t)),
+ *   L = sum_i q_i - g_i log q_i over q = H f^(k), pixels with q_i > 0;
+ *   nll_dev[0] = L (float64), dval_dev[t] = dL/dv_t (including the
+ *   dependence of h = H^T 1 on v), df0_dev = dL/df0 when not NULL (float32).
+ * The iterates are checkpointed (the plan keeps (k+1)*m float32 of workspace,
+ * grown on demand); the backward pass recomputes each step's projections.
+ * float32 plans only (CTIS_ERR_UNSUPPORTED otherwise); 0 <= k <= 4096. */
+int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_dev, int k,
+                           double* nll_dev, float* dval_dev, float* df0_dev, void* stream);
+
 /* Wait for the plan's work on `stream`, then report (and clear) any device-side
  * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
 int ctis_plan_check(const ctis_plan* plan, void* stream);

@@ -26,6 +26,7 @@ EXPORTED = (
     "ctis_plan_create", "ctis_plan_create_ex", "ctis_plan_destroy", "ctis_plan_get_info", "ctis_plan_export_taps",
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
+    "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -77,6 +78,9 @@ def load(path: str = LIB_PATH):
         "ctis_plan_set_profiling": (I, [P, I]),
         "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
+        "ctis_plan_set_values": (I, [P, f32p]),
+        "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
+        "ctis_unrolled_nll_grad": (I, [P, VP, VP, I, VP, VP, VP, VP]),
         "ctis_status_string": (ctypes.c_char_p, [I]),
         "ctis_last_error": (ctypes.c_char_p, []),
     }
@@ -268,3 +272,53 @@ class Plan:
     def check(self, stream=None):
         """Synchronise the stream and raise if a kernel reported a device-side failure."""
         _check(load().ctis_plan_check(self._h, _stream(stream)))
+
+    # -- gradients ---------------------------------------------------------------
+    @property
+    def nnz(self) -> int:
+        return int(self.info()["nnz"])
+
+    def set_values(self, vals):
+        """Replace the stored tap values (``export_taps`` order; host array or
+        tensor of nnz float32, finite and >= 0) and recompute h."""
+        if hasattr(vals, "detach"):
+            import torch
+            vals = vals.detach().to("cpu", dtype=torch.float32).numpy()
+        v = np.ascontiguousarray(vals, dtype=np.float32).ravel()
+        if v.size != self.nnz:
+            raise ValueError(f"expected {self.nnz} tap values, got {v.size}")
+        keep, ptr = _arr(v, np.float32)
+        _check(load().ctis_plan_set_values(self._h, ptr))
+
+    def psf_grad(self, f, r, out=None, stream=None):
+        """``d <r, H f> / d v_t`` for every stored tap t (float32, nnz)."""
+        import torch
+        self._check_cube(f)
+        self._check_fpa(r)
+        if out is None:
+            out = torch.empty(self.nnz, device=r.device, dtype=torch.float32)
+        if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and
+                out.numel() == self.nnz):
+            raise ValueError("out must be a contiguous CUDA float32 tensor of nnz elements")
+        _check(load().ctis_psf_grad(self._h, ctypes.c_void_p(f.data_ptr()),
+                                    ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    _stream(stream)))
+        return out
+
+    def unrolled_nll_grad(self, g, k: int, f0=None, want_df0: bool = False, stream=None):
+        """Poisson NLL after k EM updates from f0 (or ones) and its gradients:
+        ``(nll float64 scalar tensor, dL/dv (nnz), dL/df0 or None)``."""
+        import torch
+        self._check_fpa(g)
+        if f0 is not None:
+            self._check_cube(f0, torch.float32)
+        nll = torch.empty(1, device=g.device, dtype=torch.float64)
+        dval = torch.empty(self.nnz, device=g.device, dtype=torch.float32)
+        df0 = (torch.empty((self.w, self.alpha, self.a), device=g.device, dtype=torch.float32)
+               if want_df0 else None)
+        _check(load().ctis_unrolled_nll_grad(
+            self._h, ctypes.c_void_p(g.data_ptr()),
+            ctypes.c_void_p(f0.data_ptr() if f0 is not None else 0), int(k),
+            ctypes.c_void_p(nll.data_ptr()), ctypes.c_void_p(dval.data_ptr()),
+            ctypes.c_void_p(df0.data_ptr() if df0 is not None else 0), _stream(stream)))
+        return nll[0], dval, df0

@@ -234,6 +234,53 @@ __device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const T
     }
 }
 
+// Per-lane sums for the PSF-value gradient of one staged window:
+// acc[dy*K + dx] += sum_{o,c} f[o][c] * win[o + dy][c + dx], with the lane's
+// datacube block held as pairs fp[o][c/2] = (f[o][c], f[o][c+1]). The same
+// sliding pass over the window as correlate(), with the lane's values in the
+// place of the weights; each pair sum is finished (x + y) by the caller.
+template <class G, typename TIn>
+__device__ __forceinline__ void correlate_grad(float2 (&acc)[G::K * G::K], const TIn* win,
+                                               const float2 (&fp)[G::R][G::C / 2]) {
+    constexpr int K = G::K, C = G::C, R = G::R, EPC = G::EPC;
+    constexpr int NE = C + K - 1;
+    constexpr int NCH = (NE + EPC - 1) / EPC;
+    constexpr int NP = NCH * EPC / 2;
+#pragma unroll
+    for (int i = 0; i < R + K - 1; ++i) {
+        const TIn* rowp = win + i * G::BXW;
+        float raw[NCH * EPC];
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) Elem<TIn>::load_chunk(rowp + q * EPC, raw + q * EPC);
+        float2 ev[NP], od[NP - 1];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
+#pragma unroll
+        for (int k = 0; k + 1 < NP; ++k) od[k] = make_float2(raw[2 * k + 1], raw[2 * k + 2]);
+#pragma unroll
+        for (int dx = 0; dx < K; ++dx) {
+#pragma unroll
+            for (int dy = 0; dy < K; ++dy) {
+                const int o = i - dy;
+                if (o >= 0 && o < R) {
+#pragma unroll
+                    for (int c2 = 0; c2 < C / 2; ++c2) {
+                        const float2 x2 = (dx & 1) ? od[c2 + dx / 2] : ev[c2 + dx / 2];
+                        acc[dy * K + dx] = __ffma2_rn(x2, fp[o][c2], acc[dy * K + dx]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Fixed-order float32 warp sum (same tree on every run); lane 0 gets the total.
+__device__ __forceinline__ float warp_sum_f(float d) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+    return d;
+}
+
 // ---------------------------------------------------------------------------
 // epilogues (per warp, straight from the lanes' register blocks)
 // ---------------------------------------------------------------------------
@@ -451,6 +498,8 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
                 // u = g / Hf on the support of Hf (Eq. 12); the fast quotient
                 // (within 2 ulp) is used for normal Hf, the IEEE one below
                 u[c] = val >= 1.17549435e-38f ? __fdividef(gv[c], val) : (val > 0.f ? gv[c] / val : 0.f);
+                // d/dq (q - g log q) = 1 - g / q on the support of q
+                if (p.ratio_one_minus) u[c] = val > 0.f ? 1.f - u[c] : 0.f;
             }
             if (p.with_stats) {   // uniform; selects instead of branches per element
 #pragma unroll
@@ -652,6 +701,25 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         for (int o = 0; o < G::R; ++o)
 #pragma unroll
             for (int c = 0; c < G::C / 2; ++c) acc[o][c] = make_float2(0.f, 0.f);
+        // kEpiGrad: this lane's block of the datacube plane, as pairs (zero
+        // outside the field stop)
+        float2 fp[G::R][G::C / 2];
+        if constexpr (MODE == kEpiGrad) {
+            const TF* fs = static_cast<const TF*>(p.f_in) + (long long)it.plane * p.out_w * p.out_h;
+#pragma unroll
+            for (int o = 0; o < G::R; ++o) {
+                const int y = it.y0 + ty * G::R + o;
+                float fv[G::C];
+#pragma unroll
+                for (int c = 0; c < G::C; ++c) {
+                    const int x = it.x0 + tx * G::C + c;
+                    fv[c] = (y < p.out_h && x < p.out_w) ? Elem<TF>::load(fs + (long long)y * p.out_w + x)
+                                                         : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < G::C / 2; ++c) fp[o][c] = make_float2(fv[2 * c], fv[2 * c + 1]);
+            }
+        }
 
         for (int t = it.task_begin; t < it.task_end; ++t) {
             if (!failed) {
@@ -666,10 +734,26 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                 const unsigned char* stage = my_stages + cons_stage * G::STAGE_BYTES;
                 using WP = typename Elem<TF>::WPair;
                 const WP* ws = reinterpret_cast<const WP*>(stage + G::WOFF);
-                float2 w2[G::K * G::K];
+                if constexpr (MODE == kEpiGrad) {
+                    const int cl = p.tasks[t].cluster;
+                    float2 gacc[G::K * G::K];
 #pragma unroll
-                for (int q = 0; q < G::K * G::K; ++q) w2[q] = Elem<TF>::weight_pair(ws[q]);
-                correlate<G, TIn>(acc, reinterpret_cast<const TIn*>(stage) + lane_off, w2);
+                    for (int q = 0; q < G::K * G::K; ++q) gacc[q] = make_float2(0.f, 0.f);
+                    correlate_grad<G, TIn>(gacc, reinterpret_cast<const TIn*>(stage) + lane_off, fp);
+                    float* dst = p.grad_part +
+                                 ((long long)cl * p.grad_tiles_per_plane +
+                                  (it.tile - it.plane * p.grad_tiles_per_plane)) * (G::K * G::K);
+#pragma unroll
+                    for (int q = 0; q < G::K * G::K; ++q) {
+                        const float sum = warp_sum_f(gacc[q].x + gacc[q].y);
+                        if (lane == 0) dst[q] = sum;
+                    }
+                } else {
+                    float2 w2[G::K * G::K];
+#pragma unroll
+                    for (int q = 0; q < G::K * G::K; ++q) w2[q] = Elem<TF>::weight_pair(ws[q]);
+                    correlate<G, TIn>(acc, reinterpret_cast<const TIn*>(stage) + lane_off, w2);
+                }
                 // after a failed wait the stage and phase stay at the copy
                 // that did not land, where the final drain resumes
                 --outstanding;
@@ -681,6 +765,8 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             __syncwarp();   // every lane is done with the stage before it is refilled
             issue_next();
         }
+
+        if constexpr (MODE == kEpiGrad) continue;   // every task wrote its own sums
 
         float v[G::R][G::C];
 #pragma unroll

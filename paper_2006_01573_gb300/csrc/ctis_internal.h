@@ -64,7 +64,9 @@ enum Epilogue : int {
     kEpiRaw = 0,     // out_f32 = value                      (ctis_forward / ctis_adjoint)
     kEpiRatio = 1,   // u copies = g / value, 0 where value == 0  (forward inside EM)
     kEpiUpdate = 2,  // f copies = f_in * value / h_s, 0 where h_s == 0 (adjoint inside EM)
-    kEpiSet = 3      // f copies = value in the plan's dtype  (H^T g initial guess)
+    kEpiSet = 3,     // f copies = value in the plan's dtype  (H^T g initial guess)
+    kEpiGrad = 4     // no output tile: per task, the K x K sums of f_s times the
+                     // task's input window (PSF-value gradient), into grad_part
 };
 
 struct GatherParams {
@@ -94,6 +96,13 @@ struct GatherParams {
     long long f_copy_stride;
     int f_copies;
     const float* h;            // [w]
+    // kEpiRatio: write 1 - g / value instead of g / value (0 where value == 0)
+    int ratio_one_minus;
+    // kEpiGrad: f_in is the dense datacube [w][alpha][a] (out_w = a,
+    // out_h = alpha); sums go to grad_part[(cluster * tiles_per_plane + tile
+    // of the plane) * K * K + dy * K + dx]
+    float* grad_part;
+    int grad_tiles_per_plane;
     // workspace
     float* scratch;            // partial tiles, [slots][TX*TY]
     int* tickets;              // [n_tiles], zero between launches

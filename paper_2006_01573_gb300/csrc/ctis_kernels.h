@@ -52,4 +52,33 @@ cudaError_t static_scratch_ptr(void** out);   // device address on the current d
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream);
 
+// ---- gradients (ctis_gather_grad.cu)
+// PSF-value gradient pass over the adjoint's work lists (mode kEpiGrad).
+cudaError_t psf_grad_prepare(int K, int dtype, int* blocks_per_sm);
+cudaError_t psf_grad_launch(int K, int dtype, const CUtensorMap& win, const GatherParams& p,
+                            cudaStream_t stream);
+// dval[t] (+)= sum over the plane's tiles of the partial sums of tap t, plus
+// extra[tap_s[t]] when extra is not null.
+cudaError_t launch_grad_reduce(float* dval, const float* part, const int* slot, const int* tap_s,
+                               const double* extra, int nnz, int kk, int tiles_per_plane,
+                               bool accumulate, cudaStream_t stream);
+// FPA values into the adjoint's x-shifted copies: mode 0 u = g / q, mode 1
+// gq = -gu * g / q^2 (0 where q == 0).
+cudaError_t launch_fpa_to_copies(float* copies, long long copy_stride, int ncopies, int pitch,
+                                 const float* q, const float* g, const float* gu, int width,
+                                 int height, int mode, cudaStream_t stream);
+// Vector-Jacobian product of f' = f * z / h_s: a = gb f / h_s (dense and into
+// the datacube copies), gfd = gb z / h_s, per-plane float64 partials of
+// gb f z; launch_dh_finish turns them into dL/dh_s.
+int voxel_vjp_blocks();
+cudaError_t launch_voxel_vjp(float* a_dense, float* a_copies, long long copy_stride, int ncopies,
+                             int pitch, long long plane_stride, float* gfd, double* part,
+                             const float* gb, const float* f, const float* z, const float* h,
+                             int a, int alpha, int w, cudaStream_t stream);
+cudaError_t launch_dh_finish(double* dh, const double* part, const float* h, int w,
+                             cudaStream_t stream);
+cudaError_t launch_add(float* out, const float* x, const float* y, long long n,
+                       cudaStream_t stream);
+cudaError_t launch_negate(double* out, const double* in, cudaStream_t stream);
+
 }  // namespace ctis

@@ -145,7 +145,17 @@ struct ctis_plan {
     std::vector<float> tap_v;   // stored values widened to float32
     std::vector<float> h;       // [w]
     std::vector<Cluster> clusters;
+    std::vector<int32_t> tap_slot;   // cluster * K*K + dy*K + dx of every stored tap
     ProjTables fwd, adj;
+    int adj_tiles_per_plane = 0;
+    int* d_tap_slot = nullptr;
+    int* d_tap_s = nullptr;
+    float* d_grad_part = nullptr;    // [clusters][adjoint tiles per plane][K*K]
+    // unrolled-EM gradient workspace (grown on demand)
+    int ck_steps = -1;               // checkpoints held: ck_steps + 1 iterates
+    float* d_ck = nullptr;
+    float* d_work = nullptr;         // q, gu (n each); z, gfd, gb, hq, a (m each)
+    double* d_gwork = nullptr;       // vjp partials [w][blocks], dh [w], stats [4]
     float* d_h = nullptr;
     float* d_u = nullptr;        // u_copies x-shifted copies of the FPA input of the adjoint
     void* d_fwork = nullptr;     // f_copies x-shifted copies of the datacube (forward input)
@@ -214,6 +224,12 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_tickets);
     cudaFree(P->d_counters);
     cudaFree(P->d_tile_stats);
+    cudaFree(P->d_tap_slot);
+    cudaFree(P->d_tap_s);
+    cudaFree(P->d_grad_part);
+    cudaFree(P->d_ck);
+    cudaFree(P->d_work);
+    cudaFree(P->d_gwork);
     cudaSetDevice(cur);
     delete P;
 }
@@ -331,6 +347,72 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
     T.tasks.swap(wt);
 }
 
+// h = H^T 1 (Eq. 2): under the on-FPA rule every voxel of wavelength s sees
+// all of that wavelength's taps, so h_s is the float64 sum of its stored
+// values, rounded once to float32.
+void compute_h(ctis_plan* P) {
+    std::vector<double> hs(P->w, 0.0);
+    for (size_t k = 0; k < P->tap_v.size(); ++k) hs[P->tap_s[k]] += static_cast<double>(P->tap_v[k]);
+    P->h.assign(P->w, 0.f);
+    for (int s = 0; s < P->w; ++s) P->h[s] = static_cast<float>(hs[s]);
+}
+
+// Device image of one projector's weight table: per cluster its K x K values
+// (adjoint orientation: [dy][dx] as on the FPA; forward: flipped, since the
+// forward applies the cluster as a convolution), each as a duplicated pair in
+// the storage type, padded to the kernel's 16-byte weight slot.
+std::vector<unsigned char> weight_table(const ctis_plan* P, bool forward) {
+    const int K = P->K, KK = K * K;
+    const int64_t ncl = static_cast<int64_t>(P->clusters.size());
+    std::vector<float> wts(static_cast<size_t>(ncl) * KK, 0.f);
+    for (size_t k = 0; k < P->tap_v.size(); ++k) {
+        const int64_t sl = P->tap_slot[k];
+        const int64_t c = sl / KK, e = sl % KK;
+        wts[c * KK + (forward ? KK - 1 - e : e)] = P->tap_v[k];
+    }
+    const int pad = gather_weight_pad(forward, K, P->dtype);
+    std::vector<unsigned char> out;
+    if (P->dtype == kDtypeBF16) {
+        std::vector<uint32_t> b(static_cast<size_t>(ncl) * pad, 0);
+        for (int64_t c = 0; c < ncl; ++c)
+            for (int e = 0; e < KK; ++e) {
+                const uint32_t h = to_bf16_bits(wts[c * KK + e]);
+                b[c * pad + e] = h | (h << 16);
+            }
+        out.resize(b.size() * sizeof(uint32_t));
+        std::memcpy(out.data(), b.data(), out.size());
+    } else {
+        std::vector<float> f(static_cast<size_t>(ncl) * pad * 2, 0.f);
+        for (int64_t c = 0; c < ncl; ++c)
+            for (int e = 0; e < KK; ++e) {
+                f[(c * pad + e) * 2] = wts[c * KK + e];
+                f[(c * pad + e) * 2 + 1] = wts[c * KK + e];
+            }
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    }
+    return out;
+}
+
+// Writes both weight tables and h to the device; allocates them the first time.
+int write_values(ctis_plan* P, bool allocate) {
+    for (ProjTables* T : {&P->fwd, &P->adj}) {
+        const std::vector<unsigned char> img = weight_table(P, T == &P->fwd);
+        if (allocate) {
+            int rc = dmalloc(P, &T->d_weights, img.size());
+            if (rc) return rc;
+        }
+        if (!img.empty())
+            CTIS_CUDA(cudaMemcpy(T->d_weights, img.data(), img.size(), cudaMemcpyHostToDevice));
+    }
+    if (allocate) {
+        int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_h), sizeof(float) * P->w);
+        if (rc) return rc;
+    }
+    CTIS_CUDA(cudaMemcpy(P->d_h, P->h.data(), sizeof(float) * P->w, cudaMemcpyHostToDevice));
+    return CTIS_OK;
+}
+
 // Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
 // every shifted copy of every nonzero must stay on the FPA).
 int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
@@ -392,12 +474,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     }
 
     // ---- h = H^T 1 per wavelength, float64 sum of the stored values
-    P->h.assign(w, 0.f);
-    {
-        std::vector<double> hs(w, 0.0);
-        for (int64_t k = 0; k < nnz; ++k) hs[P->tap_s[k]] += static_cast<double>(P->tap_v[k]);
-        for (int s = 0; s < w; ++s) P->h[s] = static_cast<float>(hs[s]);
-    }
+    compute_h(P);
 
     // ---- clusters: 8-connected components, covered by K x K boxes
     std::vector<int64_t> s_begin(w + 1, 0);
@@ -454,8 +531,12 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         if (x.y0 != y.y0) return x.y0 < y.y0;
         return x.x0 < y.x0;
     });
-    // Cover every component with K x K boxes and fill their weights.
-    std::vector<float> wts;          // adjoint orientation, [cluster][dy][dx], float32 values
+    // Cover every component with K x K boxes. Every tap belongs to the first
+    // box (in this order) that contains it, whatever its value: tap_slot[k] =
+    // box * K*K + dy*K + dx. Boxes of one wavelength may overlap where two
+    // components' bounding boxes do; a tap is never claimed twice.
+    const int KK = K * K;
+    P->tap_slot.assign(nnz, -1);
     for (int s = 0; s < w; ++s) {
         std::unordered_map<int64_t, int64_t> at;
         for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k)
@@ -464,83 +545,34 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
             if (b.s != s) continue;
             for (int by = b.y0; by <= b.y1; by += K)
                 for (int bx = b.x0; bx <= b.x1; bx += K) {
-                    std::vector<float> wk(static_cast<size_t>(K) * K, 0.f);
-                    bool any = false;
+                    std::vector<std::pair<int64_t, int>> mine;   // (tap, slot in the box)
                     for (int dy = 0; dy < K; ++dy)
                         for (int dx = 0; dx < K; ++dx) {
                             const int64_t x = bx + dx, y = by + dy;
                             if (x > b.x1 || y > b.y1) continue;
                             auto it = at.find(y * ga + x);
-                            if (it == at.end()) continue;
-                            wk[dy * K + dx] = P->tap_v[it->second];
-                            any = true;
+                            if (it == at.end() || P->tap_slot[it->second] >= 0) continue;
+                            mine.emplace_back(it->second, dy * K + dx);
                         }
-                    if (!any) continue;
+                    if (mine.empty()) continue;
+                    const int64_t c = static_cast<int64_t>(P->clusters.size());
                     P->clusters.push_back(Cluster{s, bx, by});
-                    wts.insert(wts.end(), wk.begin(), wk.end());
+                    for (const auto& te : mine) P->tap_slot[te.first] = c * KK + te.second;
                 }
         }
     }
-    // A box is filled from every tap of its wavelength inside it, so two boxes
-    // of one wavelength must never overlap: remove taps already claimed.
-    {
-        std::vector<char> claimed(nnz, 0);
-        std::vector<std::unordered_map<int64_t, int64_t>> at(w);
-        for (int64_t k = 0; k < nnz; ++k)
-            at[P->tap_s[k]][static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
-        for (size_t c = 0; c < P->clusters.size(); ++c) {
-            const Cluster& cl = P->clusters[c];
-            for (int dy = 0; dy < K; ++dy)
-                for (int dx = 0; dx < K; ++dx) {
-                    float& wv = wts[c * K * K + dy * K + dx];
-                    if (wv == 0.f) continue;
-                    auto it = at[cl.s].find(static_cast<int64_t>(cl.Y + dy) * ga + cl.X + dx);
-                    if (claimed[it->second]) wv = 0.f;   // owned by an earlier box
-                    claimed[it->second] = 1;
-                }
-        }
-        for (int64_t k = 0; k < nnz; ++k)
-            if (!claimed[k] && P->tap_v[k] != 0.f)
-                return fail(CTIS_ERR_INVALID_ARG, "internal: tap %lld not covered by a cluster",
-                            (long long)k);
-    }
+    for (int64_t k = 0; k < nnz; ++k)
+        if (P->tap_slot[k] < 0)
+            return fail(CTIS_ERR_INVALID_ARG, "internal: tap %lld not covered by a cluster",
+                        (long long)k);
     const int64_t ncl = static_cast<int64_t>(P->clusters.size());
-
-    // weights in the plan's storage type, both orientations
-    std::vector<float> wf(wts.size());
-    for (int64_t c = 0; c < ncl; ++c)
-        for (int e = 0; e < K * K; ++e) wf[c * K * K + e] = wts[c * K * K + (K * K - 1 - e)];
-    // weights of each cluster as duplicated pairs (w, w), padded to the
-    // kernel's 16-byte weight slot
-    auto store_weights = [&](ProjTables& T, bool forward, const std::vector<float>& src) -> int {
-        const int pad = gather_weight_pad(forward, K, P->dtype);
-        const size_t kk = static_cast<size_t>(K) * K;
-        if (P->dtype == kDtypeBF16) {
-            std::vector<uint32_t> b(static_cast<size_t>(ncl) * pad, 0);
-            for (int64_t c = 0; c < ncl; ++c)
-                for (size_t e = 0; e < kk; ++e) {
-                    const uint32_t h = to_bf16_bits(src[c * kk + e]);
-                    b[c * pad + e] = h | (h << 16);
-                }
-            uint32_t* d = nullptr;
-            int rc = upload(P, &d, b);
-            T.d_weights = d;
-            return rc;
-        }
-        std::vector<float> f(static_cast<size_t>(ncl) * pad * 2, 0.f);
-        for (int64_t c = 0; c < ncl; ++c)
-            for (size_t e = 0; e < kk; ++e) {
-                f[(c * pad + e) * 2] = src[c * kk + e];
-                f[(c * pad + e) * 2 + 1] = src[c * kk + e];
-            }
-        float* d = nullptr;
-        int rc = upload(P, &d, f);
-        T.d_weights = d;
-        return rc;
-    };
 
     CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
     CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
+    {
+        int grad_blocks = 0;   // runs on the adjoint's work lists and warp count
+        CTIS_CUDA(psf_grad_prepare(K, P->dtype, &grad_blocks));
+    }
     const int warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta(true);
     const int warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta(false);
 
@@ -584,8 +616,6 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                 begin.push_back(static_cast<int>(T.tasks.size()));
             }
         schedule(T, begin, warps_fwd, P->forced_per_item);
-        int rc = store_weights(T, true, wf);
-        if (rc) return rc;
     }
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
@@ -597,6 +627,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         for (int s = 0; s < w; ++s) c_begin[s + 1] += c_begin[s];
         std::vector<int> begin{0};
         const int ntx = (a + TX - 1) / TX, nty = (al + TY - 1) / TY;
+        P->adj_tiles_per_plane = ntx * nty;
         for (int s = 0; s < w; ++s)
             for (int ty = 0; ty < nty; ++ty)
                 for (int tx = 0; tx < ntx; ++tx) {
@@ -622,8 +653,6 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                     begin.push_back(static_cast<int>(T.tasks.size()));
                 }
         schedule(T, begin, warps_adj, P->forced_per_item);
-        int rc = store_weights(T, false, wts);
-        if (rc) return rc;
     }
 
     // ---- device buffers
@@ -633,7 +662,11 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         if (!rc) rc = upload(P, &T->d_witems, T->witems);
         if (rc) return rc;
     }
-    int rc = upload(P, &P->d_h, P->h);
+    int rc = write_values(P, true);
+    if (!rc) rc = upload(P, &P->d_tap_slot, P->tap_slot);
+    if (!rc) rc = upload(P, &P->d_tap_s, P->tap_s);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_grad_part),
+                          sizeof(float) * static_cast<size_t>(ncl) * P->adj_tiles_per_plane * K * K);
     if (rc) return rc;
     const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
     P->u_copy_stride = static_cast<int64_t>(P->g_pitch) * xi;
@@ -734,6 +767,31 @@ int enqueue_adjoint(const ctis_plan* P, GatherParams p, cudaStream_t st) {
                       gather_window_rows(false, P->K, P->dtype));
     if (rc) return rc;
     CTIS_CUDA(gather_launch(false, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
+// PSF-value gradient pass: the FPA input r already sits in the plan's FPA
+// copies; f_dense is a dense datacube of the plan's dtype. Writes (or adds
+// to) dval one value per stored tap, plus extra[s] for taps of wavelength s
+// when extra is given.
+int enqueue_psf_grad(const ctis_plan* P, const void* f_dense, float* dval, bool accumulate,
+                     const double* extra, cudaStream_t st) {
+    CUtensorMap win;
+    int rc = make_map(&win, P->d_u, kDtypeF32, P->gamma + P->u_copies - 1, P->xi, P->u_copies,
+                      P->g_pitch, P->u_copy_stride, gather_box_w(false, P->K, P->dtype),
+                      gather_window_rows(false, P->K, P->dtype));
+    if (rc) return rc;
+    GatherParams p = base_params(P, P->adj);
+    p.mode = kEpiGrad;
+    p.out_w = P->a;
+    p.out_h = P->alpha;
+    p.f_in = f_dense;
+    p.grad_part = P->d_grad_part;
+    p.grad_tiles_per_plane = P->adj_tiles_per_plane;
+    CTIS_CUDA(psf_grad_launch(P->K, P->dtype, win, p, st));
+    CTIS_CUDA(launch_grad_reduce(dval, P->d_grad_part, P->d_tap_slot, P->d_tap_s, extra,
+                                 static_cast<int>(P->tap_v.size()), P->K * P->K,
+                                 P->adj_tiles_per_plane, accumulate, st));
     return CTIS_OK;
 }
 
@@ -1181,6 +1239,167 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     p.out_pitch = P->gamma;
     p.out_plane_stride = 0;
     CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
+int ctis_plan_set_values(ctis_plan* P, const float* vals) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    const size_t nnz = P->tap_v.size();
+    if (!vals && nnz) return fail(CTIS_ERR_INVALID_ARG, "vals is NULL");
+    for (size_t k = 0; k < nnz; ++k)
+        if (!std::isfinite(vals[k]) || vals[k] < 0.f)
+            return fail(CTIS_ERR_INVALID_ARG, "vals[%zu] = %g is not finite and >= 0", k,
+                        (double)vals[k]);
+    // work already queued on any stream may still read the old tables
+    CTIS_CUDA(cudaDeviceSynchronize());
+    for (size_t k = 0; k < nnz; ++k)
+        P->tap_v[k] = P->dtype == kDtypeBF16 ? bf16_bits_to_float(to_bf16_bits(vals[k])) : vals[k];
+    compute_h(P);
+    return write_values(P, false);
+}
+
+int ctis_psf_grad(const ctis_plan* P, const void* f_dev, const float* r_dev, float* dval_dev,
+                  void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!f_dev || !r_dev || !dval_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = scatter_u(P, r_dev, st);
+    if (rc) return rc;
+    return enqueue_psf_grad(P, f_dev, dval_dev, false, nullptr, st);
+}
+
+int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev, int k,
+                           double* nll_dev, float* dval_dev, float* df0_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (P->dtype != kDtypeF32)
+        return fail(CTIS_ERR_UNSUPPORTED, "the unrolled EM gradient needs a float32 plan");
+    if (!g_dev || !nll_dev || !dval_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    if (k < 0 || k > 4096) return fail(CTIS_ERR_INVALID_ARG, "k must be in [0, 4096]");
+    const int64_t m = P->m, n = P->n;
+    const int a = P->a, al = P->alpha, w = P->w, ga = P->gamma, xi = P->xi;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // ---- workspace: k + 1 checkpoints of f, the dense vectors of a step
+    if (P->ck_steps < k) {
+        CTIS_CUDA(cudaStreamSynchronize(st));
+        cudaFree(P->d_ck);
+        P->d_ck = nullptr;
+        P->ck_steps = -1;
+        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_ck), sizeof(float) * m * (k + 1));
+        if (rc) return rc;
+        P->ck_steps = k;
+    }
+    const int vb = voxel_vjp_blocks();
+    if (!P->d_work) {
+        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_work), sizeof(float) * (2 * n + 5 * m));
+        if (!rc)
+            rc = dmalloc(P, reinterpret_cast<void**>(&P->d_gwork),
+                         sizeof(double) * (static_cast<size_t>(w) * vb + w + kNumStats));
+        if (rc) return rc;
+    }
+    float* q = P->d_work;
+    float* gu = q + n;
+    float* z = gu + n;
+    float* gfd = z + m;
+    float* gb = gfd + m;
+    float* hq = gb + m;
+    float* adense = hq + m;
+    double* vjp_part = P->d_gwork;
+    double* dh = vjp_part + static_cast<size_t>(w) * vb;
+    double* stats = dh + w;
+    auto ck = [&](int t) { return P->d_ck + static_cast<int64_t>(t) * m; };
+    const int64_t fplane = static_cast<int64_t>(P->a_pitch) * al;
+
+    auto copy_out = [&](float* dst) -> int {   // f copies (copy 0) -> dense
+        CTIS_CUDA(launch_gather_copy0(kDtypeF32, dst, P->d_fwork, P->a_pitch, fplane, a, al, w, st));
+        return CTIS_OK;
+    };
+    auto forward_raw = [&](float* out) -> int {
+        GatherParams p = base_params(P, P->fwd);
+        p.mode = kEpiRaw;
+        p.out_w = ga;
+        p.out_h = xi;
+        p.out_f32 = out;
+        p.out_pitch = ga;
+        return enqueue_forward(P, p, st);
+    };
+    auto adjoint_raw = [&](float* out) -> int {
+        GatherParams p = base_params(P, P->adj);
+        p.mode = kEpiRaw;
+        p.out_w = a;
+        p.out_h = al;
+        p.out_f32 = out;
+        p.out_pitch = a;
+        p.out_plane_stride = static_cast<long long>(a) * al;
+        return enqueue_adjoint(P, p, st);
+    };
+
+    // ---- k EM updates (Eq. 2) from f0 or ones, keeping every iterate
+    rc = f0_dev ? scatter_f(P, f0_dev, kDtypeF32, 0.f, st) : scatter_f(P, nullptr, kDtypeF32, 1.f, st);
+    if (rc) return rc;
+    GatherParams pf = base_params(P, P->fwd);
+    pf.mode = kEpiRatio;
+    pf.out_w = ga;
+    pf.out_h = xi;
+    pf.out_f32 = P->d_u;
+    pf.out_pitch = P->g_pitch;
+    pf.out_copy_stride = P->u_copy_stride;
+    pf.out_copies = P->u_copies;
+    pf.g = g_dev;
+    pf.g_pitch = ga;
+    GatherParams pa = base_params(P, P->adj);
+    pa.mode = kEpiUpdate;
+    pa.out_w = a;
+    pa.out_h = al;
+    set_f_copies(P, pa);
+    for (int t = 0; t < k; ++t) {
+        rc = copy_out(ck(t));
+        if (!rc) rc = enqueue_forward(P, pf, st);
+        if (!rc) rc = enqueue_adjoint(P, pa, st);
+        if (rc) return rc;
+    }
+    rc = copy_out(ck(k));
+    if (rc) return rc;
+
+    // ---- L = sum (q - g log q) over q = H f^(k) > 0; dL/dq = 1 - g/q there
+    GatherParams pl = pf;
+    pl.ratio_one_minus = 1;
+    pl.with_stats = 1;
+    pl.stats_out = stats;
+    rc = enqueue_forward(P, pl, st);             // 1 - g/q into the FPA copies
+    if (!rc) rc = adjoint_raw(gb);               // dL/df^(k) = H^T (1 - g/q)
+    if (!rc) rc = enqueue_psf_grad(P, ck(k), dval_dev, false, nullptr, st);
+    if (rc) return rc;
+    CTIS_CUDA(launch_negate(nll_dev, stats + CTIS_STAT_LOGLIK, st));
+
+    // ---- back through the updates f' = f * H^T(g / H f) / h, newest first
+    for (int t = k - 1; t >= 0; --t) {
+        rc = scatter_f(P, ck(t), kDtypeF32, 0.f, st);
+        if (!rc) rc = forward_raw(q);                                   // q = H f
+        if (rc) return rc;
+        CTIS_CUDA(launch_fpa_to_copies(P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch, q, g_dev,
+                                       nullptr, ga, xi, 0, st));       // u = g / q
+        rc = adjoint_raw(z);                                            // z = H^T u
+        if (rc) return rc;
+        CTIS_CUDA(launch_voxel_vjp(adense, static_cast<float*>(P->d_fwork), P->f_copy_stride,
+                                   P->f_copies, P->a_pitch, fplane, gfd, vjp_part, gb, ck(t), z,
+                                   P->d_h, a, al, w, st));             // a, gfd, dL/dh parts
+        CTIS_CUDA(launch_dh_finish(dh, vjp_part, P->d_h, w, st));
+        rc = forward_raw(gu);                                           // dL/du = H a
+        if (!rc) rc = enqueue_psf_grad(P, adense, dval_dev, true, nullptr, st);   // via H^T u
+        if (rc) return rc;
+        CTIS_CUDA(launch_fpa_to_copies(P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch, q, g_dev,
+                                       gu, ga, xi, 1, st));            // dL/dq = -gu g / q^2
+        rc = adjoint_raw(hq);                                           // H^T dL/dq
+        if (!rc) rc = enqueue_psf_grad(P, ck(t), dval_dev, true, dh, st);   // via H f, and h
+        if (rc) return rc;
+        CTIS_CUDA(launch_add(gb, gfd, hq, m, st));                      // dL/df
+    }
+    if (df0_dev)
+        CTIS_CUDA(cudaMemcpyAsync(df0_dev, gb, sizeof(float) * m, cudaMemcpyDeviceToDevice, st));
     return CTIS_OK;
 }
 
