@@ -188,6 +188,24 @@ int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, do
 int ctis_forward_static_scratch(const ctis_plan* plan, const void* f_dev, float* hf_dev,
                                 void* stream);
 
+/* k EM updates on many frames at once. Frame i is reconstructed with plan
+ * plans[plan_idx[i]] from g_dev[i] (n float32) into f_dev[i] (m elements of
+ * that plan's dtype; read as the initial guess unless an INIT flag is given),
+ * exactly as ctis_reconstruct would, with every frame's own statistics:
+ * stats_dev is NULL or device float64[nframes][k+1][CTIS_NSTATS] (frame
+ * order as given). Frames of one plan run as extra copies of its work lists,
+ * so each iteration is one forward and one adjoint launch per plan covering
+ * all of its frames; the whole call is one CUDA graph, cached for the next
+ * call with the same arguments (per-frame pointers included). A plan keeps
+ * the workspace of the last frame count it served (datacube and FPA copies,
+ * partial sums and statistics for every frame). Host arrays: plans[nplans]
+ * (distinct), plan_idx, g_dev and f_dev [nframes]; they may be freed when the
+ * call returns. */
+int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
+                             const int* plan_idx, const float* const* g_dev,
+                             void* const* f_dev, int k, int flags, double* stats_dev,
+                             void* stream);
+
 /* ---- gradients (the differentiable form of the projector pair) ----------
  * The PSF values are the parameters: tap t of wavelength s, at FPA offset
  * (x_t, y_t) for field-stop pixel (0, 0), adds v_t f_s(p, r) to pixel

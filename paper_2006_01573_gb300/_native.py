@@ -26,7 +26,7 @@ EXPORTED = (
     "ctis_plan_create", "ctis_plan_create_ex", "ctis_plan_destroy", "ctis_plan_get_info", "ctis_plan_export_taps",
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
-    "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad",
+    "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
         "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "ctis_plan_set_values": (I, [P, f32p]),
+        "ctis_reconstruct_batched": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
+                                         ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
         "ctis_unrolled_nll_grad": (I, [P, VP, VP, I, VP, VP, VP, VP]),
         "ctis_status_string": (ctypes.c_char_p, [I]),
@@ -322,3 +324,40 @@ class Plan:
             ctypes.c_void_p(nll.data_ptr()), ctypes.c_void_p(dval.data_ptr()),
             ctypes.c_void_p(df0.data_ptr() if df0 is not None else 0), _stream(stream)))
         return nll[0], dval, df0
+
+
+def reconstruct_batched(plans, plan_idx, gs, k: int, fs=None, init: str | None = "ones",
+                        stats=False, stream=None):
+    """k EM updates on every frame i: plan ``plans[plan_idx[i]]``, counts
+    ``gs[i]``, result in ``fs[i]`` (allocated when ``fs`` is None; read as the
+    initial guess when ``init`` is None). One CUDA graph for the whole batch.
+    Returns ``(fs, stats)`` with stats a ``(nframes, k+1, 4)`` float64 tensor
+    when requested."""
+    import torch
+    nframes = len(plan_idx)
+    if len(gs) != nframes:
+        raise ValueError("one g per frame")
+    if any(not 0 <= i < len(plans) for i in plan_idx):
+        raise ValueError("plan_idx out of range")
+    if fs is None:
+        if init is None:
+            raise ValueError("init=None needs initial fs")
+        fs = [torch.empty((plans[i].w, plans[i].alpha, plans[i].a), device=gs[n].device,
+                          dtype=plans[i]._f_dtype()) for n, i in enumerate(plan_idx)]
+    for n, i in enumerate(plan_idx):
+        plans[i]._check_fpa(gs[n])
+        plans[i]._check_cube(fs[n])
+    flags = {"ones": CTIS_INIT_ONES, "htg": CTIS_INIT_HTG, None: 0}[init]
+    st = None
+    if isinstance(stats, torch.Tensor):
+        st = stats
+    elif stats:
+        st = torch.empty((nframes, k + 1, NSTATS), device=gs[0].device, dtype=torch.float64)
+    hp = (ctypes.c_void_p * len(plans))(*[p._h for p in plans])
+    idx = (ctypes.c_int * nframes)(*plan_idx)
+    gp = (ctypes.c_void_p * nframes)(*[g.data_ptr() for g in gs])
+    fp = (ctypes.c_void_p * nframes)(*[f.data_ptr() for f in fs])
+    _check(load().ctis_reconstruct_batched(hp, len(plans), nframes, idx, gp, fp, int(k), flags,
+                                           ctypes.c_void_p(st.data_ptr() if st is not None else 0),
+                                           _stream(stream)))
+    return fs, st

@@ -58,6 +58,71 @@ __global__ void gather_copy0_kernel(T* dst, const T* src, int src_pitch, long lo
     }
 }
 
+// ---- frames of a batch (device arrays of per-frame pointers) -------------
+// dst[f * n + i] = srcs[f][i]
+__global__ void frames_gather_kernel(float* dst, const float* const* srcs, long long n, int frames) {
+    const long long total = n * frames;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = int(i / n);
+        dst[i] = srcs[f][i - (long long)f * n];
+    }
+}
+
+// x-shifted copies of every frame's datacube: plane f * planes + z of the copies
+// receives srcs[f][z] (dense width x height planes), or `value` when srcs is null.
+template <typename T>
+__global__ void frames_scatter_copies_kernel(T* dst, long long copy_stride, int ncopies, int dst_pitch,
+                                             long long dst_plane_stride, const T* const* srcs,
+                                             float value, int width, int height, int planes,
+                                             int frames) {
+    const long long per_frame = (long long)width * height * planes;
+    const long long total = per_frame * frames;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = int(i / per_frame);
+        const long long j = i - (long long)f * per_frame;
+        const int x = int(j % width);
+        const long long r = j / width;
+        const int y = int(r % height);
+        const long long z = r / height;
+        const float v = srcs ? Elem<T>::load(srcs[f] + j) : value;
+        T* d = dst + ((long long)f * planes + z) * dst_plane_stride + (long long)y * dst_pitch + x;
+        for (int q = 0; q < ncopies; ++q) Elem<T>::store(d + q * copy_stride + q, v);
+    }
+}
+
+// copy 0 of every frame's datacube back to its dense buffer dsts[f]
+template <typename T>
+__global__ void frames_copy0_out_kernel(T* const* dsts, const T* src, int src_pitch,
+                                        long long src_plane_stride, int width, int height,
+                                        int planes, int frames) {
+    const long long per_frame = (long long)width * height * planes;
+    const long long total = per_frame * frames;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = int(i / per_frame);
+        const long long j = i - (long long)f * per_frame;
+        const int x = int(j % width);
+        const long long r = j / width;
+        const int y = int(r % height);
+        const long long z = r / height;
+        dsts[f][j] = src[((long long)f * planes + z) * src_plane_stride + (long long)y * src_pitch + x];
+    }
+}
+
+// dst row gid[f] <- src row f (rows of `len` doubles)
+__global__ void rows_scatter_kernel(double* dst, const double* src, const int* gid, int len,
+                                    int frames) {
+    const long long total = (long long)len * frames;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = int(i / len);
+        const int e = int(i - (long long)f * len);
+        dst[(long long)gid[f] * len + e] = src[i];
+    }
+}
+
 // Sec. 3 embedding: datacube element j = (p, r, s) sits at FPA pixel
 // (x, y) = (p, r) of the s-th stacked FPA vector.
 __device__ __forceinline__ long long stacked_fpa_index(int p, int r, int s, int gamma, long long n) {
@@ -188,6 +253,48 @@ cudaError_t debug_arm(const void* const lo[6], const size_t bytes[6], unsigned l
     return e != cudaSuccess ? e : debug_arm_adj(r);
 }
 #endif
+
+cudaError_t launch_frames_gather(float* dst, const float* const* srcs, long long n, int frames,
+                                 cudaStream_t stream) {
+    frames_gather_kernel<<<2048, 256, 0, stream>>>(dst, srcs, n, frames);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frames_scatter_copies(int dtype, void* dst, long long copy_stride, int ncopies,
+                                         int dst_pitch, long long dst_plane_stride,
+                                         const void* const* srcs, float value, int width,
+                                         int height, int planes, int frames, cudaStream_t stream) {
+    if (dtype == kDtypeBF16)
+        frames_scatter_copies_kernel<__nv_bfloat16><<<2048, 256, 0, stream>>>(
+            static_cast<__nv_bfloat16*>(dst), copy_stride, ncopies, dst_pitch, dst_plane_stride,
+            reinterpret_cast<const __nv_bfloat16* const*>(srcs), value, width, height, planes,
+            frames);
+    else
+        frames_scatter_copies_kernel<float><<<2048, 256, 0, stream>>>(
+            static_cast<float*>(dst), copy_stride, ncopies, dst_pitch, dst_plane_stride,
+            reinterpret_cast<const float* const*>(srcs), value, width, height, planes, frames);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frames_copy0_out(int dtype, void* const* dsts, const void* src, int src_pitch,
+                                    long long src_plane_stride, int width, int height, int planes,
+                                    int frames, cudaStream_t stream) {
+    if (dtype == kDtypeBF16)
+        frames_copy0_out_kernel<__nv_bfloat16><<<2048, 256, 0, stream>>>(
+            reinterpret_cast<__nv_bfloat16* const*>(dsts), static_cast<const __nv_bfloat16*>(src),
+            src_pitch, src_plane_stride, width, height, planes, frames);
+    else
+        frames_copy0_out_kernel<float><<<2048, 256, 0, stream>>>(
+            reinterpret_cast<float* const*>(dsts), static_cast<const float*>(src), src_pitch,
+            src_plane_stride, width, height, planes, frames);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_scatter(double* dst, const double* src, const int* gid, int len, int frames,
+                                cudaStream_t stream) {
+    rows_scatter_kernel<<<256, 256, 0, stream>>>(dst, src, gid, len, frames);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream) {

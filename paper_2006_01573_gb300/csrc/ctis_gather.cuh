@@ -489,7 +489,8 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
             }
         } else if constexpr (MODE == kEpiRatio) {
             float gv[C], u[C];
-            const float* gp = p.g + (long long)(row_ok ? y : 0) * p.g_pitch + it.x0 + col0;
+            const float* gp = p.g + it.plane * p.g_plane_stride + (long long)(row_ok ? y : 0) * p.g_pitch +
+                              it.x0 + col0;
             load_row<float, C>(gp, row_ok ? n_valid : 0,
                                (p.g_pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(gp) & 15) == 0, gv);
 #pragma unroll
@@ -516,7 +517,8 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
             }
             // all lanes of the row take part in the shuffles; rows past the
             // plane store nothing
-            float* row = p.out_f32 + (long long)(row_ok ? y : 0) * p.out_pitch + it.x0;
+            float* row = p.out_f32 + it.plane * p.out_plane_stride +
+                         (long long)(row_ok ? y : 0) * p.out_pitch + it.x0;
             store_copies<float, C, G::LX>(row, p.out_copy_stride, p.out_copies, row_ok, tx,
                                           tile_cols, u);
         } else {   // kEpiUpdate, or kEpiSet when p.mode says so
@@ -549,7 +551,8 @@ __device__ __forceinline__ double warp_sum(double d) {
 // Statistics of one finished tile, reduced in a fixed two-level tree so that
 // no single warp walks all tiles: the warp that finishes the last tile of a
 // group of 32 tiles adds that group (one tile per lane), and the warp that
-// finishes the last group adds the groups into p.stats_out. Tile sums are
+// finishes the last group of a frame adds that frame's groups into its row
+// of p.stats_out. Tile sums are
 // per-lane float32 sums of 32 elements widened to float64; everything above
 // them is float64 in a fixed order, so the result is reproducible.
 __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumStats]) {
@@ -561,14 +564,19 @@ __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumSt
 __device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx,
                                              const float (&stat)[kNumStats], int lane) {
     static_assert(kNumStats == 4, "statistics move as two double2");
-    const int n_groups = (p.n_tiles + kStatGroup - 1) / kStatGroup;
+    // tiles are numbered frame by frame; every frame has its own tree
+    const int tpf = p.stat_tiles_per_frame;
+    const int gpf = (tpf + kStatGroup - 1) / kStatGroup;   // groups per frame
+    const int frame = tile_idx / tpf;
+    const int local = tile_idx - frame * tpf;
     double* group_stats = p.tile_stats + (long long)p.n_tiles * kNumStats;
     int* group_tickets = p.tickets + p.n_tiles;
     double tot[kNumStats];
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) tot[q] = warp_sum(static_cast<double>(stat[q]));
-    const int group = tile_idx / kStatGroup;
-    const int in_group = min(kStatGroup, p.n_tiles - group * kStatGroup);
+    const int lgroup = local / kStatGroup;
+    const int group = frame * gpf + lgroup;
+    const int in_group = min(kStatGroup, tpf - lgroup * kStatGroup);
     int last = 0;
     if (lane == 0) {
         double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
@@ -582,7 +590,7 @@ __device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx
     __threadfence();
     double d[kNumStats] = {0.0, 0.0, 0.0, 0.0};
     if (lane < in_group)
-        load_stats(p.tile_stats + (long long)(group * kStatGroup + lane) * kNumStats, d);
+        load_stats(p.tile_stats + (long long)(frame * tpf + lgroup * kStatGroup + lane) * kNumStats, d);
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) d[q] = warp_sum(d[q]);
     last = 0;
@@ -592,24 +600,26 @@ __device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx
         __stcg(dst + 1, make_double2(d[2], d[3]));
         group_tickets[group] = 0;
         __threadfence();
-        last = atomicAdd(&p.counters[2], 1) == n_groups - 1;
+        last = atomicAdd(&p.stat_frame_done[frame], 1) == gpf - 1;
     }
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
     double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-    for (int g0 = 0; g0 < n_groups; g0 += 32) {   // all loads of a pass in flight at once
+    for (int g0 = 0; g0 < gpf; g0 += 32) {   // all loads of a pass in flight at once
         double e[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-        if (g0 + lane < n_groups) load_stats(group_stats + (long long)(g0 + lane) * kNumStats, e);
+        if (g0 + lane < gpf)
+            load_stats(group_stats + (long long)(frame * gpf + g0 + lane) * kNumStats, e);
 #pragma unroll
         for (int q = 0; q < kNumStats; ++q) t[q] += e[q];
     }
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) t[q] = warp_sum(t[q]);
     if (lane == 0) {
+        double* out = p.stats_out + frame * p.stats_frame_stride;
 #pragma unroll
-        for (int q = 0; q < kNumStats; ++q) p.stats_out[q] = t[q];
-        p.counters[2] = 0;
+        for (int q = 0; q < kNumStats; ++q) out[q] = t[q];
+        p.stat_frame_done[frame] = 0;
     }
 }
 
@@ -686,7 +696,8 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                     if (y < p.out_h && x < p.out_w) {
                         const void* src =
                             MODE == kEpiRatio
-                                ? static_cast<const void*>(p.g + (long long)y * p.g_pitch + x)
+                                ? static_cast<const void*>(p.g + it.plane * p.g_plane_stride +
+                                                           (long long)y * p.g_pitch + x)
                                 : static_cast<const void*>(static_cast<const TF*>(p.f_in) +
                                                            it.plane * p.f_plane_stride +
                                                            (long long)y * p.f_pitch + x);

@@ -81,13 +81,19 @@ struct GatherParams {
     int with_stats;
     // kEpiRaw output, or the kEpiRatio u copies (float32)
     float* out_f32;
-    long long out_plane_stride;
+    long long out_plane_stride;  // kEpiRaw: between output planes; kEpiRatio: between frames
     int out_pitch;
     long long out_copy_stride;   // kEpiRatio: elements between u copies
     int out_copies;              // kEpiRatio: number of u copies
-    // kEpiRatio
+    // kEpiRatio (item plane = frame of a batch, 0 otherwise)
     const float* g;
     int g_pitch;
+    long long g_plane_stride;    // elements between frames of g
+    // statistics tree: tiles per frame, per-frame count of finished groups,
+    // elements between the frames' statistics rows
+    int stat_tiles_per_frame;
+    int* stat_frame_done;
+    long long stats_frame_stride;
     // kEpiUpdate / kEpiSet (datacube copies in the plan's dtype; f_in = copy 0)
     const void* f_in;
     void* f_out;

@@ -52,6 +52,24 @@ cudaError_t static_scratch_ptr(void** out);   // device address on the current d
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream);
 
+// ---- frames of a batch (srcs / dsts: device arrays of per-frame pointers)
+// dst[f * n + i] = srcs[f][i]
+cudaError_t launch_frames_gather(float* dst, const float* const* srcs, long long n, int frames,
+                                 cudaStream_t stream);
+// x-shifted copies of the frames' datacubes (frame f, plane z -> copies'
+// plane f * planes + z), from srcs (plan dtype) or the constant `value`
+cudaError_t launch_frames_scatter_copies(int dtype, void* dst, long long copy_stride, int ncopies,
+                                         int dst_pitch, long long dst_plane_stride,
+                                         const void* const* srcs, float value, int width,
+                                         int height, int planes, int frames, cudaStream_t stream);
+// copy 0 of the frames' datacubes back to dense per-frame buffers
+cudaError_t launch_frames_copy0_out(int dtype, void* const* dsts, const void* src, int src_pitch,
+                                    long long src_plane_stride, int width, int height, int planes,
+                                    int frames, cudaStream_t stream);
+// dst row gid[f] <- src row f (rows of len doubles)
+cudaError_t launch_rows_scatter(double* dst, const double* src, const int* gid, int len, int frames,
+                                cudaStream_t stream);
+
 // ---- gradients (ctis_gather_grad.cu)
 // PSF-value gradient pass over the adjoint's work lists (mode kEpiGrad).
 cudaError_t psf_grad_prepare(int K, int dtype, int* blocks_per_sm);

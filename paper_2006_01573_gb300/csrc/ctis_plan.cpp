@@ -132,6 +132,12 @@ struct GraphKey {
 
 }  // namespace
 
+namespace {
+struct BatchState;
+void free_batch(BatchState* B);
+void drop_batched_graph_of(const ctis_plan* P);
+}  // namespace
+
 struct ctis_plan {
     int a = 0, alpha = 0, w = 0, gamma = 0, xi = 0, dtype = 0;
     int64_t m = 0, n = 0;
@@ -156,6 +162,7 @@ struct ctis_plan {
     float* d_ck = nullptr;
     float* d_work = nullptr;         // q, gu (n each); z, gfd, gb, hq, a (m each)
     double* d_gwork = nullptr;       // vjp partials [w][blocks], dh [w], stats [4]
+    BatchState* batch = nullptr;     // frames of ctis_reconstruct_batched (grown on demand)
     float* d_h = nullptr;
     float* d_u = nullptr;        // u_copies x-shifted copies of the FPA input of the adjoint
     void* d_fwork = nullptr;     // f_copies x-shifted copies of the datacube (forward input)
@@ -212,6 +219,8 @@ void destroy(ctis_plan* P) {
     cudaGetDevice(&cur);
     cudaSetDevice(P->device);
     cudaDeviceSynchronize();
+    drop_batched_graph_of(P);
+    free_batch(P->batch);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
@@ -744,6 +753,8 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.counters = P->d_counters;
     p.tile_stats = P->d_tile_stats;
     p.h = P->d_h;
+    p.stat_tiles_per_frame = p.n_tiles;
+    p.stat_frame_done = P->d_counters + 2;
     return p;
 }
 
@@ -898,6 +909,328 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
                                   static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
                                   P->w, st));
     return CTIS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches of frames (ctis_reconstruct_batched)
+// ---------------------------------------------------------------------------
+// F frames of one plan's geometry run as F more copies of its work lists, so
+// one launch per projector covers them all: every warp keeps its item list
+// and runs it once per frame. Frame f's datacube planes are planes f*w + s of
+// the copies, its FPA rows are rows f*xi + y of a tall FPA, and its tiles are
+// tiles f*T + t, each frame with its own partial-sum slots and statistics.
+struct BatchTables {
+    WorkItem* d_witems = nullptr;
+    TaskDesc* d_tasks = nullptr;
+    int* d_warp_begin = nullptr;
+    int n_warps = 0;
+    int n_tiles = 0;
+};
+
+struct BatchState {
+    int F = 0;
+    BatchTables fwd, adj;
+    void* d_fwork = nullptr;       // datacube copies, planes f*w + s
+    float* d_u = nullptr;          // FPA copies, rows f*xi + y
+    float* d_scratch = nullptr;
+    int* d_tickets = nullptr;
+    int* d_counters = nullptr;     // [8] as the plan's, then [F] statistics groups done
+    double* d_tile_stats = nullptr;
+    float* d_h = nullptr;          // h for every plane f*w + s
+    float* d_g = nullptr;          // the frames' g, contiguous
+    void** d_ptrs = nullptr;       // [F] g pointers, [F] f pointers
+    int* d_gid = nullptr;          // [F] position of each frame in the caller's order
+    double* d_stats = nullptr;     // [F][k+1][4]
+    int stats_rows = 0;
+    int64_t f_copy_stride = 0, u_copy_stride = 0;
+};
+
+void free_tables(BatchTables& t) {
+    cudaFree(t.d_witems);
+    cudaFree(t.d_tasks);
+    cudaFree(t.d_warp_begin);
+    t = BatchTables{};
+}
+
+void free_batch(BatchState* B) {
+    if (!B) return;
+    free_tables(B->fwd);
+    free_tables(B->adj);
+    cudaFree(B->d_fwork);
+    cudaFree(B->d_u);
+    cudaFree(B->d_scratch);
+    cudaFree(B->d_tickets);
+    cudaFree(B->d_counters);
+    cudaFree(B->d_tile_stats);
+    cudaFree(B->d_h);
+    cudaFree(B->d_g);
+    cudaFree(B->d_ptrs);
+    cudaFree(B->d_gid);
+    cudaFree(B->d_stats);
+    delete B;
+}
+
+// The plan's work lists repeated for F frames, warp by warp (each warp keeps
+// its items and runs them once per frame; its tasks stay contiguous).
+int replicate(ctis_plan* P, const ProjTables& T, bool forward, int F, BatchTables& B) {
+    std::vector<WorkItem> wi;
+    std::vector<TaskDesc> wt;
+    std::vector<int> wb{0};
+    wi.reserve(T.witems.size() * F);
+    wt.reserve(T.tasks.size() * F);
+    const int ntiles = static_cast<int>(T.tiles.size());
+    for (int wp = 0; wp < T.n_warps; ++wp) {
+        for (int f = 0; f < F; ++f)
+            for (int i = T.warp_begin[wp]; i < T.warp_begin[wp + 1]; ++i) {
+                WorkItem it = T.witems[i];
+                const int tb = static_cast<int>(wt.size());
+                for (int t = it.task_begin; t < it.task_end; ++t) {
+                    TaskDesc d = T.tasks[t];
+                    if (forward) {   // copies' plane q*w + s -> q*(F*w) + f*w + s
+                        const int q = d.plane / P->w, sw = d.plane % P->w;
+                        d.plane = q * (F * P->w) + f * P->w + sw;
+                    } else {         // window rows of frame f on the tall FPA
+                        d.wy += f * P->xi;
+                    }
+                    wt.push_back(d);
+                }
+                it.task_begin = tb;
+                it.task_end = static_cast<int>(wt.size());
+                it.tile += f * ntiles;
+                it.scratch_base += static_cast<int>(f * T.scratch_slots);
+                it.plane = forward ? f : f * P->w + it.plane;
+                wi.push_back(it);
+            }
+        wb.push_back(static_cast<int>(wi.size()));
+    }
+    if (static_cast<int64_t>(wt.size()) > (int64_t{1} << 31) - 1)
+        return fail(CTIS_ERR_UNSUPPORTED, "too many frames for one batch");
+    B.n_warps = T.n_warps;
+    B.n_tiles = ntiles * F;
+    int rc = upload(P, &B.d_witems, wi);
+    if (!rc) rc = upload(P, &B.d_tasks, wt);
+    if (!rc) rc = upload(P, &B.d_warp_begin, wb);
+    return rc;
+}
+
+// Makes P->batch hold exactly F frames (and statistics rows for k).
+int ensure_batch(ctis_plan* P, int F, int k) {
+    BatchState* B = P->batch;
+    if (B && B->F == F) {
+        if (B->stats_rows < k + 1) {
+            cudaFree(B->d_stats);
+            B->d_stats = nullptr;
+            B->stats_rows = 0;
+            int rc = dmalloc(P, reinterpret_cast<void**>(&B->d_stats),
+                             sizeof(double) * kNumStats * static_cast<size_t>(F) * (k + 1));
+            if (rc) return rc;
+            B->stats_rows = k + 1;
+        }
+        return CTIS_OK;
+    }
+    CTIS_CUDA(cudaDeviceSynchronize());
+    drop_batched_graph_of(P);
+    free_batch(P->batch);
+    P->batch = nullptr;
+    B = new (std::nothrow) BatchState();
+    if (!B) return fail(CTIS_ERR_NOMEM, "host allocation failed");
+    P->batch = B;
+    B->F = F;
+    int rc = replicate(P, P->fwd, true, F, B->fwd);
+    if (!rc) rc = replicate(P, P->adj, false, F, B->adj);
+    if (rc) return rc;
+    const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
+    B->f_copy_stride = static_cast<int64_t>(P->a_pitch) * P->alpha * P->w * F;
+    B->u_copy_stride = static_cast<int64_t>(P->g_pitch) * P->xi * F;
+    const size_t fbytes = es * static_cast<size_t>(B->f_copy_stride) * P->f_copies;
+    const size_t ubytes = sizeof(float) * static_cast<size_t>(B->u_copy_stride) * P->u_copies;
+    const int64_t scratch = std::max(P->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
+                                     P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
+    const size_t tpf = P->fwd.tiles.size();
+    const size_t gpf = (tpf + kStatGroup - 1) / kStatGroup;
+    const size_t ntick = std::max((tpf + gpf) * F, P->adj.tiles.size() * F);
+    rc = dmalloc(P, &B->d_fwork, fbytes);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_u), ubytes);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_scratch),
+                          sizeof(float) * static_cast<size_t>(scratch) * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tickets), sizeof(int) * ntick);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_counters), sizeof(int) * (8 + F));
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tile_stats),
+                          sizeof(double) * kNumStats * (tpf + gpf) * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_h), sizeof(float) * P->w * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_g), sizeof(float) * P->n * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_ptrs), sizeof(void*) * 2 * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_gid), sizeof(int) * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_stats),
+                          sizeof(double) * kNumStats * static_cast<size_t>(F) * (k + 1));
+    if (rc) return rc;
+    B->stats_rows = k + 1;
+    CTIS_CUDA(cudaMemset(B->d_fwork, 0, fbytes));
+    CTIS_CUDA(cudaMemset(B->d_u, 0, ubytes));
+    CTIS_CUDA(cudaMemset(B->d_tickets, 0, sizeof(int) * ntick));
+    CTIS_CUDA(cudaMemset(B->d_counters, 0, sizeof(int) * (8 + F)));
+    std::vector<float> hx(static_cast<size_t>(P->w) * F);
+    for (int f = 0; f < F; ++f) std::copy(P->h.begin(), P->h.end(), hx.begin() + f * P->w);
+    CTIS_CUDA(cudaMemcpy(B->d_h, hx.data(), sizeof(float) * hx.size(), cudaMemcpyHostToDevice));
+    return CTIS_OK;
+}
+
+GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward) {
+    const ProjTables& T = forward ? P->fwd : P->adj;
+    const BatchTables& BT = forward ? B->fwd : B->adj;
+    GatherParams p{};
+    p.items = BT.d_witems;
+    p.warp_begin = BT.d_warp_begin;
+    p.tasks = BT.d_tasks;
+    p.weights = T.d_weights;
+    p.n_warps = BT.n_warps;
+    p.n_tiles = BT.n_tiles;
+    p.scratch = B->d_scratch;
+    p.tickets = B->d_tickets;
+    p.counters = B->d_counters;
+    p.tile_stats = B->d_tile_stats;
+    p.h = B->d_h;
+    p.stat_tiles_per_frame = static_cast<int>(T.tiles.size());
+    p.stat_frame_done = B->d_counters + 8;
+    return p;
+}
+
+int batch_forward(const ctis_plan* P, const BatchState* B, GatherParams p, cudaStream_t st) {
+    CUtensorMap win;
+    const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
+    int rc = make_map(&win, B->d_fwork, P->dtype, P->a + P->f_copies - 1, P->alpha,
+                      P->w * B->F * P->f_copies, P->a_pitch, plane,
+                      gather_box_w(true, P->K, P->dtype), gather_window_rows(true, P->K, P->dtype));
+    if (rc) return rc;
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
+int batch_adjoint(const ctis_plan* P, const BatchState* B, GatherParams p, cudaStream_t st) {
+    CUtensorMap win;
+    int rc = make_map(&win, B->d_u, kDtypeF32, P->gamma + P->u_copies - 1, P->xi * B->F,
+                      P->u_copies, P->g_pitch, B->u_copy_stride,
+                      gather_box_w(false, P->K, P->dtype), gather_window_rows(false, P->K, P->dtype));
+    if (rc) return rc;
+    CTIS_CUDA(gather_launch(false, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
+// One plan's part of a batched reconstruction, as separate phases so that the
+// caller can interleave the plans: setup (g, initial f), iteration it, finish.
+struct BatchRun {
+    ctis_plan* P;
+    BatchState* B;
+    GatherParams pf, pa;
+    bool stats;
+};
+
+int batch_setup(BatchRun& r, int flags, cudaStream_t st) {
+    ctis_plan* P = r.P;
+    BatchState* B = r.B;
+    const int F = B->F;
+    const float* const* gptrs = reinterpret_cast<const float* const*>(B->d_ptrs);
+    void* const* fptrs = B->d_ptrs + F;
+    CTIS_CUDA(launch_frames_gather(B->d_g, gptrs, P->n, F, st));
+    const int64_t fplane = static_cast<int64_t>(P->a_pitch) * P->alpha;
+    if (flags & CTIS_INIT_HTG) {
+        // the frames' g into the tall FPA copies, then f = H^T g per frame
+        CTIS_CUDA(launch_scatter_copies(kDtypeF32, B->d_u, B->u_copy_stride, P->u_copies,
+                                        P->g_pitch, static_cast<int64_t>(P->g_pitch) * P->xi,
+                                        B->d_g, kDtypeF32, P->gamma, P->n, P->gamma, P->xi, F,
+                                        0.f, st));
+        GatherParams p = batch_params(P, B, false);
+        p.mode = kEpiSet;
+        p.out_w = P->a;
+        p.out_h = P->alpha;
+        p.f_in = B->d_fwork;
+        p.f_out = B->d_fwork;
+        p.f_pitch = P->a_pitch;
+        p.f_plane_stride = fplane;
+        p.f_copy_stride = B->f_copy_stride;
+        p.f_copies = P->f_copies;
+        int rc = batch_adjoint(P, B, p, st);
+        if (rc) return rc;
+    } else {
+        CTIS_CUDA(launch_frames_scatter_copies(
+            P->dtype, B->d_fwork, B->f_copy_stride, P->f_copies, P->a_pitch, fplane,
+            (flags & CTIS_INIT_ONES) ? nullptr : const_cast<const void* const*>(fptrs), 1.0f,
+            P->a, P->alpha, P->w, F, st));
+    }
+    GatherParams& pf = r.pf;
+    pf = batch_params(P, B, true);
+    pf.mode = kEpiRatio;
+    pf.out_w = P->gamma;
+    pf.out_h = P->xi;
+    pf.out_f32 = B->d_u;
+    pf.out_pitch = P->g_pitch;
+    pf.out_plane_stride = static_cast<long long>(P->g_pitch) * P->xi;   // between frames
+    pf.out_copy_stride = B->u_copy_stride;
+    pf.out_copies = P->u_copies;
+    pf.g = B->d_g;
+    pf.g_pitch = P->gamma;
+    pf.g_plane_stride = P->n;
+    GatherParams& pa = r.pa;
+    pa = batch_params(P, B, false);
+    pa.mode = kEpiUpdate;
+    pa.out_w = P->a;
+    pa.out_h = P->alpha;
+    pa.f_in = B->d_fwork;
+    pa.f_out = B->d_fwork;
+    pa.f_pitch = P->a_pitch;
+    pa.f_plane_stride = fplane;
+    pa.f_copy_stride = B->f_copy_stride;
+    pa.f_copies = P->f_copies;
+    return CTIS_OK;
+}
+
+int batch_forward_step(BatchRun& r, int it, int k, cudaStream_t st) {
+    GatherParams p = r.pf;
+    p.with_stats = r.stats ? 1 : 0;
+    p.stats_out = r.stats ? r.B->d_stats + static_cast<int64_t>(it) * kNumStats : nullptr;
+    p.stats_frame_stride = static_cast<long long>(k + 1) * kNumStats;
+    return batch_forward(r.P, r.B, p, st);
+}
+
+int batch_finish(BatchRun& r, int k, double* stats_dev, cudaStream_t st) {
+    ctis_plan* P = r.P;
+    BatchState* B = r.B;
+    CTIS_CUDA(launch_frames_copy0_out(P->dtype, B->d_ptrs + B->F, B->d_fwork, P->a_pitch,
+                                      static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
+                                      P->w, B->F, st));
+    if (r.stats)
+        CTIS_CUDA(launch_rows_scatter(stats_dev, B->d_stats, B->d_gid, (k + 1) * kNumStats, B->F, st));
+    return CTIS_OK;
+}
+
+// The cached graph of the last batched call (one entry, keyed by every input).
+struct BatchedKey {
+    std::vector<const ctis_plan*> plans;
+    std::vector<int> plan_idx;
+    std::vector<const void*> g, f;
+    int k = -1, flags = 0;
+    const void* stats = nullptr;
+    bool operator==(const BatchedKey& o) const {
+        return plans == o.plans && plan_idx == o.plan_idx && g == o.g && f == o.f && k == o.k &&
+               flags == o.flags && stats == o.stats;
+    }
+};
+std::mutex g_batched_mu;
+BatchedKey g_batched_key;
+cudaGraphExec_t g_batched_exec = nullptr;
+cudaStream_t g_batched_stream = nullptr;
+int g_batched_device = -1;
+
+void drop_batched_graph_of(const ctis_plan* P) {
+    std::lock_guard<std::mutex> lock(g_batched_mu);
+    if (!g_batched_exec) return;
+    for (const ctis_plan* q : g_batched_key.plans)
+        if (q == P) {
+            cudaGraphExecDestroy(g_batched_exec);
+            g_batched_exec = nullptr;
+            g_batched_key = BatchedKey{};
+            return;
+        }
 }
 
 }  // namespace
@@ -1403,12 +1736,127 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     return CTIS_OK;
 }
 
+int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
+                             const int* plan_idx, const float* const* g_dev, void* const* f_dev,
+                             int k, int flags, double* stats_dev, void* stream) {
+    if (!plans || nplans < 1 || nframes < 1 || !plan_idx || !g_dev || !f_dev)
+        return fail(CTIS_ERR_INVALID_ARG, "NULL array or empty batch");
+    if (k < 0) return fail(CTIS_ERR_INVALID_ARG, "k must be >= 0");
+    if (flags & ~(CTIS_INIT_ONES | CTIS_INIT_HTG) ||
+        (flags & CTIS_INIT_ONES && flags & CTIS_INIT_HTG))
+        return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    for (int p = 0; p < nplans; ++p) {
+        int rc = check_plan(plans[p]);
+        if (rc) return rc;
+        for (int q = 0; q < p; ++q)
+            if (plans[q] == plans[p])
+                return fail(CTIS_ERR_INVALID_ARG, "plan %d appears twice in plans[]", p);
+    }
+    std::vector<std::vector<int>> frames(nplans);
+    for (int i = 0; i < nframes; ++i) {
+        if (plan_idx[i] < 0 || plan_idx[i] >= nplans)
+            return fail(CTIS_ERR_INVALID_ARG, "plan_idx[%d] = %d out of range", i, plan_idx[i]);
+        if (!g_dev[i] || !f_dev[i])
+            return fail(CTIS_ERR_INVALID_ARG, "frame %d has a NULL pointer", i);
+        frames[plan_idx[i]].push_back(i);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int> used;
+    for (int p = 0; p < nplans; ++p) {
+        if (frames[p].empty()) continue;
+        int rc = ensure_batch(plans[p], static_cast<int>(frames[p].size()), k);
+        if (rc) return rc;
+        used.push_back(p);
+    }
+    // per-frame pointers and caller positions, ordered on the stream
+    for (int p : used) {
+        BatchState* B = plans[p]->batch;
+        const int F = B->F;
+        std::vector<const void*> ptrs(2 * F);
+        std::vector<int> gid(F);
+        for (int j = 0; j < F; ++j) {
+            ptrs[j] = g_dev[frames[p][j]];
+            ptrs[F + j] = f_dev[frames[p][j]];
+            gid[j] = frames[p][j];
+        }
+        CTIS_CUDA(cudaMemcpyAsync(B->d_ptrs, ptrs.data(), sizeof(void*) * 2 * F,
+                                  cudaMemcpyHostToDevice, st));
+        CTIS_CUDA(cudaMemcpyAsync(B->d_gid, gid.data(), sizeof(int) * F, cudaMemcpyHostToDevice, st));
+    }
+
+    BatchedKey key;
+    key.plans.assign(plans, plans + nplans);
+    key.plan_idx.assign(plan_idx, plan_idx + nframes);
+    key.g.assign(g_dev, g_dev + nframes);
+    key.f.assign(f_dev, f_dev + nframes);
+    key.k = k;
+    key.flags = flags;
+    key.stats = stats_dev;
+    std::lock_guard<std::mutex> lock(g_batched_mu);
+    int dev = 0;
+    CTIS_CUDA(cudaGetDevice(&dev));
+    if (!(g_batched_exec && g_batched_key == key && g_batched_device == dev)) {
+        if (g_batched_exec) {
+            cudaGraphExecDestroy(g_batched_exec);
+            g_batched_exec = nullptr;
+            g_batched_key = BatchedKey{};
+        }
+        if (g_batched_stream && g_batched_device != dev) {
+            cudaStreamDestroy(g_batched_stream);
+            g_batched_stream = nullptr;
+        }
+        if (!g_batched_stream) {
+            CTIS_CUDA(cudaStreamCreateWithFlags(&g_batched_stream, cudaStreamNonBlocking));
+            g_batched_device = dev;
+        }
+        cudaStream_t cs = g_batched_stream;
+        std::vector<BatchRun> runs;
+        for (int p : used) runs.push_back(BatchRun{plans[p], plans[p]->batch, {}, {}, stats_dev != nullptr});
+        CTIS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = CTIS_OK;
+        for (BatchRun& r : runs)
+            if (!rc) rc = batch_setup(r, flags, cs);
+        for (int it = 0; it <= k && !rc; ++it) {
+            if (it == k && !stats_dev) break;
+            for (BatchRun& r : runs)
+                if (!rc) rc = batch_forward_step(r, it, k, cs);
+            if (it == k) break;
+            for (BatchRun& r : runs)
+                if (!rc) rc = batch_adjoint(r.P, r.B, r.pa, cs);
+        }
+        for (BatchRun& r : runs)
+            if (!rc) rc = batch_finish(r, k, stats_dev, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g_batched_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g_batched_exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        g_batched_key = key;
+    }
+    CTIS_CUDA(cudaGraphLaunch(g_batched_exec, st));
+    return CTIS_OK;
+}
+
 int ctis_plan_check(const ctis_plan* P, void* stream) {
     int rc = check_plan(P);
     if (rc) return rc;
     CTIS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     int flag = 0;
     CTIS_CUDA(cudaMemcpy(&flag, P->d_counters + 3, sizeof(int), cudaMemcpyDeviceToHost));
+    if (P->batch) {   // the batched launches keep their own counters
+        int bflag = 0;
+        CTIS_CUDA(cudaMemcpy(&bflag, P->batch->d_counters + 3, sizeof(int), cudaMemcpyDeviceToHost));
+        if (bflag) CTIS_CUDA(cudaMemset(P->batch->d_counters + 3, 0, sizeof(int)));
+        flag |= bflag;
+    }
     if (flag) {
         CTIS_CUDA(cudaMemset(P->d_counters + 3, 0, sizeof(int)));
         return fail(CTIS_ERR_TIMEOUT, "a kernel's bounded wait gave up (flag %d)", flag);
