@@ -41,6 +41,7 @@ def parse_args():
     ap.add_argument("--k", type=int, default=None, help="EM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and autograd forms")
     return ap.parse_args()
 
 
@@ -363,11 +364,15 @@ def run_ours(args, wl, k):
         "e2e": {"value": e2e_value, "unit": "it/s",
                 "h2d_bytes_per_step": g_pin.numel() * 4,
                 "d2h_bytes_per_step": f_pin.numel() * 4 + st_pin.numel() * 8},
-        "gpu_launches": args.steps * (2 * k + 2),
+        # per step: f scatter, k + 1 forwards (the last for the statistics), k adjoints, f out
+        "gpu_launches": args.steps * (2 * k + 3),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
     line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value)}
+    if world == 1 and not args.no_forms:
+        line["forms"]["batched"] = batched_form(args, flush, stream)
+        line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
         v, iters_cpu, el, desc = oracle_sample(wl, g_host, args.cpu_budget)
@@ -409,6 +414,98 @@ def bf16_form(args, wl, k, psf, g, f32_result, flush, stream, f32_value):
     plan.close()
     return {"value": value, "unit": "it/s", "steps": steps, "vs_f32": value / f32_value,
             "rel_l2_vs_f32_after_k": err, "dtype": "bf16 storage, f32 accumulate"}
+
+
+def _timed_steps(fn, steps, flush, stream):
+    import torch
+    total = 0.0
+    for i in range(steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total
+
+
+def batched_form(args, flush, stream, nframes=256, k=100):
+    """The batched form: 256 frames, 3:1 of the 64x64x32 -> 512^2 and the
+    128x128x64 -> 1024^2 geometry, k EM iterations with per-frame statistics,
+    one ctis_reconstruct_batched call per step. Frame i: plan B when
+    i % 4 == 3, else A; scene (1000 + i) % 8 of its geometry (8 scenes each,
+    cycled), Poisson counts of H f scaled to the workload's peak drawn on the
+    GPU with seed 1000 + i."""
+    import torch
+    import synth
+    from paper_2006_01573_gb300 import Plan, reconstruct_batched
+    wls = [synth.MODEL_A, synth.MODEL_B]
+    plans = [Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl)) for wl in wls]
+    plan_idx = [1 if i % 4 == 3 else 0 for i in range(nframes)]
+    scenes = [[torch.from_numpy(synth.make_scene(wl, 1000 + j)).cuda() for j in range(8)]
+              for wl in wls]
+    gs = []
+    for i, p in enumerate(plan_idx):
+        hf = plans[p].forward(scenes[p][(1000 + i) % 8])
+        gen = torch.Generator(device="cuda").manual_seed(1000 + i)
+        gs.append(torch.poisson(hf * (wls[p].peak / hf.max()), generator=gen))
+    del scenes
+    fs = [torch.empty((wls[p].w, wls[p].alpha, wls[p].a), device="cuda") for p in plan_idx]
+    stats = torch.empty((nframes, k + 1, 4), device="cuda", dtype=torch.float64)
+
+    def step():
+        reconstruct_batched(plans, plan_idx, gs, k, fs=fs, init="ones", stats=stats)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    total = _timed_steps(step, steps, flush, stream)
+    for p in plans:
+        p.check()
+    voxels = sum(wls[p].m for p in plan_idx)
+    secs = total / 1e3
+    out = {"frames": nframes, "mix": "192 x 64x64x32->512^2 + 64 x 128x128x64->1024^2",
+           "k": k, "steps": steps, "ms_per_step": total / steps,
+           "frame_iterations_per_s": steps * nframes * k / secs,
+           "voxel_updates_per_s": steps * voxels * k / secs,
+           # per plan: g gather, f scatter, k + 1 forwards, k adjoints, f out, statistics rows
+           "launches_per_step": len(plans) * (2 * k + 5),
+           "data": "8 scenes per geometry cycled, per-frame Poisson noise on the GPU"}
+    for p in plans:
+        p.close()
+    return out
+
+
+def autograd_form(args, flush, stream, k=10):
+    """The autograd form: Poisson NLL after 10 unrolled EM updates of the
+    realistic workload and its gradient with respect to every PSF value
+    (checkpointed iterates, native backward pass), one call per step."""
+    import torch
+    import synth
+    from paper_2006_01573_gb300 import Plan
+    wl = synth.AUTOGRAD
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl))
+    hf = plan.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
+    g_host, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, wl.seed)
+    g = torch.from_numpy(g_host).cuda()
+
+    def step():
+        plan.unrolled_nll_grad(g, k)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    total = _timed_steps(step, steps, flush, stream)
+    plan.check()
+    info = plan.info()
+    plan.close()
+    return {"workload": wl.name, "k_unrolled": k, "steps": steps, "ms_per_step": total / steps,
+            "value_and_grad_per_s": steps / (total / 1e3),
+            "unrolled_iterations_per_s": steps * k / (total / 1e3),
+            "grad_entries": int(info["nnz"])}
 
 
 def main():

@@ -11,7 +11,7 @@
  * per wavelength is the response to a point source at field-stop pixel (0,0);
  * under shift-invariance, field-stop pixel (p, r) produces the same image
  * shifted by (p, r). H therefore has n = gamma*xi rows and m = a*alpha*w
- * columns, and H f = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k) (Eqs. 1, 8-9).
+ * columns, and H f = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k) (Eqs. 1, 8, 12).
  *
  * Layouts (all dense, row-major, no padding in caller buffers):
  *   datacube f   : f[s][r][p], element j = s*a*alpha + r*a + p (the zero-based
@@ -139,7 +139,7 @@ int ctis_index_map(const ctis_plan* plan, int64_t* out_dev, void* stream);
  * hf_dev: n float32. */
 int ctis_forward(const ctis_plan* plan, const void* f_dev, float* hf_dev, void* stream);
 
-/* out_dev = H^T r_dev (Eq. 11). r_dev: n float32; out_dev: m float32. */
+/* out_dev = H^T r_dev (Eq. 14). r_dev: n float32; out_dev: m float32. */
 int ctis_adjoint(const ctis_plan* plan, const float* r_dev, float* out_dev, void* stream);
 
 /* k EM updates (Eq. 2, Algorithm 1): per iteration u = g / (H f) (0 where

@@ -18,7 +18,7 @@ shift-invariance":
   the 0/1 embedding ``E`` built from ``Q = [I_a; 0]`` (used by :func:`dense_H`).
 * Sec. 3 index map ``i = j - s l + (gamma - a) floor((j - s l)/a) + s n``
   (:func:`index_map`).
-* Eq. 10 (forward) and Eq. 14 (back projection) in their FFT form
+* Eq. 13 (forward) and Eq. 17 (back projection) in their FFT form
   (:func:`fft_forward`, :func:`fft_adjoint`).
 * The bfloat16 storage form (datacube and PSF values kept in bfloat16, sums in
   wider precision) is not in the paper; :func:`round_bf16` states the storage
@@ -39,7 +39,7 @@ are promoted exactly. Readings of points the paper leaves open:
 
 Pins (tests/test_oracle_*.py): every function here is checked against something
 other than itself - a dense H assembled literally from Eqs. 5-7, the FFT form of
-Eqs. 10/14 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
+Eqs. 13/17 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
 for w = 1, brute-force Python loops on tiny inputs, hand-worked values in
 tests/golden/, the EM invariants (nonnegativity, flux, monotone likelihood),
 finite differences of a dense H, and PyTorch's float32 -> bfloat16 conversion
@@ -141,7 +141,7 @@ def merge_psf(geom: Geometry, psf) -> Taps:
 def index_map(geom: Geometry) -> np.ndarray:
     """Zero-based position in ``v = (I_w kron E) f`` of each datacube entry j.
 
-    Sec. 3 (after Eq. 9): ``s = floor(j / l)`` and
+    Sec. 3, Eq. 11: ``s = floor(j / l)`` and
     ``i = j - s l + (gamma - a) floor((j - s l) / a) + s n``.
     """
     j = np.arange(geom.m, dtype=np.int64)
@@ -348,7 +348,7 @@ def _calibration_column(geom: Geometry, taps: Taps, s: int) -> np.ndarray:
 
 
 def fft_forward(geom: Geometry, psf, f: np.ndarray) -> np.ndarray:
-    """Eq. 10: ``g = F^-1 sum_i d_i * (F v_i)`` with ``d_i = F c_i`` and
+    """Eq. 13: ``g = F^-1 sum_i d_i * (F v_i)`` with ``d_i = F c_i`` and
     ``v_i = E f_i`` placed by the Sec. 3 index map (real FFT of length n)."""
     taps = merge_psf(geom, psf)
     f = np.asarray(f, dtype=np.float64).ravel()
@@ -363,7 +363,7 @@ def fft_forward(geom: Geometry, psf, f: np.ndarray) -> np.ndarray:
 
 
 def fft_adjoint(geom: Geometry, psf, u: np.ndarray) -> np.ndarray:
-    """Eq. 14: ``C_i^T u = F^-1(conj(d_i) * F u)``, then the transposed index
+    """Eqs. 14, 17: ``C_i^T u = F^-1(conj(d_i) * F u)``, then the transposed index
     map ``zeta = (I_w kron E)^T z`` gathers voxel values (Sec. 3)."""
     taps = merge_psf(geom, psf)
     U = np.fft.rfft(np.asarray(u, dtype=np.float64).ravel())

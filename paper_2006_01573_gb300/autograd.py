@@ -3,7 +3,7 @@ marshalling only: every projection and gradient runs in libctis).
 
 * :func:`project` -- ``H f`` as a function of the datacube ``f`` and the PSF tap
   values ``v`` (``Plan.export_taps`` order). Backward: ``dL/df = H^T gy``
-  (Eq. 11) and ``dL/dv_t = sum_{p,r} f_s(p, r) gy(x_t + p, y_t + r)``.
+  (Eq. 14) and ``dL/dv_t = sum_{p,r} f_s(p, r) gy(x_t + p, y_t + r)``.
 * :func:`unrolled_nll` -- the Poisson negative log-likelihood after k EM
   updates (Eq. 2) as a function of ``v`` (and of the initial guess), with the
   gradient through the updates, including ``h = H^T 1``, computed natively with

@@ -1,8 +1,8 @@
 // Windowed-gather device code for the shift-invariant CTIS projector pair,
 // shared by the forward and adjoint translation units.
 //
-// Forward (Eqs. 1, 8-9):  (H f)(x, y) = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k)
-// Adjoint (Eq. 11):     (H^T r)_s(p, r) = sum_k v_{s,k} r(x_k + p, y_k + r)
+// Forward (Eqs. 1, 8, 12):  (H f)(x, y) = sum_s sum_k v_{s,k} f_s(x - x_k, y - y_k)
+// Adjoint (Eq. 14):     (H^T r)_s(p, r) = sum_k v_{s,k} r(x_k + p, y_k + r)
 //
 // The PSF nonzeros of each wavelength are grouped into K x K spot clusters.
 // Applying one cluster to an output tile is a K x K correlation of a window of
@@ -496,7 +496,7 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float val = v[o][c];
-                // u = g / Hf on the support of Hf (Eq. 12); the fast quotient
+                // u = g / Hf on the support of Hf (Eq. 2); the fast quotient
                 // (within 2 ulp) is used for normal Hf, the IEEE one below
                 u[c] = val >= 1.17549435e-38f ? __fdividef(gv[c], val) : (val > 0.f ? gv[c] / val : 0.f);
                 // d/dq (q - g log q) = 1 - g / q on the support of q

@@ -1,7 +1,7 @@
-// Adjoint projector kernels (Eq. 11): voxel tiles of one wavelength, input
+// Adjoint projector kernels (Eq. 14): voxel tiles of one wavelength, input
 // windows from the x-shifted FPA copies, cluster weights as stored.
 // Epilogues: H^T r as is (ctis_adjoint), or the EM update
-// f <- f * (H^T u) / h (Eq. 13) written into the datacube copies, which with
+// f <- f * (H^T u) / h (Eq. 2) written into the datacube copies, which with
 // no previous f sets f = H^T g (the initial guess).
 #include "ctis_gather.cuh"
 

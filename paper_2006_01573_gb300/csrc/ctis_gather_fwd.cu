@@ -1,6 +1,6 @@
-// Forward projector kernels (Eqs. 1, 8-9): FPA tiles, input windows from the
+// Forward projector kernels (Eqs. 1, 8, 12): FPA tiles, input windows from the
 // x-shifted datacube copies, flipped cluster weights. Epilogues: H f as is
-// (ctis_forward), or the EM ratio u = g / H f (Eq. 12) written into the FPA
+// (ctis_forward), or the EM ratio u = g / H f (Eq. 2) written into the FPA
 // copies, with float64 statistics of the iteration.
 #include "ctis_gather.cuh"
 

@@ -3,9 +3,9 @@
 // Both projectors are one "windowed gather" kernel. A work item names an output
 // tile and a contiguous range of tasks; a task names one spot cluster applied to
 // that tile: a K x K weight set and the origin of the input window it reads.
-//   forward  (Eqs. 1, 8-9): output = FPA tile, input windows from f_s planes,
+//   forward  (Eqs. 1, 8, 12): output = FPA tile, input windows from f_s planes,
 //            weights flipped (the cluster is applied as a convolution);
-//   adjoint  (Eq. 11):      output = voxel tile of wavelength s, input windows
+//   adjoint  (Eq. 14):      output = voxel tile of wavelength s, input windows
 //            from the FPA vector r, weights as stored (a correlation).
 // Tiles with more tasks than one item holds are split into chunks whose
 // partial sums are added, in chunk order, by the last chunk to finish.

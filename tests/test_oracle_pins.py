@@ -1,6 +1,6 @@
 """Pins for the FP64 oracle: each check compares it with something other than
 itself (hand-worked values, a dense H assembled from Eqs. 5-7, the FFT form of
-Eqs. 10/14, SciPy's 2-D convolution, brute-force loops, EM invariants)."""
+Eqs. 13/17, SciPy's 2-D convolution, brute-force loops, EM invariants)."""
 import json
 import os
 
@@ -98,7 +98,7 @@ def test_dense_form_on_synthetic_grating_psf():
                                rtol=1e-15, atol=0)
 
 
-# --- FFT form of the paper (Eqs. 10 and 14) ----------------------------------------
+# --- FFT form of the paper (Eqs. 13 and 17) ----------------------------------------
 
 def test_fft_forms_match_sparse_projectors_tiny_workload():
     wl = synth.TINY
