@@ -93,6 +93,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// GPU-scope release/acquire fence (lighter than the sequentially consistent
+// __threadfence): orders this thread's earlier memory accesses, and those it
+// has observed, before its later ones for every thread of the GPU.
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
                                             int z, uint64_t* bar) {
     asm volatile(
@@ -188,6 +195,9 @@ struct Geo {
     static constexpr int THREADS = NW * 32;
     static constexpr int STAGES_BYTES = NW * NS * STAGE_BYTES;
     static constexpr int SMEM_BYTES = STAGES_BYTES + NW * NS * 8;
+    // resident CTAs per SM the register budget must allow (4 x 4 warps = 16
+    // warps per SM when the stages fit; the occupancy query has the last word)
+    static constexpr int MIN_BLOCKS = (227 * 1024) / (SMEM_BYTES + 1024) >= 4 ? 4 : 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -405,36 +415,42 @@ template <typename T, int C, int LX>
 __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int ncopies, bool active,
                                              int tx, int tile_cols, const float (&v)[C]) {
     constexpr int NCMAX = 16 / int(sizeof(T));
+    constexpr int DMAX = (NCMAX - 1 + C - 1) / C;   // lanes to the left a copy reaches
     const int col0 = tx * C;
-    // `ncopies` is the same for every lane of the launch, so all lanes run
-    // every shuffle; lanes of rows outside the plane (`active` false) store
-    // nothing.
+    // The values of the DMAX lanes to the left, fetched once for all copies.
+    // Every lane runs the shuffles (DMAX is uniform); lanes of rows outside
+    // the plane (`active` false) store nothing.
+    float left[DMAX][C];
+#pragma unroll
+    for (int d = 1; d <= DMAX; ++d)
+#pragma unroll
+        for (int j = 0; j < C; ++j) left[d - 1][j] = __shfl_up_sync(0xffffffffu, v[j], d);
+    if (!active) return;
 #pragma unroll
     for (int q = 0; q < NCMAX; ++q) {
         if (q >= ncopies) break;
+        // destination column col0 + j of copy q holds source column col0 + j - q
         float a[C];
-        bool full = active;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            // destination column col0 + j of copy q holds source column col0 + j - q
-            const int d = j >= q ? 0 : (q - j + C - 1) / C;     // lanes to the left
-            const int e = ((j - q) % C + C) % C;                // element in that lane
-            const float up = __shfl_up_sync(0xffffffffu, v[e], d);
-            a[j] = d == 0 ? v[e] : up;
-            const int src = col0 + j - q;
-            if (tx < d || src >= tile_cols) full = false;
+            const int e = j - q;
+            if (e >= 0) {
+                a[j] = v[e];
+            } else {
+                const int d = (-e + C - 1) / C;
+                a[j] = left[d - 1][e + d * C];
+            }
         }
-        if (!active) continue;
         T* dst = row + q * copy_stride;
-        if (full) {
+        const int dneed = (q + C - 1) / C;   // lanes to the left the group reads
+        if (tx >= dneed && col0 + C - 1 - q < tile_cols) {
             DBG_CHECK_RANGE(dst + col0, C);
             Vec<T, C>::store(dst + col0, a);
         } else {
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const int d = j >= q ? 0 : (q - j + C - 1) / C;
                 const int src = col0 + j - q;
-                if (tx >= d && src >= 0 && src < tile_cols) {
+                if (src >= 0 && src < tile_cols) {
                     DBG_CHECK_RANGE(dst + col0 + j, 1);
                     Elem<T>::store(dst + col0 + j, a[j]);
                 }
@@ -582,12 +598,12 @@ __device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx
         double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
         __stcg(dst, make_double2(tot[0], tot[1]));
         __stcg(dst + 1, make_double2(tot[2], tot[3]));
-        __threadfence();
+        fence_acq_rel_gpu();
         last = atomicAdd(&group_tickets[group], 1) == in_group - 1;
     }
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     double d[kNumStats] = {0.0, 0.0, 0.0, 0.0};
     if (lane < in_group)
         load_stats(p.tile_stats + (long long)(frame * tpf + lgroup * kStatGroup + lane) * kNumStats, d);
@@ -599,12 +615,12 @@ __device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx
         __stcg(dst, make_double2(d[0], d[1]));
         __stcg(dst + 1, make_double2(d[2], d[3]));
         group_tickets[group] = 0;
-        __threadfence();
+        fence_acq_rel_gpu();
         last = atomicAdd(&p.stat_frame_done[frame], 1) == gpf - 1;
     }
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
     for (int g0 = 0; g0 < gpf; g0 += 32) {   // all loads of a pass in flight at once
         double e[kNumStats] = {0.0, 0.0, 0.0, 0.0};
@@ -800,25 +816,46 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                 for (int c = 0; c < G::C; c += 4)
                     __stcg(reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)),
                            make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]));
-            __threadfence();
+            // publish the partial sums (release), then take the tile's ticket
+            fence_acq_rel_gpu();
             __syncwarp();
             int old = 0;
             if (lane == 0) old = atomicAdd(&p.tickets[it.tile], 1);
             old = __shfl_sync(0xffffffffu, old, 0);
             finish = old == nchunks - 1;
             if (finish) {
-                __threadfence();
+                fence_acq_rel_gpu();   // acquire the other chunks' sums
+                // add every chunk's stored sums in chunk order; each pass
+                // issues a whole chunk's loads at once (one L2 round trip per
+                // chunk rather than one per chunk and row)
+                constexpr int NV = G::R * G::C / 4;
+                float4 sum[NV];
+#pragma unroll
+                for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                    for (int c = 0; c < G::C; c += 4)
+                        sum[(o * G::C + c) / 4] =
+                            __ldcg(reinterpret_cast<const float4*>(slots + tile_elem<G>(tx, ty, o, c)));
+#pragma unroll 1
+                for (int ch = 1; ch < nchunks; ++ch) {
+                    float4 q4[NV];
+#pragma unroll
+                    for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                        for (int c = 0; c < G::C; c += 4)
+                            q4[(o * G::C + c) / 4] = __ldcg(reinterpret_cast<const float4*>(
+                                slots + (long long)ch * G::TILE + tile_elem<G>(tx, ty, o, c)));
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) {
+                        sum[k].x += q4[k].x; sum[k].y += q4[k].y;
+                        sum[k].z += q4[k].z; sum[k].w += q4[k].w;
+                    }
+                }
 #pragma unroll
                 for (int o = 0; o < G::R; ++o)
 #pragma unroll
                     for (int c = 0; c < G::C; c += 4) {
-                        const int e = tile_elem<G>(tx, ty, o, c);
-                        float4 s4 = __ldcg(reinterpret_cast<const float4*>(slots + e));
-                        for (int ch = 1; ch < nchunks; ++ch) {
-                            const float4 q4 = __ldcg(
-                                reinterpret_cast<const float4*>(slots + (long long)ch * G::TILE + e));
-                            s4.x += q4.x; s4.y += q4.y; s4.z += q4.z; s4.w += q4.w;
-                        }
+                        const float4 s4 = sum[(o * G::C + c) / 4];
                         v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
                     }
                 if (lane == 0) p.tickets[it.tile] = 0;

@@ -18,7 +18,7 @@ namespace ctis {
 namespace {
 
 template <class G, typename TIn, typename TF, int MODE>
-__global__ void __launch_bounds__(G::THREADS)
+__global__ void __launch_bounds__(G::THREADS, G::MIN_BLOCKS)
     psf_grad_kernel(const __grid_constant__ CUtensorMap tm_win, const GatherParams p) {
     gather_body<G, TIn, TF, MODE>(tm_win, p);
 }
