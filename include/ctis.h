@@ -237,6 +237,16 @@ int ctis_psf_grad(const ctis_plan* plan, const void* f_dev, const float* r_dev,
 int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_dev, int k,
                            double* nll_dev, float* dval_dev, float* df0_dev, void* stream);
 
+/* Autotuner: for each projector, times the plan's EM launches (forward with
+ * the ratio and statistics, adjoint with the update) over candidate work
+ * schedules (cluster tasks per work item: the plan's model choice and
+ * 6..64) on this GPU, with g_dev (n float32) as the measurement and f = 1,
+ * and keeps the fastest. Synchronous; overwrites the plan's internal copies
+ * and drops its cached graphs (the next ctis_reconstruct re-captures).
+ * Results stay deterministic for a given schedule but may differ in the last
+ * bits between schedules (partial sums are grouped differently). */
+int ctis_plan_autotune(ctis_plan* plan, const float* g_dev, void* stream);
+
 /* Wait for the plan's work on `stream`, then report (and clear) any device-side
  * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
 int ctis_plan_check(const ctis_plan* plan, void* stream);

@@ -27,6 +27,7 @@ EXPORTED = (
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
+    "ctis_plan_autotune",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
         "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "ctis_plan_set_values": (I, [P, f32p]),
+        "ctis_plan_autotune": (I, [P, VP, VP]),
         "ctis_reconstruct_batched": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
                                          ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
@@ -274,6 +276,15 @@ class Plan:
     def check(self, stream=None):
         """Synchronise the stream and raise if a kernel reported a device-side failure."""
         _check(load().ctis_plan_check(self._h, _stream(stream)))
+
+    def autotune(self, g, stream=None):
+        """Time the EM launches over candidate work schedules with ``g`` as the
+        measurement and keep the fastest (synchronous). Returns the chosen
+        tasks per item ``(forward, adjoint)``."""
+        self._check_fpa(g)
+        _check(load().ctis_plan_autotune(self._h, ctypes.c_void_p(g.data_ptr()), _stream(stream)))
+        info = self.info()
+        return int(info["fwd_chunk"]), int(info["adj_chunk"])
 
     # -- gradients ---------------------------------------------------------------
     @property

@@ -83,7 +83,9 @@ struct Cluster {
 struct ProjTables {
     std::vector<TileDesc> tiles;
     std::vector<ItemDesc> items;
-    std::vector<TaskDesc> tasks;
+    std::vector<TaskDesc> tasks;   // warp order (what the kernel reads)
+    std::vector<TaskDesc> tile_tasks;       // tile order, the input of schedule()
+    std::vector<int> tile_task_begin;       // [tiles + 1]
     std::vector<int> warp_begin;   // [n_warps + 1]
     std::vector<int> warp_items;   // item indices, grouped by warp
     std::vector<WorkItem> witems;  // the items in warp order, as the kernel reads them
@@ -167,6 +169,8 @@ struct ctis_plan {
     float* d_u = nullptr;        // u_copies x-shifted copies of the FPA input of the adjoint
     void* d_fwork = nullptr;     // f_copies x-shifted copies of the datacube (forward input)
     float* d_scratch = nullptr;
+    int64_t scratch_capacity = 0;    // float elements of d_scratch
+    double* d_tune_stats = nullptr;  // autotuning runs' statistics row
     int* d_tickets = nullptr;
     int* d_counters = nullptr;
     double* d_tile_stats = nullptr;
@@ -230,6 +234,7 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_u);
     cudaFree(P->d_fwork);
     cudaFree(P->d_scratch);
+    cudaFree(P->d_tune_stats);
     cudaFree(P->d_tickets);
     cudaFree(P->d_counters);
     cudaFree(P->d_tile_stats);
@@ -243,9 +248,11 @@ void destroy(ctis_plan* P) {
     delete P;
 }
 
-// Cost of an item in task units: its tasks, plus the partial-sum round trip
-// and ticket of a chunked tile, plus the epilogue.
-double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 2.0 : 0.0) + 0.5; }
+// Cost of an item in task units: its tasks, plus the partial-sum store,
+// fence, ticket and (for the last chunk) the reduction of a chunked tile,
+// plus the epilogue. The chunk overhead is the measured cost on GB300 of the
+// realistic workload's chunked items, about four tasks' worth.
+double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 4.0 : 0.0) + 0.5; }
 
 // Splits every tile's task range into chunks of at most `per_item` tasks and
 // fills the item list and the scratch slot bases.
@@ -312,7 +319,8 @@ double assign_warps(ProjTables& T, int n_warps) {
 
 // Picks the chunk size that minimises the LPT estimate of the busiest warp
 // (ties: the larger chunk, i.e. fewer partial sums), or uses `forced` > 0.
-void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int forced) {
+void schedule(ProjTables& T, int n_warps, int forced) {
+    const std::vector<int>& begin = T.tile_task_begin;
     T.n_warps = n_warps;
     std::vector<int> cands;
     if (forced > 0) {
@@ -337,7 +345,7 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
     // same order, so every warp's tasks form one contiguous range
     T.witems.clear();
     std::vector<TaskDesc> wt;
-    wt.reserve(T.tasks.size());
+    wt.reserve(T.tile_tasks.size());
     for (int i : T.warp_items) {
         const ItemDesc& it = T.items[i];
         const TileDesc& td = T.tiles[it.tile];
@@ -349,11 +357,12 @@ void schedule(ProjTables& T, const std::vector<int>& begin, int n_warps, int for
         w.chunk_info = td.nchunks | (it.chunk << 16);
         w.scratch_base = td.scratch_base;
         w.task_begin = static_cast<int>(wt.size());
-        wt.insert(wt.end(), T.tasks.begin() + it.task_begin, T.tasks.begin() + it.task_end);
+        wt.insert(wt.end(), T.tile_tasks.begin() + it.task_begin,
+                  T.tile_tasks.begin() + it.task_end);
         w.task_end = static_cast<int>(wt.size());
         T.witems.push_back(w);
     }
-    T.tasks.swap(wt);
+    T.tasks = std::move(wt);
 }
 
 // h = H^T 1 (Eq. 2): under the on-FPA rule every voxel of wavelength s sees
@@ -621,10 +630,11 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                     t.cluster = c;
                     tl.push_back(t);
                 }
-                T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
-                begin.push_back(static_cast<int>(T.tasks.size()));
+                T.tile_tasks.insert(T.tile_tasks.end(), tl.begin(), tl.end());
+                begin.push_back(static_cast<int>(T.tile_tasks.size()));
             }
-        schedule(T, begin, warps_fwd, P->forced_per_item);
+        T.tile_task_begin = std::move(begin);
+        schedule(T, warps_fwd, P->forced_per_item);
     }
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
@@ -658,10 +668,11 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                         t.cluster = static_cast<int>(c);
                         tl.push_back(t);
                     }
-                    T.tasks.insert(T.tasks.end(), tl.begin(), tl.end());
-                    begin.push_back(static_cast<int>(T.tasks.size()));
+                    T.tile_tasks.insert(T.tile_tasks.end(), tl.begin(), tl.end());
+                    begin.push_back(static_cast<int>(T.tile_tasks.size()));
                 }
-        schedule(T, begin, warps_adj, P->forced_per_item);
+        T.tile_task_begin = std::move(begin);
+        schedule(T, warps_adj, P->forced_per_item);
     }
 
     // ---- device buffers
@@ -688,6 +699,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                  P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch),
                           sizeof(float) * static_cast<size_t>(scratch_elems));
+    P->scratch_capacity = scratch_elems;
     // tickets: one per tile (chunked tiles), then one per group of
     // kStatGroup forward tiles (statistics); statistics: per forward tile,
     // then per group
@@ -1842,6 +1854,120 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
         g_batched_key = key;
     }
     CTIS_CUDA(cudaGraphLaunch(g_batched_exec, st));
+    return CTIS_OK;
+}
+
+int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!g_dev) return fail(CTIS_ERR_INVALID_ARG, "g_dev is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CTIS_CUDA(cudaDeviceSynchronize());
+    // the tables change: drop everything built on the old ones
+    if (P->gexec) {
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+        P->gkey = GraphKey{};
+    }
+    drop_batched_graph_of(P);
+    free_batch(P->batch);
+    P->batch = nullptr;
+    if (!P->d_tune_stats) {
+        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tune_stats), sizeof(double) * kNumStats);
+        if (rc) return rc;
+    }
+    // realistic operands: f = 1 in the datacube copies, g in the FPA copies
+    rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
+    if (!rc) rc = scatter_u(P, g_dev, st);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CTIS_CUDA(cudaEventCreate(&e0));
+    {
+        const cudaError_t e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    auto reupload = [&](ProjTables& T) -> int {
+        cudaFree(T.d_tasks);
+        cudaFree(T.d_warp_begin);
+        cudaFree(T.d_witems);
+        T.d_tasks = nullptr;
+        T.d_warp_begin = nullptr;
+        T.d_witems = nullptr;
+        int r = upload(P, &T.d_tasks, T.tasks);
+        if (!r) r = upload(P, &T.d_warp_begin, T.warp_begin);
+        if (!r) r = upload(P, &T.d_witems, T.witems);
+        if (r) return r;
+        const int64_t need = T.scratch_slots * T.tile_w * T.tile_h;
+        if (need > P->scratch_capacity) {
+            cudaFree(P->d_scratch);
+            P->d_scratch = nullptr;
+            P->scratch_capacity = 0;
+            r = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch), sizeof(float) * need);
+            if (r) return r;
+            P->scratch_capacity = need;
+        }
+        return CTIS_OK;
+    };
+    // the EM launches (ratio with statistics; update) on the candidate tables
+    auto run = [&](bool forward) -> int {
+        if (forward) {
+            GatherParams p = base_params(P, P->fwd);
+            p.mode = kEpiRatio;
+            p.out_w = P->gamma;
+            p.out_h = P->xi;
+            p.out_f32 = P->d_u;
+            p.out_pitch = P->g_pitch;
+            p.out_copy_stride = P->u_copy_stride;
+            p.out_copies = P->u_copies;
+            p.g = g_dev;
+            p.g_pitch = P->gamma;
+            p.with_stats = 1;
+            p.stats_out = P->d_tune_stats;
+            return enqueue_forward(P, p, st);
+        }
+        GatherParams p = base_params(P, P->adj);
+        p.mode = kEpiUpdate;
+        p.out_w = P->a;
+        p.out_h = P->alpha;
+        set_f_copies(P, p);
+        return enqueue_adjoint(P, p, st);
+    };
+    const int cands[] = {0, 6, 8, 12, 16, 24, 32, 48, 64};
+    int result = CTIS_OK;
+    for (ProjTables* T : {&P->fwd, &P->adj}) {
+        const bool forward = T == &P->fwd;
+        float best_ms = -1.f;
+        int best = 0;
+        for (int c : cands) {
+            schedule(*T, T->n_warps, c);
+            if (c != 0 && T->per_item != c) continue;
+            result = reupload(*T);
+            for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
+            cudaError_t e = result ? cudaSuccess : cudaEventRecord(e0, st);
+            for (int r = 0; r < 5 && !result && e == cudaSuccess; ++r) result = run(forward);
+            if (!result && e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (!result && e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!result && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (!result && e != cudaSuccess) result = cuda_fail(e, "timing a candidate schedule");
+            if (result) break;
+            if (best_ms < 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = T->per_item;
+            }
+        }
+        if (result) break;
+        schedule(*T, T->n_warps, best);
+        result = reupload(*T);
+        if (result) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result) return result;
+    CTIS_CUDA(cudaStreamSynchronize(st));
     return CTIS_OK;
 }
 

@@ -1,0 +1,62 @@
+"""GPU tests of the schedule autotuner: it keeps a schedule from its candidate
+set, and reconstructions on the tuned plan still meet the parity bounds and
+stay bit-reproducible (the schedule only regroups the chunk partial sums)."""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle as O
+import synth
+from paper_2006_01573_gb300 import Plan
+from tests.helpers import floored_rel, problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CANDIDATES = {6, 8, 12, 16, 24, 32, 48, 64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def test_autotuned_plan_matches_oracle_and_is_reproducible():
+    wl = synth.TINY
+    geom, psf, H, _, g = problem(wl)
+    ref, _ = O.mlem(H, g, wl.k)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        model_choice = plan.info()["fwd_chunk"], plan.info()["adj_chunk"]
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        fc, ac = plan.autotune(gt)
+        assert fc in CANDIDATES | {model_choice[0]} and ac in CANDIDATES | {model_choice[1]}
+        a, _ = plan.reconstruct(gt, k=wl.k, init="ones")
+        a = a.clone()
+        b, _ = plan.reconstruct(gt, k=wl.k, init="ones")
+        plan.check()
+        got = b.cpu().numpy().ravel()
+    assert torch.equal(a, b)
+    assert floored_rel(got, ref) <= wl.k * 1e-5
+    assert rel_l2(got, ref) <= 1e-5 * np.sqrt(wl.k)
+
+
+def test_autotune_full_size_stays_within_tolerance_of_untuned():
+    wl = synth.REALISTIC
+    psf = synth.make_psf(wl)
+    k = 10
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as p1, \
+            Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as p2:
+        hf = p1.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
+        g, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, wl.seed)
+        gt = torch.from_numpy(g).cuda()
+        p2.autotune(gt)
+        a, sa = p1.reconstruct(gt, k=k, init="ones", stats=True)
+        b, sb = p2.reconstruct(gt, k=k, init="ones", stats=True)
+        p1.check()
+        p2.check()
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        sa, sb = sa.cpu().numpy(), sb.cpu().numpy()
+    # two float32 reconstructions that differ only in the grouping of sums
+    assert floored_rel(b, a) <= 2 * k * 1e-5
+    assert np.all(np.abs(sb - sa) <= 2e-5 * np.abs(sa))
