@@ -367,8 +367,9 @@ def run_ours(args, wl, k):
         "e2e": {"value": e2e_value, "unit": "it/s",
                 "h2d_bytes_per_step": g_pin.numel() * 4,
                 "d2h_bytes_per_step": f_pin.numel() * 4 + st_pin.numel() * 8},
-        # per step: f scatter, k + 1 forwards (the last for the statistics), k adjoints, f out
-        "gpu_launches": args.steps * (2 * k + 3),
+        # per step: f scatter, k + 1 forwards (the last for the statistics), k adjoints,
+        # the last forward's statistics reduction, f out
+        "gpu_launches": args.steps * (2 * k + 4),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
@@ -476,8 +477,9 @@ def batched_form(args, flush, stream, nframes=256, k=100):
            "k": k, "steps": steps, "ms_per_step": total / steps,
            "frame_iterations_per_s": steps * nframes * k / secs,
            "voxel_updates_per_s": steps * voxels * k / secs,
-           # per plan: g gather, f scatter, k + 1 forwards, k adjoints, f out, statistics rows
-           "launches_per_step": len(plans) * (2 * k + 5),
+           # per plan: g gather, f scatter, k + 1 forwards, k adjoints, f out, the last
+           # forward's statistics reduction, statistics rows
+           "launches_per_step": len(plans) * (2 * k + 6),
            "data": "8 scenes per geometry cycled, per-frame Poisson noise on the GPU"}
     for p in plans:
         p.close()

@@ -123,6 +123,15 @@ __global__ void rows_scatter_kernel(double* dst, const double* src, const int* g
     }
 }
 
+// Frame totals of the forward's tile statistics when no following launch
+// adds them: one warp per frame.
+__global__ void stats_reduce_kernel(double* out, const double* tile_stats, int tiles, int frames,
+                                    long long frame_stride) {
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (f >= frames) return;
+    reduce_frame_stats(tile_stats, tiles, f, out + f * frame_stride, threadIdx.x & 31);
+}
+
 // Sec. 3 embedding: datacube element j = (p, r, s) sits at FPA pixel
 // (x, y) = (p, r) of the s-th stacked FPA vector.
 __device__ __forceinline__ long long stacked_fpa_index(int p, int r, int s, int gamma, long long n) {
@@ -293,6 +302,14 @@ cudaError_t launch_frames_copy0_out(int dtype, void* const* dsts, const void* sr
 cudaError_t launch_rows_scatter(double* dst, const double* src, const int* gid, int len, int frames,
                                 cudaStream_t stream) {
     rows_scatter_kernel<<<256, 256, 0, stream>>>(dst, src, gid, len, frames);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_reduce(double* out, const double* tile_stats, int tiles, int frames,
+                                long long frame_stride, cudaStream_t stream) {
+    const int warps_per_block = 4;
+    stats_reduce_kernel<<<(frames + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
+                          stream>>>(out, tile_stats, tiles, frames, frame_stride);
     return cudaGetLastError();
 }
 

@@ -564,78 +564,48 @@ __device__ __forceinline__ double warp_sum(double d) {
     return d;
 }
 
-// Statistics of one finished tile, reduced in a fixed two-level tree so that
-// no single warp walks all tiles: the warp that finishes the last tile of a
-// group of 32 tiles adds that group (one tile per lane), and the warp that
-// finishes the last group of a frame adds that frame's groups into its row
-// of p.stats_out. Tile sums are
-// per-lane float32 sums of 32 elements widened to float64; everything above
-// them is float64 in a fixed order, so the result is reproducible.
 __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumStats]) {
     const double2 a = __ldcg(reinterpret_cast<const double2*>(src));
     const double2 b = __ldcg(reinterpret_cast<const double2*>(src) + 1);
     d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
 }
 
-__device__ __forceinline__ void finish_stats(const GatherParams& p, int tile_idx,
-                                             const float (&stat)[kNumStats], int lane) {
+// Statistics of one finished tile: the warp's per-lane float32 sums (32
+// elements each) widened to float64 and added in a fixed tree; lane 0 stores
+// the tile's four values. The frame totals are added later, in tile order, by
+// reduce_frame_stats (at the start of the next launch in stream order), so no
+// fence or atomic sits on the tile's path.
+__device__ __forceinline__ void store_tile_stats(const GatherParams& p, int tile_idx,
+                                                 const float (&stat)[kNumStats], int lane) {
     static_assert(kNumStats == 4, "statistics move as two double2");
-    // tiles are numbered frame by frame; every frame has its own tree
-    const int tpf = p.stat_tiles_per_frame;
-    const int gpf = (tpf + kStatGroup - 1) / kStatGroup;   // groups per frame
-    const int frame = tile_idx / tpf;
-    const int local = tile_idx - frame * tpf;
-    double* group_stats = p.tile_stats + (long long)p.n_tiles * kNumStats;
-    int* group_tickets = p.tickets + p.n_tiles;
     double tot[kNumStats];
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) tot[q] = warp_sum(static_cast<double>(stat[q]));
-    const int lgroup = local / kStatGroup;
-    const int group = frame * gpf + lgroup;
-    const int in_group = min(kStatGroup, tpf - lgroup * kStatGroup);
-    int last = 0;
     if (lane == 0) {
         double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
         __stcg(dst, make_double2(tot[0], tot[1]));
         __stcg(dst + 1, make_double2(tot[2], tot[3]));
-        fence_acq_rel_gpu();
-        last = atomicAdd(&group_tickets[group], 1) == in_group - 1;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    fence_acq_rel_gpu();
-    double d[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-    if (lane < in_group)
-        load_stats(p.tile_stats + (long long)(frame * tpf + lgroup * kStatGroup + lane) * kNumStats, d);
-#pragma unroll
-    for (int q = 0; q < kNumStats; ++q) d[q] = warp_sum(d[q]);
-    last = 0;
-    if (lane == 0) {
-        double2* dst = reinterpret_cast<double2*>(group_stats + (long long)group * kNumStats);
-        __stcg(dst, make_double2(d[0], d[1]));
-        __stcg(dst + 1, make_double2(d[2], d[3]));
-        group_tickets[group] = 0;
-        fence_acq_rel_gpu();
-        last = atomicAdd(&p.stat_frame_done[frame], 1) == gpf - 1;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    fence_acq_rel_gpu();
+}
+
+// One warp adds the tile statistics of one frame in a fixed order (lane l
+// sums tiles l, l + 32, ..., then a fixed warp tree) into that frame's row.
+// All loads of a pass are in flight together.
+__device__ __forceinline__ void reduce_frame_stats(const double* tile_stats, int tiles, int frame,
+                                                   double* out, int lane) {
+    const double* src = tile_stats + (long long)frame * tiles * kNumStats;
     double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-    for (int g0 = 0; g0 < gpf; g0 += 32) {   // all loads of a pass in flight at once
+    for (int i0 = 0; i0 < tiles; i0 += 32) {
         double e[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-        if (g0 + lane < gpf)
-            load_stats(group_stats + (long long)(frame * gpf + g0 + lane) * kNumStats, e);
+        if (i0 + lane < tiles) load_stats(src + (long long)(i0 + lane) * kNumStats, e);
 #pragma unroll
         for (int q = 0; q < kNumStats; ++q) t[q] += e[q];
     }
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) t[q] = warp_sum(t[q]);
     if (lane == 0) {
-        double* out = p.stats_out + frame * p.stats_frame_stride;
 #pragma unroll
         for (int q = 0; q < kNumStats; ++q) out[q] = t[q];
-        p.stat_frame_done[frame] = 0;
     }
 }
 
@@ -656,6 +626,10 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * G::NW + warp;
+    // the previous forward's statistics, one warp per frame
+    if (p.red_out && gw < p.red_frames)
+        reduce_frame_stats(p.red_src, p.red_tiles_per_frame, gw, p.red_out + gw * p.red_frame_stride,
+                           lane);
     if (gw >= p.n_warps) return;
     const int ib = p.warp_begin[gw], ie = p.warp_begin[gw + 1];
     if (ib >= ie) return;   // nothing issued, nothing to drain
@@ -865,7 +839,7 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
             epilogue<G, TF, MODE>(p, it, tx, ty, v, stat);
             if constexpr (MODE == kEpiRatio) {
-                if (p.with_stats) finish_stats(p, it.tile, stat, lane);
+                if (p.with_stats) store_tile_stats(p, it.tile, stat, lane);
             }
         }
     }

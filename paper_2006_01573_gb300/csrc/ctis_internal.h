@@ -21,7 +21,6 @@
 namespace ctis {
 
 constexpr int kNumStats = 4;   // flux_hf, flux_g, loglik, resid2 (see ctis.h)
-constexpr int kStatGroup = 32; // forward tiles per group of the statistics tree
 
 struct TileDesc {        // 32 bytes (host-side bookkeeping)
     int x0, y0;          // output origin: FPA (x, y) forward, voxel (p, r) adjoint
@@ -89,11 +88,13 @@ struct GatherParams {
     const float* g;
     int g_pitch;
     long long g_plane_stride;    // elements between frames of g
-    // statistics tree: tiles per frame, per-frame count of finished groups,
-    // elements between the frames' statistics rows
-    int stat_tiles_per_frame;
-    int* stat_frame_done;
-    long long stats_frame_stride;
+    // frame totals of a previous forward's tile statistics, added by warps
+    // 0 .. red_frames-1 at the start of this launch (red_out null: none)
+    const double* red_src;       // [frames][tiles][kNumStats]
+    double* red_out;             // frame f's row at red_out + f * red_frame_stride
+    int red_tiles_per_frame;
+    int red_frames;
+    long long red_frame_stride;
     // kEpiUpdate / kEpiSet (datacube copies in the plan's dtype; f_in = copy 0)
     const void* f_in;
     void* f_out;
@@ -112,9 +113,8 @@ struct GatherParams {
     // workspace
     float* scratch;            // partial tiles, [slots][TX*TY]
     int* tickets;              // [n_tiles], zero between launches
-    int* counters;             // [2] statistics groups done, [3] error flag (others unused)
-    double* tile_stats;        // [n_tiles][kNumStats]
-    double* stats_out;         // [kNumStats] or nullptr
+    int* counters;             // [3] error flag (others unused)
+    double* tile_stats;        // [n_tiles][kNumStats] written by kEpiRatio with_stats
 };
 
 // Compile-time configuration of one gather kernel instantiation.

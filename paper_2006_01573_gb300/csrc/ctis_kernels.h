@@ -52,6 +52,11 @@ cudaError_t static_scratch_ptr(void** out);   // device address on the current d
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream);
 
+// Frame totals of a forward's tile statistics (one warp per frame, fixed
+// order): out + f * frame_stride <- sum over tile_stats[f][0..tiles).
+cudaError_t launch_stats_reduce(double* out, const double* tile_stats, int tiles, int frames,
+                                long long frame_stride, cudaStream_t stream);
+
 // ---- frames of a batch (srcs / dsts: device arrays of per-frame pointers)
 // dst[f * n + i] = srcs[f][i]
 cudaError_t launch_frames_gather(float* dst, const float* const* srcs, long long n, int frames,

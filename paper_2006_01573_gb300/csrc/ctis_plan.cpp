@@ -170,7 +170,6 @@ struct ctis_plan {
     void* d_fwork = nullptr;     // f_copies x-shifted copies of the datacube (forward input)
     float* d_scratch = nullptr;
     int64_t scratch_capacity = 0;    // float elements of d_scratch
-    double* d_tune_stats = nullptr;  // autotuning runs' statistics row
     int* d_tickets = nullptr;
     int* d_counters = nullptr;
     double* d_tile_stats = nullptr;
@@ -234,7 +233,6 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_u);
     cudaFree(P->d_fwork);
     cudaFree(P->d_scratch);
-    cudaFree(P->d_tune_stats);
     cudaFree(P->d_tickets);
     cudaFree(P->d_counters);
     cudaFree(P->d_tile_stats);
@@ -700,15 +698,12 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch),
                           sizeof(float) * static_cast<size_t>(scratch_elems));
     P->scratch_capacity = scratch_elems;
-    // tickets: one per tile (chunked tiles), then one per group of
-    // kStatGroup forward tiles (statistics); statistics: per forward tile,
-    // then per group
-    const size_t stat_groups = (P->fwd.tiles.size() + kStatGroup - 1) / kStatGroup;
-    const size_t ntiles = std::max(P->fwd.tiles.size() + stat_groups, P->adj.tiles.size());
+    // tickets: one per tile (chunked tiles); statistics: per forward tile
+    const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 8);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
-                          sizeof(double) * kNumStats * (P->fwd.tiles.size() + stat_groups));
+                          sizeof(double) * kNumStats * P->fwd.tiles.size());
     if (rc) return rc;
     // copies start zeroed: the elements past each copy's shifted end are never
     // written and must read as zero
@@ -765,8 +760,6 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.counters = P->d_counters;
     p.tile_stats = P->d_tile_stats;
     p.h = P->d_h;
-    p.stat_tiles_per_frame = p.n_tiles;
-    p.stat_frame_done = P->d_counters + 2;
     return p;
 }
 
@@ -907,16 +900,25 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
         ev += 2;
         return r;
     };
+    pf.with_stats = stats != nullptr;
+    const int ftiles = static_cast<int>(P->fwd.tiles.size());
     for (int it = 0; it <= k; ++it) {
         if (it == k && !stats) break;
-        pf.with_stats = stats != nullptr;
-        pf.stats_out = stats ? stats + static_cast<int64_t>(it) * kNumStats : nullptr;
         rc = timed(P->prof_fwd, [&] { return enqueue_forward(P, pf, st); });
         if (rc) return rc;
         if (it == k) break;
+        if (stats) {   // the adjoint adds this forward's tile statistics first
+            pa.red_src = P->d_tile_stats;
+            pa.red_out = stats + static_cast<int64_t>(it) * kNumStats;
+            pa.red_tiles_per_frame = ftiles;
+            pa.red_frames = 1;
+        }
         rc = timed(P->prof_adj, [&] { return enqueue_adjoint(P, pa, st); });
         if (rc) return rc;
     }
+    if (stats)
+        CTIS_CUDA(launch_stats_reduce(stats + static_cast<int64_t>(k) * kNumStats, P->d_tile_stats,
+                                      ftiles, 1, 0, st));
     CTIS_CUDA(launch_gather_copy0(P->dtype, f, P->d_fwork, P->a_pitch,
                                   static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
                                   P->w, st));
@@ -1059,8 +1061,7 @@ int ensure_batch(ctis_plan* P, int F, int k) {
     const int64_t scratch = std::max(P->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
                                      P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
     const size_t tpf = P->fwd.tiles.size();
-    const size_t gpf = (tpf + kStatGroup - 1) / kStatGroup;
-    const size_t ntick = std::max((tpf + gpf) * F, P->adj.tiles.size() * F);
+    const size_t ntick = std::max(tpf * F, P->adj.tiles.size() * F);
     rc = dmalloc(P, &B->d_fwork, fbytes);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_u), ubytes);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_scratch),
@@ -1068,7 +1069,7 @@ int ensure_batch(ctis_plan* P, int F, int k) {
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tickets), sizeof(int) * ntick);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_counters), sizeof(int) * (8 + F));
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tile_stats),
-                          sizeof(double) * kNumStats * (tpf + gpf) * F);
+                          sizeof(double) * kNumStats * tpf * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_h), sizeof(float) * P->w * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_g), sizeof(float) * P->n * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_ptrs), sizeof(void*) * 2 * F);
@@ -1102,8 +1103,6 @@ GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward)
     p.counters = B->d_counters;
     p.tile_stats = B->d_tile_stats;
     p.h = B->d_h;
-    p.stat_tiles_per_frame = static_cast<int>(T.tiles.size());
-    p.stat_frame_done = B->d_counters + 8;
     return p;
 }
 
@@ -1196,12 +1195,30 @@ int batch_setup(BatchRun& r, int flags, cudaStream_t st) {
     return CTIS_OK;
 }
 
-int batch_forward_step(BatchRun& r, int it, int k, cudaStream_t st) {
+int batch_forward_step(BatchRun& r, cudaStream_t st) {
     GatherParams p = r.pf;
     p.with_stats = r.stats ? 1 : 0;
-    p.stats_out = r.stats ? r.B->d_stats + static_cast<int64_t>(it) * kNumStats : nullptr;
-    p.stats_frame_stride = static_cast<long long>(k + 1) * kNumStats;
     return batch_forward(r.P, r.B, p, st);
+}
+
+// The adjoint of iteration it; it first adds the frames' statistics of that
+// iteration's forward (one warp per frame; a separate launch when the batch
+// has more frames than the adjoint has warps).
+int batch_adjoint_step(BatchRun& r, int it, int k, cudaStream_t st) {
+    GatherParams p = r.pa;
+    const int tiles = static_cast<int>(r.P->fwd.tiles.size());
+    double* out = r.B->d_stats + static_cast<int64_t>(it) * kNumStats;
+    const long long stride = static_cast<long long>(k + 1) * kNumStats;
+    if (r.stats && r.B->F <= p.n_warps) {
+        p.red_src = r.B->d_tile_stats;
+        p.red_out = out;
+        p.red_tiles_per_frame = tiles;
+        p.red_frames = r.B->F;
+        p.red_frame_stride = stride;
+    } else if (r.stats) {
+        CTIS_CUDA(launch_stats_reduce(out, r.B->d_tile_stats, tiles, r.B->F, stride, st));
+    }
+    return batch_adjoint(r.P, r.B, p, st);
 }
 
 int batch_finish(BatchRun& r, int k, double* stats_dev, cudaStream_t st) {
@@ -1210,8 +1227,12 @@ int batch_finish(BatchRun& r, int k, double* stats_dev, cudaStream_t st) {
     CTIS_CUDA(launch_frames_copy0_out(P->dtype, B->d_ptrs + B->F, B->d_fwork, P->a_pitch,
                                       static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
                                       P->w, B->F, st));
-    if (r.stats)
+    if (r.stats) {   // the last forward's statistics, then every frame's rows to the caller
+        CTIS_CUDA(launch_stats_reduce(B->d_stats + static_cast<int64_t>(k) * kNumStats,
+                                      B->d_tile_stats, static_cast<int>(P->fwd.tiles.size()), B->F,
+                                      static_cast<long long>(k + 1) * kNumStats, st));
         CTIS_CUDA(launch_rows_scatter(stats_dev, B->d_stats, B->d_gid, (k + 1) * kNumStats, B->F, st));
+    }
     return CTIS_OK;
 }
 
@@ -1713,9 +1734,11 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     GatherParams pl = pf;
     pl.ratio_one_minus = 1;
     pl.with_stats = 1;
-    pl.stats_out = stats;
     rc = enqueue_forward(P, pl, st);             // 1 - g/q into the FPA copies
-    if (!rc) rc = adjoint_raw(gb);               // dL/df^(k) = H^T (1 - g/q)
+    if (rc) return rc;
+    CTIS_CUDA(launch_stats_reduce(stats, P->d_tile_stats, static_cast<int>(P->fwd.tiles.size()), 1,
+                                  0, st));
+    rc = adjoint_raw(gb);                        // dL/df^(k) = H^T (1 - g/q)
     if (!rc) rc = enqueue_psf_grad(P, ck(k), dval_dev, false, nullptr, st);
     if (rc) return rc;
     CTIS_CUDA(launch_negate(nll_dev, stats + CTIS_STAT_LOGLIK, st));
@@ -1831,10 +1854,10 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
         for (int it = 0; it <= k && !rc; ++it) {
             if (it == k && !stats_dev) break;
             for (BatchRun& r : runs)
-                if (!rc) rc = batch_forward_step(r, it, k, cs);
+                if (!rc) rc = batch_forward_step(r, cs);
             if (it == k) break;
             for (BatchRun& r : runs)
-                if (!rc) rc = batch_adjoint(r.P, r.B, r.pa, cs);
+                if (!rc) rc = batch_adjoint_step(r, it, k, cs);
         }
         for (BatchRun& r : runs)
             if (!rc) rc = batch_finish(r, k, stats_dev, cs);
@@ -1872,10 +1895,6 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
     drop_batched_graph_of(P);
     free_batch(P->batch);
     P->batch = nullptr;
-    if (!P->d_tune_stats) {
-        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tune_stats), sizeof(double) * kNumStats);
-        if (rc) return rc;
-    }
     // realistic operands: f = 1 in the datacube copies, g in the FPA copies
     rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
     if (!rc) rc = scatter_u(P, g_dev, st);
@@ -1924,8 +1943,7 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
             p.out_copies = P->u_copies;
             p.g = g_dev;
             p.g_pitch = P->gamma;
-            p.with_stats = 1;
-            p.stats_out = P->d_tune_stats;
+            p.with_stats = 1;   // tile statistics, as inside the EM loop
             return enqueue_forward(P, p, st);
         }
         GatherParams p = base_params(P, P->adj);
