@@ -239,8 +239,9 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
 
 /* Autotuner: for each projector, times the plan's EM launches (forward with
  * the ratio and statistics, adjoint with the update) over candidate work
- * schedules (cluster tasks per work item: the plan's model choice and
- * 6..64) on this GPU, with g_dev (n float32) as the measurement and f = 1,
+ * schedules (cluster tasks per work item, shared by a CTA's warps: the
+ * plan's model choice and 16..192) on this GPU, with g_dev (n float32) as the
+ * measurement and f = 1,
  * and keeps the fastest. Synchronous; overwrites the plan's internal copies
  * and drops its cached graphs (the next ctis_reconstruct re-captures).
  * Results stay deterministic for a given schedule but may differ in the last

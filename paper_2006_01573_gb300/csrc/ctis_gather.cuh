@@ -13,9 +13,10 @@
 // so results are bit-reproducible.
 //
 // GB300 mapping:
-//  * every warp is an independent persistent worker with a static list of
-//    work items (balanced longest-first on the host) whose tasks are stored
-//    contiguously: no work-fetch atomics, no block-wide barriers;
+//  * persistent CTAs with static item lists balanced longest-first on the
+//    host; the CTA's warps share each item's tasks and add their sums in
+//    shared memory (no work-fetch atomics, no global traffic for a tile that
+//    one CTA finishes);
 //  * lane 0 stages the input window of each task with tensor TMA
 //    (cp.async.bulk.tensor) and the task's weights with a bulk copy into one
 //    of NS shared-memory stages completed on an mbarrier, NS tasks ahead of
@@ -91,6 +92,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         }
     }
     return true;
+}
+
+// Barrier over the CTA's warps only (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void cta_barrier(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 // GPU-scope release/acquire fence (lighter than the sequentially consistent
@@ -194,7 +200,15 @@ struct Geo {
     static constexpr int TILE = TX * TY;
     static constexpr int THREADS = NW * 32;
     static constexpr int STAGES_BYTES = NW * NS * STAGE_BYTES;
-    static constexpr int SMEM_BYTES = STAGES_BYTES + NW * NS * 8;
+    // the CTA's tile reduction: NW - 1 partial tiles, then a flag word
+    static constexpr int RED_OFF = STAGES_BYTES;
+    static constexpr int RED_BYTES = (NW - 1) * TILE * 4;
+    static constexpr int FLAG_OFF = RED_OFF + RED_BYTES;
+    static constexpr int TSTAT_OFF = FLAG_OFF + 16;       // [NW][4] float64 tile statistics
+    static constexpr int BAR_OFF = TSTAT_OFF + NW * 4 * 8;
+    static constexpr int SMEM_BYTES = BAR_OFF + NW * NS * 8;
+    static constexpr int ER = R / NW;   // epilogue rows of each lane's block per warp
+    static_assert(R % NW == 0, "the epilogue splits a lane's rows evenly over the warps");
     // resident CTAs per SM the register budget must allow (4 x 4 warps = 16
     // warps per SM when the stages fit; the occupancy query has the last word)
     static constexpr int MIN_BLOCKS = (227 * 1024) / (SMEM_BYTES + 1024) >= 4 ? 4 : 1;
@@ -468,11 +482,12 @@ __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int 
     }
 }
 
-// Applies the epilogue MODE to the lane's outputs v[o][c] of the item's tile;
-// accumulates the forward statistics of the lane in stat[].
-template <class G, typename TF, int MODE>
+// Applies the epilogue MODE to ER of the lane's rows (rows o0 .. o0+ER-1 of
+// its block; v[o][c]) of the item's tile; accumulates the forward statistics
+// of the lane in stat[].
+template <class G, typename TF, int MODE, int ER>
 __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& it, int tx,
-                                         int ty, const float (&v)[G::R][G::C],
+                                         int ty, int o0, const float (&v)[ER][G::C],
                                          float (&stat)[kNumStats]) {
     constexpr int C = G::C;
     const int tile_cols = min(G::TX, p.out_w - it.x0);
@@ -484,8 +499,8 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
         rh = hs != 0.f ? 1.0f / hs : 0.f;
     }
 #pragma unroll
-    for (int o = 0; o < G::R; ++o) {
-        const int y = it.y0 + ty * G::R + o;
+    for (int o = 0; o < ER; ++o) {
+        const int y = it.y0 + ty * G::R + o0 + o;
         const bool row_ok = y < p.out_h;      // warp-divergent only at the bottom edge
         if constexpr (MODE == kEpiRaw) {
             if (!row_ok || n_valid <= 0) continue;
@@ -570,21 +585,35 @@ __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumSt
     d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
 }
 
-// Statistics of one finished tile: the warp's per-lane float32 sums (32
-// elements each) widened to float64 and added in a fixed tree; lane 0 stores
-// the tile's four values. The frame totals are added later, in tile order, by
+// Statistics of one finished tile: each warp's per-lane float32 sums (32
+// elements each) widened to float64 and added in a fixed tree, then the CTA's
+// warps' values added in warp order by warp 0, which stores the tile's four
+// values. The frame totals are added later, in tile order, by
 // reduce_frame_stats (at the start of the next launch in stream order), so no
 // fence or atomic sits on the tile's path.
+template <int NW, int THREADS>
 __device__ __forceinline__ void store_tile_stats(const GatherParams& p, int tile_idx,
-                                                 const float (&stat)[kNumStats], int lane) {
+                                                 const float (&stat)[kNumStats], int warp, int lane,
+                                                 double* tstat) {
     static_assert(kNumStats == 4, "statistics move as two double2");
     double tot[kNumStats];
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) tot[q] = warp_sum(static_cast<double>(stat[q]));
     if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kNumStats; ++q) tstat[warp * kNumStats + q] = tot[q];
+    }
+    cta_barrier(THREADS);
+    if (warp == 0 && lane == 0) {
+        double t[kNumStats];
+#pragma unroll
+        for (int q = 0; q < kNumStats; ++q) {
+            t[q] = tstat[q];
+            for (int w = 1; w < NW; ++w) t[q] += tstat[w * kNumStats + q];
+        }
         double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
-        __stcg(dst, make_double2(tot[0], tot[1]));
-        __stcg(dst + 1, make_double2(tot[2], tot[3]));
+        __stcg(dst, make_double2(t[0], t[1]));
+        __stcg(dst + 1, make_double2(t[2], t[3]));
     }
 }
 
@@ -595,11 +624,20 @@ __device__ __forceinline__ void reduce_frame_stats(const double* tile_stats, int
                                                    double* out, int lane) {
     const double* src = tile_stats + (long long)frame * tiles * kNumStats;
     double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-    for (int i0 = 0; i0 < tiles; i0 += 32) {
-        double e[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-        if (i0 + lane < tiles) load_stats(src + (long long)(i0 + lane) * kNumStats, e);
+    constexpr int B = 8;   // passes whose loads are issued together
+    for (int i0 = 0; i0 < tiles; i0 += 32 * B) {
+        double e[B][kNumStats];
 #pragma unroll
-        for (int q = 0; q < kNumStats; ++q) t[q] += e[q];
+        for (int b = 0; b < B; ++b) {
+            const int i = i0 + 32 * b + lane;
+#pragma unroll
+            for (int q = 0; q < kNumStats; ++q) e[b][q] = 0.0;
+            if (i < tiles) load_stats(src + (long long)i * kNumStats, e[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int q = 0; q < kNumStats; ++q) t[q] += e[b][q];
     }
 #pragma unroll
     for (int q = 0; q < kNumStats; ++q) t[q] = warp_sum(t[q]);
@@ -612,17 +650,21 @@ __device__ __forceinline__ void reduce_frame_stats(const double* tile_stats, int
 // ---------------------------------------------------------------------------
 // the kernel body (wrapped by forward_kernel / adjoint_kernel)
 // ---------------------------------------------------------------------------
-// Every warp owns a contiguous range of items (a static, longest-first
-// balanced list made on the host), and the tasks of those items are stored
-// contiguously in the same order, so the TMA issue cursor is a plain counter
-// over the warp's task range running NS tasks ahead of the compute loop,
-// across item boundaries. Only lane 0 reads task descriptors (it alone issues
-// the copies); it loads the next one right after each issue, so the load's
-// latency overlaps a task of compute.
+// The host balances work items (a tile, or a chunk of a long tile) over the
+// CTAs, longest first. The NW warps of a CTA walk parallel item lists: warp w
+// runs the w-th quarter of each item's tasks, then the warps add their sums
+// through shared memory (fixed order), a tile split over CTAs adds its chunks
+// through global memory in chunk order (the last chunk to arrive, by ticket),
+// and each warp applies the epilogue to its share of the tile's rows. Each
+// warp's tasks are stored contiguously, so its TMA issue cursor is a plain
+// counter running NS tasks ahead of the compute loop, across item boundaries.
+// Only lane 0 reads task descriptors (it alone issues the copies); it loads
+// the next one right after each issue, so the load's latency overlaps a task
+// of compute.
 template <class G, typename TIn, typename TF, int MODE>
 __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const GatherParams& p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + G::STAGES_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + G::BAR_OFF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * G::NW + warp;
@@ -680,8 +722,8 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         if constexpr (MODE == kEpiRatio || MODE == kEpiUpdate) {
             if (MODE == kEpiRatio || p.mode == kEpiUpdate) {
 #pragma unroll
-                for (int o = 0; o < G::R; ++o) {
-                    const int y = it.y0 + ty * G::R + o;
+                for (int o = 0; o < G::ER; ++o) {
+                    const int y = it.y0 + ty * G::R + warp * G::ER + o;
                     const int x = it.x0 + tx * G::C;
                     if (y < p.out_h && x < p.out_w) {
                         const void* src =
@@ -769,77 +811,124 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
 
         if constexpr (MODE == kEpiGrad) continue;   // every task wrote its own sums
 
-        float v[G::R][G::C];
-#pragma unroll
-        for (int o = 0; o < G::R; ++o)
-#pragma unroll
-            for (int c = 0; c < G::C / 2; ++c) {
-                v[o][2 * c] = acc[o][c].x;
-                v[o][2 * c + 1] = acc[o][c].y;
-            }
-
-        const int nchunks = it.chunk_info & 0xffff;
-        const int chunk = it.chunk_info >> 16;
-        bool finish = true;
-        if (nchunks > 1) {
-            float* slots = p.scratch + (long long)it.scratch_base * G::TILE;
-            float* mine = slots + (long long)chunk * G::TILE;
+        // The CTA's warps ran disjoint parts of this item's tasks: add their
+        // sums through shared memory in warp order, ((p0 + p1) + p2) + p3.
+        float* red = reinterpret_cast<float*>(smem_raw + G::RED_OFF);
+        int* flag = reinterpret_cast<int*>(smem_raw + G::FLAG_OFF);
+        if (warp != 0) {
+            float* mine = red + (warp - 1) * G::TILE;
 #pragma unroll
             for (int o = 0; o < G::R; ++o)
 #pragma unroll
                 for (int c = 0; c < G::C; c += 4)
-                    __stcg(reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)),
-                           make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]));
-            // publish the partial sums (release), then take the tile's ticket
-            fence_acq_rel_gpu();
-            __syncwarp();
-            int old = 0;
-            if (lane == 0) old = atomicAdd(&p.tickets[it.tile], 1);
-            old = __shfl_sync(0xffffffffu, old, 0);
-            finish = old == nchunks - 1;
-            if (finish) {
-                fence_acq_rel_gpu();   // acquire the other chunks' sums
-                // add every chunk's stored sums in chunk order; each pass
-                // issues a whole chunk's loads at once (one L2 round trip per
-                // chunk rather than one per chunk and row)
-                constexpr int NV = G::R * G::C / 4;
-                float4 sum[NV];
+                    *reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)) =
+                        make_float4(acc[o][c / 2].x, acc[o][c / 2].y, acc[o][c / 2 + 1].x,
+                                    acc[o][c / 2 + 1].y);
+        }
+        cta_barrier(G::THREADS);
+        if (warp == 0) {
+            float v[G::R][G::C];
+#pragma unroll
+            for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                for (int c = 0; c < G::C; c += 4) {
+                    float4 s4 = make_float4(acc[o][c / 2].x, acc[o][c / 2].y, acc[o][c / 2 + 1].x,
+                                            acc[o][c / 2 + 1].y);
+#pragma unroll
+                    for (int w = 1; w < G::NW; ++w) {
+                        const float4 q4 = *reinterpret_cast<const float4*>(
+                            red + (w - 1) * G::TILE + tile_elem<G>(tx, ty, o, c));
+                        s4.x += q4.x; s4.y += q4.y; s4.z += q4.z; s4.w += q4.w;
+                    }
+                    v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
+                }
+            // Tiles longer than one item are split over CTAs: chunk sums go
+            // through global memory and the last chunk adds them in order.
+            const int nchunks = it.chunk_info & 0xffff;
+            const int chunk = it.chunk_info >> 16;
+            bool finish = true;
+            if (nchunks > 1) {
+                float* slots = p.scratch + (long long)it.scratch_base * G::TILE;
+                float* mine = slots + (long long)chunk * G::TILE;
 #pragma unroll
                 for (int o = 0; o < G::R; ++o)
 #pragma unroll
                     for (int c = 0; c < G::C; c += 4)
-                        sum[(o * G::C + c) / 4] =
-                            __ldcg(reinterpret_cast<const float4*>(slots + tile_elem<G>(tx, ty, o, c)));
-#pragma unroll 1
-                for (int ch = 1; ch < nchunks; ++ch) {
-                    float4 q4[NV];
+                        __stcg(reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)),
+                               make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]));
+                fence_acq_rel_gpu();   // publish the chunk's sums (release)
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(&p.tickets[it.tile], 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                finish = old == nchunks - 1;
+                if (finish) {
+                    fence_acq_rel_gpu();   // acquire the other chunks' sums
+                    constexpr int NV = G::R * G::C / 4;
+                    float4 sum[NV];
 #pragma unroll
                     for (int o = 0; o < G::R; ++o)
 #pragma unroll
                         for (int c = 0; c < G::C; c += 4)
-                            q4[(o * G::C + c) / 4] = __ldcg(reinterpret_cast<const float4*>(
-                                slots + (long long)ch * G::TILE + tile_elem<G>(tx, ty, o, c)));
+                            sum[(o * G::C + c) / 4] = __ldcg(
+                                reinterpret_cast<const float4*>(slots + tile_elem<G>(tx, ty, o, c)));
+#pragma unroll 1
+                    for (int ch = 1; ch < nchunks; ++ch) {
+                        float4 q4[NV];
 #pragma unroll
-                    for (int k = 0; k < NV; ++k) {
-                        sum[k].x += q4[k].x; sum[k].y += q4[k].y;
-                        sum[k].z += q4[k].z; sum[k].w += q4[k].w;
+                        for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                            for (int c = 0; c < G::C; c += 4)
+                                q4[(o * G::C + c) / 4] = __ldcg(reinterpret_cast<const float4*>(
+                                    slots + (long long)ch * G::TILE + tile_elem<G>(tx, ty, o, c)));
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) {
+                            sum[q].x += q4[q].x; sum[q].y += q4[q].y;
+                            sum[q].z += q4[q].z; sum[q].w += q4[q].w;
+                        }
                     }
+#pragma unroll
+                    for (int o = 0; o < G::R; ++o)
+#pragma unroll
+                        for (int c = 0; c < G::C; c += 4) {
+                            const float4 s4 = sum[(o * G::C + c) / 4];
+                            v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
+                        }
+                    if (lane == 0) p.tickets[it.tile] = 0;
                 }
+            }
+            if (finish) {   // the tile's total, for every warp's epilogue rows
 #pragma unroll
                 for (int o = 0; o < G::R; ++o)
 #pragma unroll
-                    for (int c = 0; c < G::C; c += 4) {
-                        const float4 s4 = sum[(o * G::C + c) / 4];
-                        v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
-                    }
-                if (lane == 0) p.tickets[it.tile] = 0;
+                    for (int c = 0; c < G::C; c += 4)
+                        *reinterpret_cast<float4*>(red + tile_elem<G>(tx, ty, o, c)) =
+                            make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]);
             }
+            if (lane == 0) *flag = finish ? 1 : 0;
         }
+        cta_barrier(G::THREADS);
+        const bool finish = *flag != 0;
+        float ve[G::ER][G::C];
+        if (finish) {
+#pragma unroll
+            for (int o = 0; o < G::ER; ++o)
+#pragma unroll
+                for (int c = 0; c < G::C; c += 4) {
+                    const float4 s4 = *reinterpret_cast<const float4*>(
+                        red + tile_elem<G>(tx, ty, warp * G::ER + o, c));
+                    ve[o][c] = s4.x; ve[o][c + 1] = s4.y; ve[o][c + 2] = s4.z; ve[o][c + 3] = s4.w;
+                }
+        }
+        cta_barrier(G::THREADS);   // the buffer is free for the next item
         if (finish) {
             float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
-            epilogue<G, TF, MODE>(p, it, tx, ty, v, stat);
+            epilogue<G, TF, MODE, G::ER>(p, it, tx, ty, warp * G::ER, ve, stat);
             if constexpr (MODE == kEpiRatio) {
-                if (p.with_stats) store_tile_stats(p, it.tile, stat, lane);
+                if (p.with_stats)   // uniform over the launch: every warp takes the barrier
+                    store_tile_stats<G::NW, G::THREADS>(
+                        p, it.tile, stat, warp, lane,
+                        reinterpret_cast<double*>(smem_raw + G::TSTAT_OFF));
             }
         }
     }

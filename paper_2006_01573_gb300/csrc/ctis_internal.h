@@ -8,10 +8,9 @@
 //   adjoint  (Eq. 14):      output = voxel tile of wavelength s, input windows
 //            from the FPA vector r, weights as stored (a correlation).
 // Tiles with more tasks than one item holds are split into chunks whose
-// partial sums are added, in chunk order, by the last chunk to finish.
-// Every warp is an independent worker with a static list of items, balanced
-// longest-first on the host, so the kernels need no work-fetch atomics and
-// no block-wide barriers.
+// partial sums are added, in chunk order, by the last chunk to finish. Items
+// are balanced longest-first over persistent CTAs; the warps of a CTA share
+// each item's tasks and add their sums in shared memory.
 #pragma once
 
 #include <cstdint>
@@ -37,8 +36,9 @@ struct ItemDesc {        // 16 bytes (host-side bookkeeping)
     int task_end;
 };
 
-// One work item as a warp reads it: everything it needs in a single 32-byte
-// load, stored in the order the warp processes its items.
+// One work item as a warp reads it (its share of the item's tasks):
+// everything it needs in a single 32-byte load, stored in the order the warp
+// processes its items.
 struct WorkItem {
     int tile, x0, y0, plane;
     int chunk_info;      // nchunks | (chunk << 16)
@@ -122,7 +122,7 @@ struct GatherShape {
     int C;    // columns per lane
     int R;    // rows per lane
     int LX;   // lanes along x (32 / LX along y)
-    int NW;   // warps per CTA (independent workers; they share nothing)
+    int NW;   // warps per CTA (they share each item's tasks)
     int NS;   // TMA stages per warp
 };
 

@@ -87,13 +87,15 @@ struct ProjTables {
     std::vector<TaskDesc> tile_tasks;       // tile order, the input of schedule()
     std::vector<int> tile_task_begin;       // [tiles + 1]
     std::vector<int> warp_begin;   // [n_warps + 1]
-    std::vector<int> warp_items;   // item indices, grouped by warp
+    std::vector<int> cta_begin;    // [CTAs + 1]
+    std::vector<int> cta_items;    // item indices, grouped by CTA
+    int nw = 4;                    // warps per CTA of the projector's kernel
     std::vector<WorkItem> witems;  // the items in warp order, as the kernel reads them
     int tile_w = 0, tile_h = 0;
     int64_t scratch_slots = 0;
     int per_item = 0;              // chunk size chosen for this table
     int n_warps = 0;
-    double max_warp_load = 0.0;    // LPT estimate of the busiest warp, task units
+    double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
     int* d_warp_begin = nullptr;
     WorkItem* d_witems = nullptr;
@@ -246,11 +248,13 @@ void destroy(ctis_plan* P) {
     delete P;
 }
 
-// Cost of an item in task units: its tasks, plus the partial-sum store,
-// fence, ticket and (for the last chunk) the reduction of a chunked tile,
-// plus the epilogue. The chunk overhead is the measured cost on GB300 of the
-// realistic workload's chunked items, about four tasks' worth.
-double item_cost(int tasks, bool chunked) { return tasks + (chunked ? 4.0 : 0.0) + 0.5; }
+// Cost of an item in tasks per warp: the CTA's warps share its tasks, then
+// add their sums in shared memory and split the epilogue (about half a task),
+// and a tile split over CTAs pays the chunk sums' round trip through global
+// memory (about a task and a half).
+double item_cost(int tasks, int nw, bool chunked) {
+    return (tasks + nw - 1) / nw + (chunked ? 1.5 : 0.0) + 0.5;
+}
 
 // Splits every tile's task range into chunks of at most `per_item` tasks and
 // fills the item list and the scratch slot bases.
@@ -278,88 +282,100 @@ void make_items(ProjTables& T, const std::vector<int>& tile_task_begin, int per_
     }
 }
 
-// Longest-processing-time-first assignment of the items to n_warps warps.
-// Returns the load of the busiest warp; fills warp_begin / warp_items.
-double assign_warps(ProjTables& T, int n_warps) {
+// Longest-processing-time-first assignment of the items to n_ctas CTAs.
+// Returns the load of the busiest CTA (tasks per warp); fills cta_begin /
+// cta_items.
+double assign_ctas(ProjTables& T, int n_ctas) {
     std::vector<int> order(T.items.size());
     std::iota(order.begin(), order.end(), 0);
     auto cost = [&](int i) {
         const ItemDesc& it = T.items[i];
-        return item_cost(it.task_end - it.task_begin, T.tiles[it.tile].nchunks > 1);
+        return item_cost(it.task_end - it.task_begin, T.nw, T.tiles[it.tile].nchunks > 1);
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    using Slot = std::pair<double, int>;   // (load, warp)
+    using Slot = std::pair<double, int>;   // (load, CTA)
     std::vector<Slot> heap;
-    heap.reserve(n_warps);
-    for (int w = 0; w < n_warps; ++w) heap.emplace_back(0.0, w);
+    heap.reserve(n_ctas);
+    for (int c = 0; c < n_ctas; ++c) heap.emplace_back(0.0, c);
     auto cmp = [](const Slot& x, const Slot& y) {
         return x.first != y.first ? x.first > y.first : x.second > y.second;
     };
     std::make_heap(heap.begin(), heap.end(), cmp);
-    std::vector<std::vector<int>> per_warp(n_warps);
+    std::vector<std::vector<int>> per_cta(n_ctas);
     double max_load = 0.0;
     for (int i : order) {
         std::pop_heap(heap.begin(), heap.end(), cmp);
         Slot& sl = heap.back();
-        per_warp[sl.second].push_back(i);
+        per_cta[sl.second].push_back(i);
         sl.first += cost(i);
         max_load = std::max(max_load, sl.first);
         std::push_heap(heap.begin(), heap.end(), cmp);
     }
-    T.warp_begin.assign(1, 0);
-    T.warp_items.clear();
-    for (int w = 0; w < n_warps; ++w) {
-        T.warp_items.insert(T.warp_items.end(), per_warp[w].begin(), per_warp[w].end());
-        T.warp_begin.push_back(static_cast<int>(T.warp_items.size()));
+    T.cta_begin.assign(1, 0);
+    T.cta_items.clear();
+    for (int c = 0; c < n_ctas; ++c) {
+        T.cta_items.insert(T.cta_items.end(), per_cta[c].begin(), per_cta[c].end());
+        T.cta_begin.push_back(static_cast<int>(T.cta_items.size()));
     }
     return max_load;
 }
 
-// Picks the chunk size that minimises the LPT estimate of the busiest warp
-// (ties: the larger chunk, i.e. fewer partial sums), or uses `forced` > 0.
+// Picks the item size (cluster tasks per CTA item) that minimises the LPT
+// estimate of the busiest CTA (ties: the larger, i.e. fewer partial sums), or
+// uses `forced` > 0. Then lays out, for every warp, its part of each of its
+// CTA's items: warp w of a CTA runs tasks [b + w*n/NW, b + (w+1)*n/NW) of an
+// item of n tasks; the warps' item lists are parallel (same tiles, same
+// order) and every warp's tasks are stored contiguously.
 void schedule(ProjTables& T, int n_warps, int forced) {
     const std::vector<int>& begin = T.tile_task_begin;
-    T.n_warps = n_warps;
+    const int nw = T.nw;
+    const int n_ctas = n_warps / nw;
+    T.n_warps = n_ctas * nw;
     std::vector<int> cands;
     if (forced > 0) {
         cands.push_back(forced);
     } else {
-        for (int c : {64, 48, 32, 24, 16, 13, 12, 10, 9, 8, 7, 6, 5, 4}) cands.push_back(c);
+        for (int c : {256, 192, 128, 96, 64, 48, 32, 24, 16, 12, 8}) cands.push_back(c);
     }
     int best = cands[0];
     double best_load = -1.0;
     for (int c : cands) {
         make_items(T, begin, c);
-        const double load = assign_warps(T, n_warps);
+        const double load = assign_ctas(T, n_ctas);
         if (best_load < 0 || load < best_load - 1e-9) {
             best_load = load;
             best = c;
         }
     }
     make_items(T, begin, best);
-    T.max_warp_load = assign_warps(T, n_warps);
+    T.max_warp_load = assign_ctas(T, n_ctas);
     T.per_item = best;
-    // the kernel's view: items in warp order, and their tasks stored in the
-    // same order, so every warp's tasks form one contiguous range
     T.witems.clear();
+    T.warp_begin.assign(1, 0);
     std::vector<TaskDesc> wt;
     wt.reserve(T.tile_tasks.size());
-    for (int i : T.warp_items) {
-        const ItemDesc& it = T.items[i];
-        const TileDesc& td = T.tiles[it.tile];
-        WorkItem w;
-        w.tile = it.tile;
-        w.x0 = td.x0;
-        w.y0 = td.y0;
-        w.plane = td.plane;
-        w.chunk_info = td.nchunks | (it.chunk << 16);
-        w.scratch_base = td.scratch_base;
-        w.task_begin = static_cast<int>(wt.size());
-        wt.insert(wt.end(), T.tile_tasks.begin() + it.task_begin,
-                  T.tile_tasks.begin() + it.task_end);
-        w.task_end = static_cast<int>(wt.size());
-        T.witems.push_back(w);
-    }
+    for (int c = 0; c < n_ctas; ++c)
+        for (int w = 0; w < nw; ++w) {
+            for (int k = T.cta_begin[c]; k < T.cta_begin[c + 1]; ++k) {
+                const ItemDesc& it = T.items[T.cta_items[k]];
+                const TileDesc& td = T.tiles[it.tile];
+                const int n = it.task_end - it.task_begin;
+                const int tb = it.task_begin + static_cast<int>(static_cast<int64_t>(n) * w / nw);
+                const int te = it.task_begin + static_cast<int>(static_cast<int64_t>(n) * (w + 1) / nw);
+                WorkItem wi;
+                wi.tile = it.tile;
+                wi.x0 = td.x0;
+                wi.y0 = td.y0;
+                wi.plane = td.plane;
+                wi.chunk_info = td.nchunks | (it.chunk << 16);
+                wi.scratch_base = td.scratch_base;
+                wi.task_begin = static_cast<int>(wt.size());
+                wt.insert(wt.end(), T.tile_tasks.begin() + tb, T.tile_tasks.begin() + te);
+                wi.task_end = static_cast<int>(wt.size());
+                T.witems.push_back(wi);
+            }
+            T.warp_begin.push_back(static_cast<int>(T.witems.size()));
+        }
     T.tasks = std::move(wt);
 }
 
@@ -596,6 +612,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     {
         ProjTables& T = P->fwd;
         const int TX = T.tile_w = gather_tile_w(true, P->dtype), TY = T.tile_h = gather_tile_h(true, P->dtype);
+        T.nw = gather_warps_per_cta(true);
         const int ntx = (ga + TX - 1) / TX, nty = (xi + TY - 1) / TY;
         const int fw = a + K - 1, fh = al + K - 1;   // footprint of one cluster
         std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
@@ -639,6 +656,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     {
         ProjTables& T = P->adj;
         const int TX = T.tile_w = gather_tile_w(false, P->dtype), TY = T.tile_h = gather_tile_h(false, P->dtype);
+        T.nw = gather_warps_per_cta(false);
         std::vector<int64_t> c_begin(w + 1, 0);
         for (int64_t c = 0; c < ncl; ++c) c_begin[P->clusters[c].s + 1]++;
         for (int s = 0; s < w; ++s) c_begin[s + 1] += c_begin[s];
@@ -1953,7 +1971,7 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
         set_f_copies(P, p);
         return enqueue_adjoint(P, p, st);
     };
-    const int cands[] = {0, 6, 8, 12, 16, 24, 32, 48, 64};
+    const int cands[] = {0, 16, 24, 32, 48, 64, 96, 128, 192};
     int result = CTIS_OK;
     for (ProjTables* T : {&P->fwd, &P->adj}) {
         const bool forward = T == &P->fwd;

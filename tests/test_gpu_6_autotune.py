@@ -13,7 +13,7 @@ from tests.helpers import floored_rel, problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-CANDIDATES = {6, 8, 12, 16, 24, 32, 48, 64}
+CANDIDATES = {16, 24, 32, 48, 64, 96, 128, 192}
 
 
 @pytest.fixture(scope="module", autouse=True)
