@@ -483,12 +483,13 @@ __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int 
 }
 
 // Applies the epilogue MODE to ER of the lane's rows (rows o0 .. o0+ER-1 of
-// its block; v[o][c]) of the item's tile; accumulates the forward statistics
-// of the lane in stat[].
+// its block; v[o][c]) of the item's tile, with the rows' inputs ein (g for
+// the ratio, f for the update) already loaded; accumulates the forward
+// statistics of the lane in stat[].
 template <class G, typename TF, int MODE, int ER>
 __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& it, int tx,
                                          int ty, int o0, const float (&v)[ER][G::C],
-                                         float (&stat)[kNumStats]) {
+                                         const float (&ein)[ER][G::C], float (&stat)[kNumStats]) {
     constexpr int C = G::C;
     const int tile_cols = min(G::TX, p.out_w - it.x0);
     const int col0 = tx * C;
@@ -519,11 +520,8 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
                 for (int c = 0; c < C && c < n_valid; ++c) dst[c] = v[o][c];
             }
         } else if constexpr (MODE == kEpiRatio) {
-            float gv[C], u[C];
-            const float* gp = p.g + it.plane * p.g_plane_stride + (long long)(row_ok ? y : 0) * p.g_pitch +
-                              it.x0 + col0;
-            load_row<float, C>(gp, row_ok ? n_valid : 0,
-                               (p.g_pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(gp) & 15) == 0, gv);
+            float u[C];
+            const float (&gv)[C] = ein[o];   // g of this row (loaded by the caller)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float val = v[o][c];
@@ -556,12 +554,9 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
             const long long rowoff = it.plane * p.f_plane_stride +
                                      (long long)(row_ok ? y : 0) * p.f_pitch + it.x0;
             float fv[C];
-            if (p.mode == kEpiUpdate) {
-                float fi[C];
-                load_row<TF, C>(static_cast<const TF*>(p.f_in) + rowoff + col0,
-                                row_ok ? n_valid : 0, true, fi);
+            if (p.mode == kEpiUpdate) {   // ein: f_in of this row (loaded by the caller)
 #pragma unroll
-                for (int c = 0; c < C; ++c) fv[c] = fi[c] * v[o][c] * rh;
+                for (int c = 0; c < C; ++c) fv[c] = ein[o][c] * v[o][c] * rh;
             } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) fv[c] = v[o][c];
@@ -811,119 +806,124 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
 
         if constexpr (MODE == kEpiGrad) continue;   // every task wrote its own sums
 
-        // The CTA's warps ran disjoint parts of this item's tasks: add their
-        // sums through shared memory in warp order, ((p0 + p1) + p2) + p3.
-        float* red = reinterpret_cast<float*>(smem_raw + G::RED_OFF);
-        int* flag = reinterpret_cast<int*>(smem_raw + G::FLAG_OFF);
-        if (warp != 0) {
-            float* mine = red + (warp - 1) * G::TILE;
+        // The CTA's warps ran disjoint parts of this item's tasks. Warp d
+        // finalises rows d*ER .. d*ER+ER-1 of every lane's block: each warp
+        // publishes in shared memory the rows the other warps finalise, and
+        // each warp adds its rows over the warps in order, p0 + p1 + p2 + p3.
+        constexpr int NW = G::NW, ER = G::ER, C = G::C;
+        float* pub = reinterpret_cast<float*>(smem_raw + G::RED_OFF);
+        auto pub_at = [&](int w, int d, int o) {   // warp w's copy of warp d's row o
+            const int slot = d < w ? d : d - 1;
+            return pub + (((w * (NW - 1) + slot) * ER + o) * 32 + lane) * C;
+        };
+        // this warp's epilogue inputs, loaded now so their latency overlaps
+        // the reduction (rows beyond the plane read as zero and are not used)
+        float ein[ER][C];
+        if constexpr (MODE == kEpiRatio || MODE == kEpiUpdate) {
+            const int tile_cols = min(G::TX, p.out_w - it.x0);
+            const int n_valid = tile_cols - tx * C;
 #pragma unroll
-            for (int o = 0; o < G::R; ++o)
+            for (int o = 0; o < ER; ++o) {
+                const int y = it.y0 + ty * G::R + warp * ER + o;
+                const bool row_ok = y < p.out_h;
+                if constexpr (MODE == kEpiRatio) {
+                    const float* gp = p.g + it.plane * p.g_plane_stride +
+                                      (long long)(row_ok ? y : 0) * p.g_pitch + it.x0 + tx * C;
+                    load_row<float, C>(gp, row_ok ? n_valid : 0,
+                                       (p.g_pitch % 4) == 0 && (reinterpret_cast<uintptr_t>(gp) & 15) == 0,
+                                       ein[o]);
+                } else {
+                    if (p.mode == kEpiUpdate) {
+                        const long long rowoff = it.plane * p.f_plane_stride +
+                                                 (long long)(row_ok ? y : 0) * p.f_pitch + it.x0;
+                        load_row<TF, C>(static_cast<const TF*>(p.f_in) + rowoff + tx * C,
+                                        row_ok ? n_valid : 0, true, ein[o]);
+                    }
+                }
+            }
+        }
 #pragma unroll
-                for (int c = 0; c < G::C; c += 4)
-                    *reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)) =
-                        make_float4(acc[o][c / 2].x, acc[o][c / 2].y, acc[o][c / 2 + 1].x,
-                                    acc[o][c / 2 + 1].y);
+        for (int d = 0; d < NW; ++d) {
+            if (d == warp) continue;
+#pragma unroll
+            for (int o = 0; o < ER; ++o) {
+                float row[C];
+#pragma unroll
+                for (int c = 0; c < C / 2; ++c) {
+                    row[2 * c] = acc[d * ER + o][c].x;
+                    row[2 * c + 1] = acc[d * ER + o][c].y;
+                }
+                Vec<float, C>::store(pub_at(warp, d, o), row);
+            }
         }
         cta_barrier(G::THREADS);
-        if (warp == 0) {
-            float v[G::R][G::C];
+        float ve[ER][C];
 #pragma unroll
-            for (int o = 0; o < G::R; ++o)
+        for (int o = 0; o < ER; ++o) {
 #pragma unroll
-                for (int c = 0; c < G::C; c += 4) {
-                    float4 s4 = make_float4(acc[o][c / 2].x, acc[o][c / 2].y, acc[o][c / 2 + 1].x,
-                                            acc[o][c / 2 + 1].y);
+            for (int w = 0; w < NW; ++w) {
+                float row[C];
+                if (w == warp) {
 #pragma unroll
-                    for (int w = 1; w < G::NW; ++w) {
-                        const float4 q4 = *reinterpret_cast<const float4*>(
-                            red + (w - 1) * G::TILE + tile_elem<G>(tx, ty, o, c));
-                        s4.x += q4.x; s4.y += q4.y; s4.z += q4.z; s4.w += q4.w;
+                    for (int c = 0; c < C / 2; ++c) {
+                        row[2 * c] = acc[warp * ER + o][c].x;
+                        row[2 * c + 1] = acc[warp * ER + o][c].y;
                     }
-                    v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
+                } else {
+                    Vec<float, C>::load(pub_at(w, warp, o), row);
                 }
-            // Tiles longer than one item are split over CTAs: chunk sums go
-            // through global memory and the last chunk adds them in order.
-            const int nchunks = it.chunk_info & 0xffff;
+#pragma unroll
+                for (int c = 0; c < C; ++c) ve[o][c] = w == 0 ? row[c] : ve[o][c] + row[c];
+            }
+        }
+        cta_barrier(G::THREADS);   // the published rows are free for the next item
+
+        // Tiles longer than one item are split over CTAs: chunk sums go
+        // through global memory, each warp its own rows, and the last chunk
+        // to arrive (one ticket per chunk) adds them in chunk order.
+        const int nchunks = it.chunk_info & 0xffff;
+        bool finish = true;
+        if (nchunks > 1) {
             const int chunk = it.chunk_info >> 16;
-            bool finish = true;
-            if (nchunks > 1) {
-                float* slots = p.scratch + (long long)it.scratch_base * G::TILE;
-                float* mine = slots + (long long)chunk * G::TILE;
+            float* slots = p.scratch + (long long)it.scratch_base * G::TILE;
 #pragma unroll
-                for (int o = 0; o < G::R; ++o)
+            for (int o = 0; o < ER; ++o)
 #pragma unroll
-                    for (int c = 0; c < G::C; c += 4)
-                        __stcg(reinterpret_cast<float4*>(mine + tile_elem<G>(tx, ty, o, c)),
-                               make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]));
-                fence_acq_rel_gpu();   // publish the chunk's sums (release)
-                __syncwarp();
-                int old = 0;
-                if (lane == 0) old = atomicAdd(&p.tickets[it.tile], 1);
-                old = __shfl_sync(0xffffffffu, old, 0);
-                finish = old == nchunks - 1;
-                if (finish) {
-                    fence_acq_rel_gpu();   // acquire the other chunks' sums
-                    constexpr int NV = G::R * G::C / 4;
-                    float4 sum[NV];
+                for (int c = 0; c < C; c += 4)
+                    __stcg(reinterpret_cast<float4*>(slots + (long long)chunk * G::TILE +
+                                                     tile_elem<G>(tx, ty, warp * ER + o, c)),
+                           make_float4(ve[o][c], ve[o][c + 1], ve[o][c + 2], ve[o][c + 3]));
+            fence_acq_rel_gpu();   // publish this warp's rows (release)
+            cta_barrier(G::THREADS);
+            int* flag = reinterpret_cast<int*>(smem_raw + G::FLAG_OFF);
+            if (warp == 0 && lane == 0) {   // release every warp's rows, then the ticket
+                fence_acq_rel_gpu();
+                *flag = atomicAdd(&p.tickets[it.tile], 1) == nchunks - 1 ? 1 : 0;
+            }
+            cta_barrier(G::THREADS);
+            finish = *flag != 0;
+            cta_barrier(G::THREADS);   // the flag is free for the next item
+            if (finish) {
+                fence_acq_rel_gpu();   // acquire the other chunks' sums
 #pragma unroll
-                    for (int o = 0; o < G::R; ++o)
+                for (int o = 0; o < ER; ++o)
 #pragma unroll
-                        for (int c = 0; c < G::C; c += 4)
-                            sum[(o * G::C + c) / 4] = __ldcg(
-                                reinterpret_cast<const float4*>(slots + tile_elem<G>(tx, ty, o, c)));
-#pragma unroll 1
-                    for (int ch = 1; ch < nchunks; ++ch) {
-                        float4 q4[NV];
-#pragma unroll
-                        for (int o = 0; o < G::R; ++o)
-#pragma unroll
-                            for (int c = 0; c < G::C; c += 4)
-                                q4[(o * G::C + c) / 4] = __ldcg(reinterpret_cast<const float4*>(
-                                    slots + (long long)ch * G::TILE + tile_elem<G>(tx, ty, o, c)));
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) {
-                            sum[q].x += q4[q].x; sum[q].y += q4[q].y;
-                            sum[q].z += q4[q].z; sum[q].w += q4[q].w;
+                    for (int c = 0; c < C; c += 4) {
+                        const int e = tile_elem<G>(tx, ty, warp * ER + o, c);
+                        float4 s4 = __ldcg(reinterpret_cast<const float4*>(slots + e));
+                        for (int ch = 1; ch < nchunks; ++ch) {
+                            const float4 q4 = __ldcg(
+                                reinterpret_cast<const float4*>(slots + (long long)ch * G::TILE + e));
+                            s4.x += q4.x; s4.y += q4.y; s4.z += q4.z; s4.w += q4.w;
                         }
+                        ve[o][c] = s4.x; ve[o][c + 1] = s4.y; ve[o][c + 2] = s4.z; ve[o][c + 3] = s4.w;
                     }
-#pragma unroll
-                    for (int o = 0; o < G::R; ++o)
-#pragma unroll
-                        for (int c = 0; c < G::C; c += 4) {
-                            const float4 s4 = sum[(o * G::C + c) / 4];
-                            v[o][c] = s4.x; v[o][c + 1] = s4.y; v[o][c + 2] = s4.z; v[o][c + 3] = s4.w;
-                        }
-                    if (lane == 0) p.tickets[it.tile] = 0;
-                }
+                if (warp == 0 && lane == 0) p.tickets[it.tile] = 0;
             }
-            if (finish) {   // the tile's total, for every warp's epilogue rows
-#pragma unroll
-                for (int o = 0; o < G::R; ++o)
-#pragma unroll
-                    for (int c = 0; c < G::C; c += 4)
-                        *reinterpret_cast<float4*>(red + tile_elem<G>(tx, ty, o, c)) =
-                            make_float4(v[o][c], v[o][c + 1], v[o][c + 2], v[o][c + 3]);
-            }
-            if (lane == 0) *flag = finish ? 1 : 0;
         }
-        cta_barrier(G::THREADS);
-        const bool finish = *flag != 0;
-        float ve[G::ER][G::C];
-        if (finish) {
-#pragma unroll
-            for (int o = 0; o < G::ER; ++o)
-#pragma unroll
-                for (int c = 0; c < G::C; c += 4) {
-                    const float4 s4 = *reinterpret_cast<const float4*>(
-                        red + tile_elem<G>(tx, ty, warp * G::ER + o, c));
-                    ve[o][c] = s4.x; ve[o][c + 1] = s4.y; ve[o][c + 2] = s4.z; ve[o][c + 3] = s4.w;
-                }
-        }
-        cta_barrier(G::THREADS);   // the buffer is free for the next item
         if (finish) {
             float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
-            epilogue<G, TF, MODE, G::ER>(p, it, tx, ty, warp * G::ER, ve, stat);
+            epilogue<G, TF, MODE, ER>(p, it, tx, ty, warp * ER, ve, ein, stat);
             if constexpr (MODE == kEpiRatio) {
                 if (p.with_stats)   // uniform over the launch: every warp takes the barrier
                     store_tile_stats<G::NW, G::THREADS>(
