@@ -31,6 +31,14 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # 80.5 TFLOP/s
 L2_FLUSH_BYTES = 256 << 20
 
 
+
+def schedule_name(sched):
+    """("chunk", n) -> "chunks of <= n tasks, longest first"; ("split", q) -> the balanced split."""
+    kind, v = sched
+    if kind == "split":
+        return f"balanced split, item overhead {v / 4:g} tasks"
+    return f"chunks of <= {v} tasks, longest first"
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +381,7 @@ def run_ours(args, wl, k):
                    "voxels": wl.m, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "stats": "float64 flux/loglik/resid per iteration",
-                   "schedule": {"tasks_per_item_fwd": tuned[0], "tasks_per_item_adj": tuned[1],
+                   "schedule": {"forward": schedule_name(tuned[0]), "adjoint": schedule_name(tuned[1]),
                                 "chosen_by": "ctis_plan_autotune"}},
         "voxel_updates_per_s": value * wl.m,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,

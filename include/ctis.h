@@ -91,10 +91,15 @@ int ctis_plan_create(ctis_plan** out, int a, int alpha, int w, int gamma, int xi
 /* Optional plan settings (zero-initialise, set struct_size). */
 typedef struct {
     int struct_size;       /* sizeof(ctis_plan_options)                         */
-    int tasks_per_item;    /* cluster tasks per work item; 0 = chosen by the plan
-                              (the chunk size whose simulated longest-first
-                              schedule over the GPU's warps finishes first)     */
-    int reserved[6];       /* must be 0                                          */
+    int tasks_per_item;    /* > 0: tiles cut into work items of at most this many
+                              cluster tasks, assigned to CTAs longest first     */
+    int item_overhead_q;   /* > 0: balanced split: the tiles' tasks, in tile
+                              order, cut into one run of equal estimated cost
+                              per CTA, with a per-item overhead of this many
+                              quarter tasks. Exclusive with tasks_per_item;
+                              both 0 = the candidate with the smallest
+                              estimated busiest CTA                             */
+    int reserved[5];       /* must be 0                                          */
 } ctis_plan_options;
 
 /* ctis_plan_create with options; opt may be NULL (all defaults). */
@@ -117,8 +122,11 @@ typedef struct {
     int64_t scratch_bytes;       /* device workspace owned by the plan         */
     int64_t dtype;
     int64_t fwd_warps, adj_warps;          /* persistent warps per launch        */
-    int64_t fwd_chunk, adj_chunk;          /* tasks per work item                */
+    int64_t fwd_chunk, adj_chunk;          /* tasks per work item (chunk schedule;
+                                              0 under the balanced split)       */
     int64_t fwd_load_milli, adj_load_milli;/* busiest warp's scheduled tasks x1000 */
+    int64_t fwd_split_q, adj_split_q;      /* balanced split's item overhead in
+                                              quarter tasks; 0 = chunk schedule */
 } ctis_plan_info;
 
 int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
@@ -239,10 +247,10 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
 
 /* Autotuner: for each projector, times the plan's EM launches (forward with
  * the ratio and statistics, adjoint with the update) over candidate work
- * schedules (cluster tasks per work item, shared by a CTA's warps: the
- * plan's model choice and 16..192) on this GPU, with g_dev (n float32) as the
- * measurement and f = 1,
- * and keeps the fastest. Synchronous; overwrites the plan's internal copies
+ * schedules on this GPU, with g_dev (n float32) as the measurement and f = 1,
+ * and keeps the fastest. Candidates: the plan's model choice, work items of
+ * at most 16..192 cluster tasks assigned longest first, and the balanced
+ * split with item overheads of 2..24 quarter tasks (ctis_plan_options). Synchronous; overwrites the plan's internal copies
  * and drops its cached graphs (the next ctis_reconstruct re-captures).
  * Results stay deterministic for a given schedule but may differ in the last
  * bits between schedules (partial sums are grouped differently). */

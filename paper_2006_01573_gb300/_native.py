@@ -43,12 +43,12 @@ class PlanInfo(ctypes.Structure):
         "a", "alpha", "w", "gamma", "xi", "m", "n", "nnz", "clusters", "cluster_k",
         "fwd_tiles", "fwd_tasks", "fwd_items", "adj_tiles", "adj_tasks", "adj_items",
         "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
-        "fwd_load_milli", "adj_load_milli")]
+        "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q")]
 
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("tasks_per_item", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("item_overhead_q", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 def load(path: str = LIB_PATH):
@@ -124,7 +124,8 @@ class Plan:
     ``(xi, gamma)`` float32, all on the plan's device.
     """
 
-    def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0):
+    def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0,
+                 item_overhead_q: int = 0):
         lib = load()
         ptr, _ = _arr(psf[0], np.int32)
         x, _ = _arr(psf[1], np.int32)
@@ -135,7 +136,7 @@ class Plan:
         self.dtype = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
         handle = ctypes.c_void_p()
         i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item))
+        opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q))
         _check(lib.ctis_plan_create_ex(ctypes.byref(handle), a, alpha, w, gamma, xi, i32(ptr),
                                        i32(x), i32(y),
                                        v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
@@ -280,11 +281,20 @@ class Plan:
     def autotune(self, g, stream=None):
         """Time the EM launches over candidate work schedules with ``g`` as the
         measurement and keep the fastest (synchronous). Returns the chosen
-        tasks per item ``(forward, adjoint)``."""
+        schedules ``(forward, adjoint)`` (see ``schedules``)."""
         self._check_fpa(g)
         _check(load().ctis_plan_autotune(self._h, ctypes.c_void_p(g.data_ptr()), _stream(stream)))
+        return self.schedules()
+
+    def schedules(self):
+        """The projectors' work schedules ``(forward, adjoint)``, each
+        ``("chunk", tasks_per_item)`` or ``("split", item_overhead_q)``."""
         info = self.info()
-        return int(info["fwd_chunk"]), int(info["adj_chunk"])
+        out = []
+        for side in ("fwd", "adj"):
+            q = int(info[side + "_split_q"])
+            out.append(("split", q) if q > 0 else ("chunk", int(info[side + "_chunk"])))
+        return tuple(out)
 
     # -- gradients ---------------------------------------------------------------
     @property

@@ -124,12 +124,14 @@ __global__ void rows_scatter_kernel(double* dst, const double* src, const int* g
 }
 
 // Frame totals of the forward's tile statistics when no following launch
-// adds them: one warp per frame.
+// adds them: kStatSlices warps per frame.
 __global__ void stats_reduce_kernel(double* out, const double* tile_stats, int tiles, int frames,
-                                    long long frame_stride) {
-    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (f >= frames) return;
-    reduce_frame_stats(tile_stats, tiles, f, out + f * frame_stride, threadIdx.x & 31);
+                                    long long frame_stride, double* part, int* tickets) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= frames * kStatSlices) return;
+    const int f = r / kStatSlices;
+    reduce_frame_slice(tile_stats, tiles, f, r - f * kStatSlices, part, tickets,
+                       out + f * frame_stride, threadIdx.x & 31);
 }
 
 // Sec. 3 embedding: datacube element j = (p, r, s) sits at FPA pixel
@@ -306,10 +308,12 @@ cudaError_t launch_rows_scatter(double* dst, const double* src, const int* gid, 
 }
 
 cudaError_t launch_stats_reduce(double* out, const double* tile_stats, int tiles, int frames,
-                                long long frame_stride, cudaStream_t stream) {
+                                long long frame_stride, double* part, int* tickets,
+                                cudaStream_t stream) {
     const int warps_per_block = 4;
-    stats_reduce_kernel<<<(frames + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
-                          stream>>>(out, tile_stats, tiles, frames, frame_stride);
+    const long long warps = (long long)frames * kStatSlices;
+    stats_reduce_kernel<<<int((warps + warps_per_block - 1) / warps_per_block), 32 * warps_per_block,
+                          0, stream>>>(out, tile_stats, tiles, frames, frame_stride, part, tickets);
     return cudaGetLastError();
 }
 

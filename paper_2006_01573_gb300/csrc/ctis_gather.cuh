@@ -580,66 +580,94 @@ __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumSt
     d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
 }
 
+// Float64 sum over the warp of four values per lane, as a reduce-scatter
+// (fixed tree, same on every run): the first two levels halve the set of
+// values a lane carries (lanes with bit 4 clear keep values 0 and 1, the
+// others 2 and 3; then bit 3 picks one of the two), the last three add
+// within groups of eight lanes. Six float64 additions per lane instead of
+// twenty; lane l ends with the total of value l >> 3 (all eight lanes of a
+// group hold it).
+__device__ __forceinline__ double warp_sum4(const double (&v)[kNumStats], int lane) {
+    static_assert(kNumStats == 4, "four values per lane");
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    const double k0 = hi16 ? v[2] : v[0], k1 = hi16 ? v[3] : v[1];
+    const double s0 = hi16 ? v[0] : v[2], s1 = hi16 ? v[1] : v[3];
+    const double a0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const double a1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+    double m = (hi8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi8 ? a0 : a1, 8);
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+    return m;
+}
+
 // Statistics of one finished tile: each warp's per-lane float32 sums (32
-// elements each) widened to float64 and added in a fixed tree, then the CTA's
-// warps' values added in warp order by warp 0, which stores the tile's four
-// values. The frame totals are added later, in tile order, by
-// reduce_frame_stats (at the start of the next launch in stream order), so no
-// fence or atomic sits on the tile's path.
+// elements each) widened to float64 and added by warp_sum4, then the CTA's
+// warps' values added in warp order (lanes 0..3 of warp 0, one value each),
+// which store the tile's four values. The frame totals are added later, in
+// fixed order, by reduce_frame_slice (at the start of the next launch in
+// stream order), so no fence or atomic sits on the tile's path.
 template <int NW, int THREADS>
 __device__ __forceinline__ void store_tile_stats(const GatherParams& p, int tile_idx,
                                                  const float (&stat)[kNumStats], int warp, int lane,
                                                  double* tstat) {
-    static_assert(kNumStats == 4, "statistics move as two double2");
-    double tot[kNumStats];
+    double d[kNumStats];
 #pragma unroll
-    for (int q = 0; q < kNumStats; ++q) tot[q] = warp_sum(static_cast<double>(stat[q]));
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < kNumStats; ++q) tstat[warp * kNumStats + q] = tot[q];
-    }
+    for (int q = 0; q < kNumStats; ++q) d[q] = static_cast<double>(stat[q]);
+    const double tot = warp_sum4(d, lane);
+    if ((lane & 7) == 0) tstat[warp * kNumStats + (lane >> 3)] = tot;
     cta_barrier(THREADS);
-    if (warp == 0 && lane == 0) {
-        double t[kNumStats];
-#pragma unroll
-        for (int q = 0; q < kNumStats; ++q) {
-            t[q] = tstat[q];
-            for (int w = 1; w < NW; ++w) t[q] += tstat[w * kNumStats + q];
-        }
-        double2* dst = reinterpret_cast<double2*>(p.tile_stats + (long long)tile_idx * kNumStats);
-        __stcg(dst, make_double2(t[0], t[1]));
-        __stcg(dst + 1, make_double2(t[2], t[3]));
+    if (warp == 0 && lane < kNumStats) {
+        double t = tstat[lane];
+        for (int w = 1; w < NW; ++w) t += tstat[w * kNumStats + lane];
+        __stcg(p.tile_stats + (long long)tile_idx * kNumStats + lane, t);
     }
 }
 
-// One warp adds the tile statistics of one frame in a fixed order (lane l
-// sums tiles l, l + 32, ..., then a fixed warp tree) into that frame's row.
-// All loads of a pass are in flight together.
-__device__ __forceinline__ void reduce_frame_stats(const double* tile_stats, int tiles, int frame,
+// Frame totals of a forward's tile statistics, in two fixed-order float64
+// levels. Slice `slice` of frame `frame` (one warp) adds the tiles
+// [slice*T/S, (slice+1)*T/S): lane l adds value l & 3 of every eighth tile
+// from offset l >> 2 on, in tile order, then the eight lanes of each value
+// add theirs in a fixed tree, and lanes 0..3 store the slice's four sums.
+// The slice that arrives last (one ticket per frame) adds the S slice sums
+// in slice order and writes the frame's row, so the result does not depend
+// on which warp finishes when.
+__device__ __forceinline__ void reduce_frame_slice(const double* tile_stats, int tiles, int frame,
+                                                   int slice, double* part, int* tickets,
                                                    double* out, int lane) {
     const double* src = tile_stats + (long long)frame * tiles * kNumStats;
-    double t[kNumStats] = {0.0, 0.0, 0.0, 0.0};
-    constexpr int B = 8;   // passes whose loads are issued together
-    for (int i0 = 0; i0 < tiles; i0 += 32 * B) {
-        double e[B][kNumStats];
+    const int b = int((long long)tiles * slice / kStatSlices);
+    const int e = int((long long)tiles * (slice + 1) / kStatSlices);
+    const int q = lane & 3, j = lane >> 2;
+    double t = 0.0;
+    constexpr int B = 4;   // loads in flight per lane
+    for (int i0 = b; i0 < e; i0 += 8 * B) {
+        double v[B];
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int i = i0 + 32 * b + lane;
-#pragma unroll
-            for (int q = 0; q < kNumStats; ++q) e[b][q] = 0.0;
-            if (i < tiles) load_stats(src + (long long)i * kNumStats, e[b]);
+        for (int k = 0; k < B; ++k) {
+            const int i = i0 + 8 * k + j;
+            v[k] = i < e ? __ldcg(src + (long long)i * kNumStats + q) : 0.0;
         }
 #pragma unroll
-        for (int b = 0; b < B; ++b)
-#pragma unroll
-            for (int q = 0; q < kNumStats; ++q) t[q] += e[b][q];
+        for (int k = 0; k < B; ++k) t += v[k];
     }
 #pragma unroll
-    for (int q = 0; q < kNumStats; ++q) t[q] = warp_sum(t[q]);
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < kNumStats; ++q) out[q] = t[q];
+    for (int off = 4; off < 32; off <<= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    double* fpart = part + (long long)frame * kStatSlices * kNumStats;
+    if (lane < kNumStats) {
+        __stcg(fpart + slice * kNumStats + lane, t);
+        fence_acq_rel_gpu();   // release this slice's sums
     }
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(tickets + frame, 1) == kStatSlices - 1;
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    fence_acq_rel_gpu();       // acquire the other slices' sums
+    if (lane < kNumStats) {
+        double sum = __ldcg(fpart + lane);
+        for (int k = 1; k < kStatSlices; ++k) sum += __ldcg(fpart + k * kNumStats + lane);
+        out[lane] = sum;
+    }
+    if (lane == 0) tickets[frame] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -663,10 +691,16 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * G::NW + warp;
-    // the previous forward's statistics, one warp per frame
-    if (p.red_out && gw < p.red_frames)
-        reduce_frame_stats(p.red_src, p.red_tiles_per_frame, gw, p.red_out + gw * p.red_frame_stride,
-                           lane);
+    // the previous forward's statistics: slice r of the frames' reduction on
+    // warp r / gridDim.x of CTA r % gridDim.x (the CTAs' first warps first)
+    if (p.red_out) {
+        const int r = warp * gridDim.x + blockIdx.x;
+        if (r < p.red_frames * kStatSlices) {
+            const int f = r / kStatSlices;
+            reduce_frame_slice(p.red_src, p.red_tiles_per_frame, f, r - f * kStatSlices, p.red_part,
+                               p.red_tickets, p.red_out + f * p.red_frame_stride, lane);
+        }
+    }
     if (gw >= p.n_warps) return;
     const int ib = p.warp_begin[gw], ie = p.warp_begin[gw + 1];
     if (ib >= ie) return;   // nothing issued, nothing to drain

@@ -20,6 +20,9 @@
 namespace ctis {
 
 constexpr int kNumStats = 4;   // flux_hf, flux_g, loglik, resid2 (see ctis.h)
+// slices (one warp each) of a frame's tile statistics in the two-level
+// float64 frame reduction
+constexpr int kStatSlices = 8;
 
 struct TileDesc {        // 32 bytes (host-side bookkeeping)
     int x0, y0;          // output origin: FPA (x, y) forward, voxel (p, r) adjoint
@@ -88,13 +91,15 @@ struct GatherParams {
     const float* g;
     int g_pitch;
     long long g_plane_stride;    // elements between frames of g
-    // frame totals of a previous forward's tile statistics, added by warps
-    // 0 .. red_frames-1 at the start of this launch (red_out null: none)
+    // frame totals of a previous forward's tile statistics, added at the start
+    // of this launch by red_frames * kStatSlices warps (red_out null: none)
     const double* red_src;       // [frames][tiles][kNumStats]
     double* red_out;             // frame f's row at red_out + f * red_frame_stride
     int red_tiles_per_frame;
     int red_frames;
     long long red_frame_stride;
+    double* red_part;            // [frames][kStatSlices][kNumStats] slice sums
+    int* red_tickets;            // [frames], zero between launches
     // kEpiUpdate / kEpiSet (datacube copies in the plan's dtype; f_in = copy 0)
     const void* f_in;
     void* f_out;

@@ -52,10 +52,13 @@ cudaError_t static_scratch_ptr(void** out);   // device address on the current d
 cudaError_t launch_index_map(long long* out, int a, int alpha, int w, int gamma, long long n,
                              cudaStream_t stream);
 
-// Frame totals of a forward's tile statistics (one warp per frame, fixed
-// order): out + f * frame_stride <- sum over tile_stats[f][0..tiles).
+// Frame totals of a forward's tile statistics (kStatSlices warps per frame,
+// fixed order): out + f * frame_stride <- sum over tile_stats[f][0..tiles).
+// part: [frames][kStatSlices][kNumStats] scratch; tickets: [frames], zero
+// before and after.
 cudaError_t launch_stats_reduce(double* out, const double* tile_stats, int tiles, int frames,
-                                long long frame_stride, cudaStream_t stream);
+                                long long frame_stride, double* part, int* tickets,
+                                cudaStream_t stream);
 
 // ---- frames of a batch (srcs / dsts: device arrays of per-frame pointers)
 // dst[f * n + i] = srcs[f][i]

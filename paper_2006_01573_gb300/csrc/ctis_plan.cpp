@@ -93,7 +93,8 @@ struct ProjTables {
     std::vector<WorkItem> witems;  // the items in warp order, as the kernel reads them
     int tile_w = 0, tile_h = 0;
     int64_t scratch_slots = 0;
-    int per_item = 0;              // chunk size chosen for this table
+    int per_item = 0;              // chunk size of the longest-first schedule (0: split)
+    int split_q = 0;               // balanced split: item overhead in quarter tasks (0: chunks)
     int n_warps = 0;
     double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
@@ -173,14 +174,16 @@ struct ctis_plan {
     float* d_scratch = nullptr;
     int64_t scratch_capacity = 0;    // float elements of d_scratch
     int* d_tickets = nullptr;
-    int* d_counters = nullptr;
+    int* d_counters = nullptr;   // [3] error flag, [8] the frame reduction's ticket
     double* d_tile_stats = nullptr;
+    double* d_red_part = nullptr;   // [kStatSlices][kNumStats] frame reduction slices
     int64_t device_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     GraphKey gkey;
     cudaGraphExec_t gexec = nullptr;
     bool profiling = false;
     int forced_per_item = 0;          // 0: chosen by schedule()
+    int forced_split_q = 0;           // 0: chosen by schedule()
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -238,6 +241,7 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_tickets);
     cudaFree(P->d_counters);
     cudaFree(P->d_tile_stats);
+    cudaFree(P->d_red_part);
     cudaFree(P->d_tap_slot);
     cudaFree(P->d_tap_s);
     cudaFree(P->d_grad_part);
@@ -282,6 +286,23 @@ void make_items(ProjTables& T, const std::vector<int>& tile_task_begin, int per_
     }
 }
 
+// Writes the CTAs' item lists in order of decreasing estimated load (ties:
+// original order). The SM's warp schedulers favour the warps of the CTAs that
+// became resident first (the lower block indices), so those run their tasks
+// faster while all CTAs are active; the heaviest lists go to them.
+void place_ctas(ProjTables& T, const std::vector<std::vector<int>>& per_cta,
+                const std::vector<double>& load) {
+    std::vector<int> ord(per_cta.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return load[x] > load[y]; });
+    T.cta_begin.assign(1, 0);
+    T.cta_items.clear();
+    for (int c : ord) {
+        T.cta_items.insert(T.cta_items.end(), per_cta[c].begin(), per_cta[c].end());
+        T.cta_begin.push_back(static_cast<int>(T.cta_items.size()));
+    }
+}
+
 // Longest-processing-time-first assignment of the items to n_ctas CTAs.
 // Returns the load of the busiest CTA (tasks per warp); fills cta_begin /
 // cta_items.
@@ -302,54 +323,165 @@ double assign_ctas(ProjTables& T, int n_ctas) {
     };
     std::make_heap(heap.begin(), heap.end(), cmp);
     std::vector<std::vector<int>> per_cta(n_ctas);
+    std::vector<double> load(n_ctas, 0.0);
     double max_load = 0.0;
     for (int i : order) {
         std::pop_heap(heap.begin(), heap.end(), cmp);
         Slot& sl = heap.back();
         per_cta[sl.second].push_back(i);
         sl.first += cost(i);
+        load[sl.second] = sl.first;
         max_load = std::max(max_load, sl.first);
         std::push_heap(heap.begin(), heap.end(), cmp);
     }
-    T.cta_begin.assign(1, 0);
-    T.cta_items.clear();
-    for (int c = 0; c < n_ctas; ++c) {
-        T.cta_items.insert(T.cta_items.end(), per_cta[c].begin(), per_cta[c].end());
-        T.cta_begin.push_back(static_cast<int>(T.cta_items.size()));
-    }
+    place_ctas(T, per_cta, load);
     return max_load;
 }
 
-// Picks the item size (cluster tasks per CTA item) that minimises the LPT
-// estimate of the busiest CTA (ties: the larger, i.e. fewer partial sums), or
-// uses `forced` > 0. Then lays out, for every warp, its part of each of its
-// CTA's items: warp w of a CTA runs tasks [b + w*n/NW, b + (w+1)*n/NW) of an
-// item of n tasks; the warps' item lists are parallel (same tiles, same
-// order) and every warp's tasks are stored contiguously.
-void schedule(ProjTables& T, int n_warps, int forced) {
+// Balanced contiguous split: the tiles' tasks, in tile order, are cut into
+// runs of nearly equal estimated cost, one run per CTA. A piece of a tile
+// costs the warps' share of its tasks plus `e` (the shared-memory sum and
+// the epilogue, in tasks per warp); a tile cut by a run boundary becomes
+// chunks on consecutive CTAs, and each of its pieces also pays the chunk
+// sums' round trip. The per-CTA budget is the smallest (bisection) for which
+// the greedy fill needs at most n_ctas CTAs. Fills items (chunk order within
+// a tile), cta_begin / cta_items and the tiles' chunk counts; returns the
+// busiest CTA's estimate.
+double split_items(ProjTables& T, int n_ctas, double e) {
+    constexpr double kChunkCost = 1.5;
+    const std::vector<int>& begin = T.tile_task_begin;
+    const int nw = T.nw;
+    const int ntiles = static_cast<int>(T.tiles.size());
+    struct Piece {
+        int tile, b, e, cta;
+    };
+    std::vector<Piece> pieces;
+    auto share = [nw](int n) { return static_cast<double>((n + nw - 1) / nw); };
+    // CTAs the greedy fill under budget B needs (n_ctas + 1 when it needs more)
+    auto fill = [&](double B, double* max_load) -> int {
+        pieces.clear();
+        int cta = 0;
+        double load = 0.0, top = 0.0;
+        for (int t = 0; t < ntiles; ++t) {
+            int pos = begin[t];
+            const int end = begin[t + 1];
+            bool cut = false;
+            for (;;) {
+                const double whole = share(end - pos) + e + (cut ? kChunkCost : 0.0);
+                if (load + whole <= B) {
+                    pieces.push_back({t, pos, end, cta});
+                    load += whole;
+                    top = std::max(top, load);
+                    break;
+                }
+                // a piece of it here, the rest on the next CTAs
+                const double room = B - load - e - kChunkCost;
+                const int n = room >= 1.0 ? std::min(end - pos, static_cast<int>(room) * nw) : 0;
+                if (n > 0 && n < end - pos) {
+                    pieces.push_back({t, pos, pos + n, cta});
+                    top = std::max(top, load + share(n) + e + kChunkCost);
+                    pos += n;
+                    cut = true;
+                }
+                if (++cta >= n_ctas) return n_ctas + 1;
+                load = 0.0;
+            }
+        }
+        if (max_load) *max_load = top;
+        return load > 0.0 ? cta + 1 : cta;
+    };
+    double total = 0.0;
+    for (int t = 0; t < ntiles; ++t) total += share(begin[t + 1] - begin[t]) + e;
+    double lo = std::max(total / n_ctas, e + kChunkCost + 1.0), hi = total + e + kChunkCost + 1.0;
+    if (fill(lo, nullptr) > n_ctas) {
+        for (int i = 0; i < 60 && hi - lo > 1e-3; ++i) {
+            const double mid = 0.5 * (lo + hi);
+            (fill(mid, nullptr) <= n_ctas ? hi : lo) = mid;
+        }
+    } else {
+        hi = lo;
+    }
+    double max_load = 0.0;
+    fill(hi, &max_load);
+    // items, chunk numbering and scratch slots
+    T.items.clear();
+    T.scratch_slots = 0;
+    for (auto& td : T.tiles) {
+        td.nchunks = 0;
+        td.scratch_base = 0;
+    }
+    for (const Piece& pc : pieces) T.tiles[pc.tile].nchunks++;
+    for (auto& td : T.tiles) {
+        if (td.nchunks > 1) {
+            td.scratch_base = static_cast<int>(T.scratch_slots);
+            T.scratch_slots += td.nchunks;
+        }
+    }
+    std::vector<int> next_chunk(T.tiles.size(), 0);
+    std::vector<std::vector<int>> per_cta(n_ctas);
+    std::vector<double> load(n_ctas, 0.0);
+    for (const Piece& pc : pieces) {
+        ItemDesc it;
+        it.tile = pc.tile;
+        it.chunk = next_chunk[pc.tile]++;
+        it.task_begin = pc.b;
+        it.task_end = pc.e;
+        per_cta[pc.cta].push_back(static_cast<int>(T.items.size()));
+        load[pc.cta] += share(pc.e - pc.b) + e + (T.tiles[pc.tile].nchunks > 1 ? kChunkCost : 0.0);
+        T.items.push_back(it);
+    }
+    place_ctas(T, per_cta, load);
+    return max_load;
+}
+
+// Picks the work schedule: `forced_split_q` > 0 forces the balanced split
+// with a per-item overhead of forced_split_q / 4 tasks, `forced` > 0 the
+// longest-first assignment of chunks of at most `forced` tasks; otherwise the
+// candidate (chunk sizes, and the balanced split with a half-task overhead)
+// with the smallest estimate of the busiest CTA. Then lays out, for every
+// warp, its part of each of its CTA's items: warp w of a CTA runs tasks
+// [b + w*n/NW, b + (w+1)*n/NW) of an item of n tasks; the warps' item lists
+// are parallel (same tiles, same order) and every warp's tasks are stored
+// contiguously.
+void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q) {
     const std::vector<int>& begin = T.tile_task_begin;
     const int nw = T.nw;
     const int n_ctas = n_warps / nw;
     T.n_warps = n_ctas * nw;
-    std::vector<int> cands;
-    if (forced > 0) {
-        cands.push_back(forced);
+    constexpr int kModelSplitQ = 2;
+    int split_q = 0;
+    if (forced_split_q > 0) {
+        split_q = forced_split_q;
     } else {
-        for (int c : {256, 192, 128, 96, 64, 48, 32, 24, 16, 12, 8}) cands.push_back(c);
-    }
-    int best = cands[0];
-    double best_load = -1.0;
-    for (int c : cands) {
-        make_items(T, begin, c);
-        const double load = assign_ctas(T, n_ctas);
-        if (best_load < 0 || load < best_load - 1e-9) {
-            best_load = load;
-            best = c;
+        std::vector<int> cands;
+        if (forced > 0) {
+            cands.push_back(forced);
+        } else {
+            for (int c : {256, 192, 128, 96, 64, 48, 32, 24, 16, 12, 8}) cands.push_back(c);
+        }
+        int best = cands[0];
+        double best_load = -1.0;
+        for (int c : cands) {
+            make_items(T, begin, c);
+            const double load = assign_ctas(T, n_ctas);
+            if (best_load < 0 || load < best_load - 1e-9) {
+                best_load = load;
+                best = c;
+            }
+        }
+        if (forced <= 0 && split_items(T, n_ctas, kModelSplitQ / 4.0) < best_load - 1e-9) {
+            split_q = kModelSplitQ;
+        } else {
+            make_items(T, begin, best);
+            T.max_warp_load = assign_ctas(T, n_ctas);
+            T.per_item = best;
         }
     }
-    make_items(T, begin, best);
-    T.max_warp_load = assign_ctas(T, n_ctas);
-    T.per_item = best;
+    if (split_q > 0) {
+        T.max_warp_load = split_items(T, n_ctas, split_q / 4.0);
+        T.per_item = 0;
+    }
+    T.split_q = split_q;
     T.witems.clear();
     T.warp_begin.assign(1, 0);
     std::vector<TaskDesc> wt;
@@ -649,7 +781,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                 begin.push_back(static_cast<int>(T.tile_tasks.size()));
             }
         T.tile_task_begin = std::move(begin);
-        schedule(T, warps_fwd, P->forced_per_item);
+        schedule(T, warps_fwd, P->forced_per_item, P->forced_split_q);
     }
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
@@ -688,7 +820,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                     begin.push_back(static_cast<int>(T.tile_tasks.size()));
                 }
         T.tile_task_begin = std::move(begin);
-        schedule(T, warps_adj, P->forced_per_item);
+        schedule(T, warps_adj, P->forced_per_item, P->forced_split_q);
     }
 
     // ---- device buffers
@@ -719,16 +851,19 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     // tickets: one per tile (chunked tiles); statistics: per forward tile
     const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
-    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 8);
+    // counters: [3] the bounded waits' error flag, [8] the frame reduction's ticket
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 16);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
                           sizeof(double) * kNumStats * P->fwd.tiles.size());
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_red_part),
+                          sizeof(double) * kNumStats * kStatSlices);
     if (rc) return rc;
     // copies start zeroed: the elements past each copy's shifted end are never
     // written and must read as zero
     CTIS_CUDA(cudaMemset(P->d_u, 0, sizeof(float) * static_cast<size_t>(P->u_copy_stride) * P->u_copies));
     CTIS_CUDA(cudaMemset(P->d_fwork, 0, es * static_cast<size_t>(P->f_copy_stride) * P->f_copies));
     CTIS_CUDA(cudaMemset(P->d_tickets, 0, sizeof(int) * ntiles));
-    CTIS_CUDA(cudaMemset(P->d_counters, 0, sizeof(int) * 8));
+    CTIS_CUDA(cudaMemset(P->d_counters, 0, sizeof(int) * 16));
     CTIS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
     CTIS_CUDA(cudaDeviceSynchronize());
     return CTIS_OK;
@@ -930,13 +1065,15 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
             pa.red_out = stats + static_cast<int64_t>(it) * kNumStats;
             pa.red_tiles_per_frame = ftiles;
             pa.red_frames = 1;
+            pa.red_part = P->d_red_part;
+            pa.red_tickets = P->d_counters + 8;
         }
         rc = timed(P->prof_adj, [&] { return enqueue_adjoint(P, pa, st); });
         if (rc) return rc;
     }
     if (stats)
         CTIS_CUDA(launch_stats_reduce(stats + static_cast<int64_t>(k) * kNumStats, P->d_tile_stats,
-                                      ftiles, 1, 0, st));
+                                      ftiles, 1, 0, P->d_red_part, P->d_counters + 8, st));
     CTIS_CUDA(launch_gather_copy0(P->dtype, f, P->d_fwork, P->a_pitch,
                                   static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
                                   P->w, st));
@@ -966,8 +1103,9 @@ struct BatchState {
     float* d_u = nullptr;          // FPA copies, rows f*xi + y
     float* d_scratch = nullptr;
     int* d_tickets = nullptr;
-    int* d_counters = nullptr;     // [8] as the plan's, then [F] statistics groups done
+    int* d_counters = nullptr;     // [3] error flag, [8 + f] frame f's reduction ticket
     double* d_tile_stats = nullptr;
+    double* d_red_part = nullptr;  // [F][kStatSlices][kNumStats]
     float* d_h = nullptr;          // h for every plane f*w + s
     float* d_g = nullptr;          // the frames' g, contiguous
     void** d_ptrs = nullptr;       // [F] g pointers, [F] f pointers
@@ -994,6 +1132,7 @@ void free_batch(BatchState* B) {
     cudaFree(B->d_tickets);
     cudaFree(B->d_counters);
     cudaFree(B->d_tile_stats);
+    cudaFree(B->d_red_part);
     cudaFree(B->d_h);
     cudaFree(B->d_g);
     cudaFree(B->d_ptrs);
@@ -1088,6 +1227,8 @@ int ensure_batch(ctis_plan* P, int F, int k) {
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_counters), sizeof(int) * (8 + F));
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tile_stats),
                           sizeof(double) * kNumStats * tpf * F);
+    if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_red_part),
+                          sizeof(double) * kNumStats * kStatSlices * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_h), sizeof(float) * P->w * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_g), sizeof(float) * P->n * F);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_ptrs), sizeof(void*) * 2 * F);
@@ -1227,14 +1368,17 @@ int batch_adjoint_step(BatchRun& r, int it, int k, cudaStream_t st) {
     const int tiles = static_cast<int>(r.P->fwd.tiles.size());
     double* out = r.B->d_stats + static_cast<int64_t>(it) * kNumStats;
     const long long stride = static_cast<long long>(k + 1) * kNumStats;
-    if (r.stats && r.B->F <= p.n_warps) {
+    if (r.stats && static_cast<int64_t>(r.B->F) * kStatSlices <= p.n_warps) {
         p.red_src = r.B->d_tile_stats;
         p.red_out = out;
         p.red_tiles_per_frame = tiles;
         p.red_frames = r.B->F;
         p.red_frame_stride = stride;
+        p.red_part = r.B->d_red_part;
+        p.red_tickets = r.B->d_counters + 8;
     } else if (r.stats) {
-        CTIS_CUDA(launch_stats_reduce(out, r.B->d_tile_stats, tiles, r.B->F, stride, st));
+        CTIS_CUDA(launch_stats_reduce(out, r.B->d_tile_stats, tiles, r.B->F, stride,
+                                      r.B->d_red_part, r.B->d_counters + 8, st));
     }
     return batch_adjoint(r.P, r.B, p, st);
 }
@@ -1248,7 +1392,8 @@ int batch_finish(BatchRun& r, int k, double* stats_dev, cudaStream_t st) {
     if (r.stats) {   // the last forward's statistics, then every frame's rows to the caller
         CTIS_CUDA(launch_stats_reduce(B->d_stats + static_cast<int64_t>(k) * kNumStats,
                                       B->d_tile_stats, static_cast<int>(P->fwd.tiles.size()), B->F,
-                                      static_cast<long long>(k + 1) * kNumStats, st));
+                                      static_cast<long long>(k + 1) * kNumStats, B->d_red_part,
+                                      B->d_counters + 8, st));
         CTIS_CUDA(launch_rows_scatter(stats_dev, B->d_stats, B->d_gid, (k + 1) * kNumStats, B->F, st));
     }
     return CTIS_OK;
@@ -1317,7 +1462,7 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
                         const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
                         const float* psf_val, int dtype, const ctis_plan_options* opt) {
     if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
-    int forced_per_item = 0;
+    int forced_per_item = 0, forced_split_q = 0;
     if (opt) {
         if (opt->struct_size != static_cast<int>(sizeof(ctis_plan_options)))
             return fail(CTIS_ERR_INVALID_ARG, "ctis_plan_options.struct_size mismatch");
@@ -1325,7 +1470,12 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
             if (r != 0) return fail(CTIS_ERR_INVALID_ARG, "reserved option fields must be 0");
         if (opt->tasks_per_item < 0 || opt->tasks_per_item > 1 << 20)
             return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item out of range");
+        if (opt->item_overhead_q < 0 || opt->item_overhead_q > 1 << 16)
+            return fail(CTIS_ERR_INVALID_ARG, "item_overhead_q out of range");
+        if (opt->tasks_per_item > 0 && opt->item_overhead_q > 0)
+            return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item and item_overhead_q are exclusive");
         forced_per_item = opt->tasks_per_item;
+        forced_split_q = opt->item_overhead_q;
     }
     *out = nullptr;
     if (a < 1 || alpha < 1 || w < 1 || gamma < 1 || xi < 1)
@@ -1366,6 +1516,7 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     P->f_copies = gather_input_copies(true, dtype);
     P->u_copies = gather_input_copies(false, dtype);
     P->forced_per_item = forced_per_item;
+    P->forced_split_q = forced_split_q;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
@@ -1416,6 +1567,8 @@ int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
     info->adj_chunk = P->adj.per_item;
     info->fwd_load_milli = static_cast<int64_t>(P->fwd.max_warp_load * 1000.0);
     info->adj_load_milli = static_cast<int64_t>(P->adj.max_warp_load * 1000.0);
+    info->fwd_split_q = P->fwd.split_q;
+    info->adj_split_q = P->adj.split_q;
     return CTIS_OK;
 }
 
@@ -1755,7 +1908,7 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     rc = enqueue_forward(P, pl, st);             // 1 - g/q into the FPA copies
     if (rc) return rc;
     CTIS_CUDA(launch_stats_reduce(stats, P->d_tile_stats, static_cast<int>(P->fwd.tiles.size()), 1,
-                                  0, st));
+                                  0, P->d_red_part, P->d_counters + 8, st));
     rc = adjoint_raw(gb);                        // dL/df^(k) = H^T (1 - g/q)
     if (!rc) rc = enqueue_psf_grad(P, ck(k), dval_dev, false, nullptr, st);
     if (rc) return rc;
@@ -1971,15 +2124,22 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
         set_f_copies(P, p);
         return enqueue_adjoint(P, p, st);
     };
-    const int cands[] = {0, 16, 24, 32, 48, 64, 96, 128, 192};
+    // candidates: the model's choice, chunks of 16..192 tasks (longest-first),
+    // and the balanced split with item overheads of 0.5..6 tasks
+    struct Cand {
+        int chunk, split_q;
+    };
+    std::vector<Cand> cands{{0, 0}};
+    for (int c : {16, 24, 32, 48, 64, 96, 128, 192}) cands.push_back({c, 0});
+    for (int q : {2, 4, 8, 12, 16, 24}) cands.push_back({0, q});
     int result = CTIS_OK;
     for (ProjTables* T : {&P->fwd, &P->adj}) {
         const bool forward = T == &P->fwd;
         float best_ms = -1.f;
-        int best = 0;
-        for (int c : cands) {
-            schedule(*T, T->n_warps, c);
-            if (c != 0 && T->per_item != c) continue;
+        Cand best{0, 0};
+        for (const Cand& c : cands) {
+            schedule(*T, T->n_warps, c.chunk, c.split_q);
+            if (c.chunk != 0 && T->per_item != c.chunk) continue;
             result = reupload(*T);
             for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
             cudaError_t e = result ? cudaSuccess : cudaEventRecord(e0, st);
@@ -1992,11 +2152,11 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
             if (result) break;
             if (best_ms < 0.f || ms < best_ms) {
                 best_ms = ms;
-                best = T->per_item;
+                best = {T->per_item, T->split_q};
             }
         }
         if (result) break;
-        schedule(*T, T->n_warps, best);
+        schedule(*T, T->n_warps, best.chunk, best.split_q);
         result = reupload(*T);
         if (result) break;
     }

@@ -13,7 +13,8 @@ from tests.helpers import floored_rel, problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-CANDIDATES = {16, 24, 32, 48, 64, 96, 128, 192}
+CANDIDATES = ({("chunk", c) for c in (16, 24, 32, 48, 64, 96, 128, 192)}
+              | {("split", q) for q in (2, 4, 8, 12, 16, 24)})
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -27,7 +28,7 @@ def test_autotuned_plan_matches_oracle_and_is_reproducible():
     geom, psf, H, _, g = problem(wl)
     ref, _ = O.mlem(H, g, wl.k)
     with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
-        model_choice = plan.info()["fwd_chunk"], plan.info()["adj_chunk"]
+        model_choice = plan.schedules()
         gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
         fc, ac = plan.autotune(gt)
         assert fc in CANDIDATES | {model_choice[0]} and ac in CANDIDATES | {model_choice[1]}
@@ -60,3 +61,32 @@ def test_autotune_full_size_stays_within_tolerance_of_untuned():
     # two float32 reconstructions that differ only in the grouping of sums
     assert floored_rel(b, a) <= 2 * k * 1e-5
     assert np.all(np.abs(sb - sa) <= 2e-5 * np.abs(sa))
+
+
+@pytest.mark.parametrize("opts", [dict(tasks_per_item=24), dict(item_overhead_q=2),
+                                  dict(item_overhead_q=24)])
+def test_forced_schedules_match_oracle(opts):
+    """Every schedule form (chunks assigned longest first; the balanced split,
+    whose runs cut tiles into chunks on consecutive CTAs) gives the EM
+    iterates within the parity bounds, on the tiny and the ragged workloads."""
+    for wl in (synth.TINY, synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7,
+                                          "mask_spectra", 100.0, 5)):
+        geom, psf, H, _, g = problem(wl)
+        ref, _ = O.mlem(H, g, wl.k)
+        with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, **opts) as plan:
+            kind = "chunk" if "tasks_per_item" in opts else "split"
+            assert all(s[0] == kind for s in plan.schedules())
+            gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+            got, _ = plan.reconstruct(gt, k=wl.k, init="ones")
+            plan.check()
+            got = got.cpu().numpy().ravel()
+        assert floored_rel(got, ref) <= wl.k * 1e-5, wl.name
+        assert rel_l2(got, ref) <= 1e-5 * np.sqrt(wl.k), wl.name
+
+
+def test_schedule_options_are_exclusive():
+    from paper_2006_01573_gb300 import CtisError
+    wl = synth.TINY
+    with pytest.raises(CtisError):
+        Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), tasks_per_item=16,
+             item_overhead_q=4)
