@@ -33,11 +33,11 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 def schedule_name(sched):
-    """("chunk", n) -> "chunks of <= n tasks, longest first"; ("split", q) -> the balanced split."""
-    kind, v = sched
-    if kind == "split":
-        return f"balanced split, item overhead {v / 4:g} tasks"
-    return f"chunks of <= {v} tasks, longest first"
+    """A plan schedule ``(kind, value, skew)`` in words."""
+    kind, v, skew = sched
+    name = (f"balanced split, item overhead {v / 4:g} tasks" if kind == "split"
+            else f"chunks of <= {v} tasks, longest first")
+    return name + (f", CTA priority skew {skew / 1000:g}" if skew else "")
 
 def parse_args():
     ap = argparse.ArgumentParser()

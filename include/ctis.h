@@ -99,7 +99,11 @@ typedef struct {
                               quarter tasks. Exclusive with tasks_per_item;
                               both 0 = the candidate with the smallest
                               estimated busiest CTA                             */
-    int reserved[5];       /* must be 0                                          */
+    int cta_skew_permille; /* 0..900: schedule for CTAs whose speed falls
+                              linearly from 1 + skew to 1 - skew over the block
+                              indices (the SM's warp schedulers favour the CTAs
+                              resident first); 0 = equal speeds                 */
+    int reserved[4];       /* must be 0                                          */
 } ctis_plan_options;
 
 /* ctis_plan_create with options; opt may be NULL (all defaults). */
@@ -127,6 +131,7 @@ typedef struct {
     int64_t fwd_load_milli, adj_load_milli;/* busiest warp's scheduled tasks x1000 */
     int64_t fwd_split_q, adj_split_q;      /* balanced split's item overhead in
                                               quarter tasks; 0 = chunk schedule */
+    int64_t fwd_skew_pm, adj_skew_pm;      /* CTA priority skew of the schedule  */
 } ctis_plan_info;
 
 int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
@@ -250,7 +255,8 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
  * schedules on this GPU, with g_dev (n float32) as the measurement and f = 1,
  * and keeps the fastest. Candidates: the plan's model choice, work items of
  * at most 16..192 cluster tasks assigned longest first, and the balanced
- * split with item overheads of 2..24 quarter tasks (ctis_plan_options). Synchronous; overwrites the plan's internal copies
+ * split with item overheads of 2..24 quarter tasks, some of them also with
+ * CTA priority skews of 100..300 permille (ctis_plan_options). Synchronous; overwrites the plan's internal copies
  * and drops its cached graphs (the next ctis_reconstruct re-captures).
  * Results stay deterministic for a given schedule but may differ in the last
  * bits between schedules (partial sums are grouped differently). */

@@ -43,12 +43,14 @@ class PlanInfo(ctypes.Structure):
         "a", "alpha", "w", "gamma", "xi", "m", "n", "nnz", "clusters", "cluster_k",
         "fwd_tiles", "fwd_tasks", "fwd_items", "adj_tiles", "adj_tasks", "adj_items",
         "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
-        "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q")]
+        "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q", "fwd_skew_pm",
+        "adj_skew_pm")]
 
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("tasks_per_item", ctypes.c_int),
-                ("item_overhead_q", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("item_overhead_q", ctypes.c_int), ("cta_skew_permille", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 def load(path: str = LIB_PATH):
@@ -125,7 +127,7 @@ class Plan:
     """
 
     def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0,
-                 item_overhead_q: int = 0):
+                 item_overhead_q: int = 0, cta_skew_permille: int = 0):
         lib = load()
         ptr, _ = _arr(psf[0], np.int32)
         x, _ = _arr(psf[1], np.int32)
@@ -136,7 +138,8 @@ class Plan:
         self.dtype = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
         handle = ctypes.c_void_p()
         i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q))
+        opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
+                          int(cta_skew_permille))
         _check(lib.ctis_plan_create_ex(ctypes.byref(handle), a, alpha, w, gamma, xi, i32(ptr),
                                        i32(x), i32(y),
                                        v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
@@ -288,12 +291,14 @@ class Plan:
 
     def schedules(self):
         """The projectors' work schedules ``(forward, adjoint)``, each
-        ``("chunk", tasks_per_item)`` or ``("split", item_overhead_q)``."""
+        ``("chunk", tasks_per_item, skew)`` or ``("split", item_overhead_q,
+        skew)``, skew the CTA priority skew in permille."""
         info = self.info()
         out = []
         for side in ("fwd", "adj"):
             q = int(info[side + "_split_q"])
-            out.append(("split", q) if q > 0 else ("chunk", int(info[side + "_chunk"])))
+            kind, v = ("split", q) if q > 0 else ("chunk", int(info[side + "_chunk"]))
+            out.append((kind, v, int(info[side + "_skew_pm"])))
         return tuple(out)
 
     # -- gradients ---------------------------------------------------------------

@@ -95,6 +95,7 @@ struct ProjTables {
     int64_t scratch_slots = 0;
     int per_item = 0;              // chunk size of the longest-first schedule (0: split)
     int split_q = 0;               // balanced split: item overhead in quarter tasks (0: chunks)
+    int skew_pm = 0;               // CTA priority skew of the schedule (permille)
     int n_warps = 0;
     double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
@@ -184,6 +185,7 @@ struct ctis_plan {
     bool profiling = false;
     int forced_per_item = 0;          // 0: chosen by schedule()
     int forced_split_q = 0;           // 0: chosen by schedule()
+    int forced_skew_pm = 0;           // CTA priority skew of the model's schedule
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -253,11 +255,12 @@ void destroy(ctis_plan* P) {
 }
 
 // Cost of an item in tasks per warp: the CTA's warps share its tasks, then
-// add their sums in shared memory and split the epilogue (about half a task),
-// and a tile split over CTAs pays the chunk sums' round trip through global
-// memory (about a task and a half).
+// wait for each other, add their sums in shared memory and run the epilogue
+// (measured on GB300: about three tasks' time), and a tile split over CTAs
+// pays the chunk sums' round trip through global memory (about three more).
+constexpr double kItemCost = 3.0, kChunkCost = 3.0;
 double item_cost(int tasks, int nw, bool chunked) {
-    return (tasks + nw - 1) / nw + (chunked ? 1.5 : 0.0) + 0.5;
+    return (tasks + nw - 1) / nw + (chunked ? kChunkCost : 0.0) + kItemCost;
 }
 
 // Splits every tile's task range into chunks of at most `per_item` tasks and
@@ -303,10 +306,20 @@ void place_ctas(ProjTables& T, const std::vector<std::vector<int>>& per_cta,
     }
 }
 
-// Longest-processing-time-first assignment of the items to n_ctas CTAs.
-// Returns the load of the busiest CTA (tasks per warp); fills cta_begin /
-// cta_items.
-double assign_ctas(ProjTables& T, int n_ctas) {
+// Relative speed of CTA c of n under a priority skew of skew_pm permille:
+// the SM's warp schedulers favour the warps of the CTAs that became resident
+// first (the lower block indices), so while all CTAs are active CTA c runs
+// about 1 + skew (1 - 2 c / (n - 1)) times the mean rate.
+double cta_speed(int c, int n, int skew_pm) {
+    if (n <= 1 || skew_pm == 0) return 1.0;
+    return 1.0 + skew_pm / 1000.0 * (1.0 - 2.0 * c / (n - 1));
+}
+
+// Longest-processing-time-first assignment of the items to n_ctas CTAs: each
+// item, largest first, goes to the CTA with the earliest estimated finish
+// (load / speed; ties: the lower index). Returns the latest estimated finish
+// (tasks per warp at the mean rate); fills cta_begin / cta_items.
+double assign_ctas(ProjTables& T, int n_ctas, int skew_pm) {
     std::vector<int> order(T.items.size());
     std::iota(order.begin(), order.end(), 0);
     auto cost = [&](int i) {
@@ -314,7 +327,9 @@ double assign_ctas(ProjTables& T, int n_ctas) {
         return item_cost(it.task_end - it.task_begin, T.nw, T.tiles[it.tile].nchunks > 1);
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    using Slot = std::pair<double, int>;   // (load, CTA)
+    std::vector<double> speed(n_ctas);
+    for (int c = 0; c < n_ctas; ++c) speed[c] = cta_speed(c, n_ctas, skew_pm);
+    using Slot = std::pair<double, int>;   // (estimated finish, CTA)
     std::vector<Slot> heap;
     heap.reserve(n_ctas);
     for (int c = 0; c < n_ctas; ++c) heap.emplace_back(0.0, c);
@@ -324,18 +339,19 @@ double assign_ctas(ProjTables& T, int n_ctas) {
     std::make_heap(heap.begin(), heap.end(), cmp);
     std::vector<std::vector<int>> per_cta(n_ctas);
     std::vector<double> load(n_ctas, 0.0);
-    double max_load = 0.0;
+    double max_finish = 0.0;
     for (int i : order) {
         std::pop_heap(heap.begin(), heap.end(), cmp);
         Slot& sl = heap.back();
-        per_cta[sl.second].push_back(i);
-        sl.first += cost(i);
-        load[sl.second] = sl.first;
-        max_load = std::max(max_load, sl.first);
+        const int c = sl.second;
+        per_cta[c].push_back(i);
+        load[c] += cost(i);
+        sl.first = load[c] / speed[c];
+        max_finish = std::max(max_finish, sl.first);
         std::push_heap(heap.begin(), heap.end(), cmp);
     }
     place_ctas(T, per_cta, load);
-    return max_load;
+    return max_finish;
 }
 
 // Balanced contiguous split: the tiles' tasks, in tile order, are cut into
@@ -347,8 +363,7 @@ double assign_ctas(ProjTables& T, int n_ctas) {
 // the greedy fill needs at most n_ctas CTAs. Fills items (chunk order within
 // a tile), cta_begin / cta_items and the tiles' chunk counts; returns the
 // busiest CTA's estimate.
-double split_items(ProjTables& T, int n_ctas, double e) {
-    constexpr double kChunkCost = 1.5;
+double split_items(ProjTables& T, int n_ctas, double e, int skew_pm) {
     const std::vector<int>& begin = T.tile_task_begin;
     const int nw = T.nw;
     const int ntiles = static_cast<int>(T.tiles.size());
@@ -358,7 +373,10 @@ double split_items(ProjTables& T, int n_ctas, double e) {
     std::vector<Piece> pieces;
     auto share = [nw](int n) { return static_cast<double>((n + nw - 1) / nw); };
     // CTAs the greedy fill under budget B needs (n_ctas + 1 when it needs more)
-    auto fill = [&](double B, double* max_load) -> int {
+    std::vector<double> speed(n_ctas);
+    for (int c = 0; c < n_ctas; ++c) speed[c] = cta_speed(c, n_ctas, skew_pm);
+    // CTA c's budget is B * speed[c]; the estimate is the latest finish
+    auto fill = [&](double B, double* max_finish) -> int {
         pieces.clear();
         int cta = 0;
         double load = 0.0, top = 0.0;
@@ -367,19 +385,20 @@ double split_items(ProjTables& T, int n_ctas, double e) {
             const int end = begin[t + 1];
             bool cut = false;
             for (;;) {
+                const double cap = B * speed[cta];
                 const double whole = share(end - pos) + e + (cut ? kChunkCost : 0.0);
-                if (load + whole <= B) {
+                if (load + whole <= cap) {
                     pieces.push_back({t, pos, end, cta});
                     load += whole;
-                    top = std::max(top, load);
+                    top = std::max(top, load / speed[cta]);
                     break;
                 }
                 // a piece of it here, the rest on the next CTAs
-                const double room = B - load - e - kChunkCost;
+                const double room = cap - load - e - kChunkCost;
                 const int n = room >= 1.0 ? std::min(end - pos, static_cast<int>(room) * nw) : 0;
                 if (n > 0 && n < end - pos) {
                     pieces.push_back({t, pos, pos + n, cta});
-                    top = std::max(top, load + share(n) + e + kChunkCost);
+                    top = std::max(top, (load + share(n) + e + kChunkCost) / speed[cta]);
                     pos += n;
                     cut = true;
                 }
@@ -387,12 +406,15 @@ double split_items(ProjTables& T, int n_ctas, double e) {
                 load = 0.0;
             }
         }
-        if (max_load) *max_load = top;
+        if (max_finish) *max_finish = top;
         return load > 0.0 ? cta + 1 : cta;
     };
     double total = 0.0;
     for (int t = 0; t < ntiles; ++t) total += share(begin[t + 1] - begin[t]) + e;
-    double lo = std::max(total / n_ctas, e + kChunkCost + 1.0), hi = total + e + kChunkCost + 1.0;
+    double min_speed = 1.0;
+    for (double v : speed) min_speed = std::min(min_speed, v);
+    double lo = std::max(total / n_ctas, e + kChunkCost + 1.0);
+    double hi = (total + e + kChunkCost + 1.0) / min_speed;
     if (fill(lo, nullptr) > n_ctas) {
         for (int i = 0; i < 60 && hi - lo > 1e-3; ++i) {
             const double mid = 0.5 * (lo + hi);
@@ -437,18 +459,19 @@ double split_items(ProjTables& T, int n_ctas, double e) {
 // Picks the work schedule: `forced_split_q` > 0 forces the balanced split
 // with a per-item overhead of forced_split_q / 4 tasks, `forced` > 0 the
 // longest-first assignment of chunks of at most `forced` tasks; otherwise the
-// candidate (chunk sizes, and the balanced split with a half-task overhead)
-// with the smallest estimate of the busiest CTA. Then lays out, for every
-// warp, its part of each of its CTA's items: warp w of a CTA runs tasks
+// candidate (chunk sizes, and the balanced split with the model's item
+// overhead) with the smallest estimate of the latest CTA. CTA speeds follow
+// the priority skew skew_pm (permille; see cta_speed). Then lays out, for
+// every warp, its part of each of its CTA's items: warp w of a CTA runs tasks
 // [b + w*n/NW, b + (w+1)*n/NW) of an item of n tasks; the warps' item lists
 // are parallel (same tiles, same order) and every warp's tasks are stored
 // contiguously.
-void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q) {
+void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q, int skew_pm) {
     const std::vector<int>& begin = T.tile_task_begin;
     const int nw = T.nw;
     const int n_ctas = n_warps / nw;
     T.n_warps = n_ctas * nw;
-    constexpr int kModelSplitQ = 2;
+    constexpr int kModelSplitQ = 12;   // the item overhead of item_cost, in quarter tasks
     int split_q = 0;
     if (forced_split_q > 0) {
         split_q = forced_split_q;
@@ -463,25 +486,27 @@ void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q) {
         double best_load = -1.0;
         for (int c : cands) {
             make_items(T, begin, c);
-            const double load = assign_ctas(T, n_ctas);
+            const double load = assign_ctas(T, n_ctas, skew_pm);
             if (best_load < 0 || load < best_load - 1e-9) {
                 best_load = load;
                 best = c;
             }
         }
-        if (forced <= 0 && split_items(T, n_ctas, kModelSplitQ / 4.0) < best_load - 1e-9) {
+        if (forced <= 0 &&
+            split_items(T, n_ctas, kModelSplitQ / 4.0, skew_pm) < best_load - 1e-9) {
             split_q = kModelSplitQ;
         } else {
             make_items(T, begin, best);
-            T.max_warp_load = assign_ctas(T, n_ctas);
+            T.max_warp_load = assign_ctas(T, n_ctas, skew_pm);
             T.per_item = best;
         }
     }
     if (split_q > 0) {
-        T.max_warp_load = split_items(T, n_ctas, split_q / 4.0);
+        T.max_warp_load = split_items(T, n_ctas, split_q / 4.0, skew_pm);
         T.per_item = 0;
     }
     T.split_q = split_q;
+    T.skew_pm = skew_pm;
     T.witems.clear();
     T.warp_begin.assign(1, 0);
     std::vector<TaskDesc> wt;
@@ -756,9 +781,13 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                 for (int tx = tx0; tx <= tx1; ++tx)
                     per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));
         }
+        // Tiles no footprint meets hold H f = 0 whatever f is: they are left out
+        // of the lists (the raw forward zeroes its output first; the ratio's
+        // u copies and the tile statistics are zero there).
         std::vector<int> begin{0};
         for (int ty = 0; ty < nty; ++ty)
             for (int tx = 0; tx < ntx; ++tx) {
+                if (per_tile[static_cast<size_t>(ty) * ntx + tx].empty()) continue;
                 TileDesc td{};
                 td.x0 = tx * TX;
                 td.y0 = ty * TY;
@@ -781,7 +810,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                 begin.push_back(static_cast<int>(T.tile_tasks.size()));
             }
         T.tile_task_begin = std::move(begin);
-        schedule(T, warps_fwd, P->forced_per_item, P->forced_split_q);
+        schedule(T, warps_fwd, P->forced_per_item, P->forced_split_q, P->forced_skew_pm);
     }
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
@@ -820,7 +849,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                     begin.push_back(static_cast<int>(T.tile_tasks.size()));
                 }
         T.tile_task_begin = std::move(begin);
-        schedule(T, warps_adj, P->forced_per_item, P->forced_split_q);
+        schedule(T, warps_adj, P->forced_per_item, P->forced_split_q, P->forced_skew_pm);
     }
 
     // ---- device buffers
@@ -917,7 +946,20 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
 }
 
 // Forward pass from the plan's datacube copies.
+// The raw forward's output outside the listed tiles (no footprint meets
+// them, H f = 0 there) is zeroed before the launch.
+int zero_raw_output(const GatherParams& p, cudaStream_t st) {
+    CTIS_CUDA(cudaMemset2DAsync(p.out_f32, sizeof(float) * static_cast<size_t>(p.out_pitch), 0,
+                                sizeof(float) * static_cast<size_t>(p.out_w),
+                                static_cast<size_t>(p.out_h), st));
+    return CTIS_OK;
+}
+
 int enqueue_forward(const ctis_plan* P, GatherParams p, cudaStream_t st) {
+    if (p.mode == kEpiRaw) {
+        const int rc = zero_raw_output(p, st);
+        if (rc) return rc;
+    }
     CUtensorMap win;
     const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
     int rc = make_map(&win, P->d_fwork, P->dtype, P->a + P->f_copies - 1, P->alpha,
@@ -983,6 +1025,15 @@ int scatter_u(const ctis_plan* P, const float* src, cudaStream_t st) {
     return CTIS_OK;
 }
 
+// Zeroes the FPA copies (the ratio forward leaves the pixels outside every
+// footprint untouched; they must read as zero, whatever an earlier call
+// scattered there).
+int zero_u(const ctis_plan* P, cudaStream_t st) {
+    CTIS_CUDA(cudaMemsetAsync(P->d_u, 0,
+                              sizeof(float) * static_cast<size_t>(P->u_copy_stride) * P->u_copies, st));
+    return CTIS_OK;
+}
+
 void set_f_copies(const ctis_plan* P, GatherParams& p) {
     p.f_in = P->d_fwork;
     p.f_out = P->d_fwork;
@@ -1002,7 +1053,8 @@ int record(ctis_plan* P, int idx, cudaStream_t st) {
 // Enqueues the whole reconstruction on `st`.
 int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
                         double* stats, cudaStream_t st) {
-    int rc;
+    int rc = zero_u(P, st);   // the ratio writes u only where H f can be nonzero
+    if (rc) return rc;
     if (flags & CTIS_INIT_ONES) {
         rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
     } else if (flags & CTIS_INIT_HTG) {
@@ -1462,7 +1514,7 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
                         const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
                         const float* psf_val, int dtype, const ctis_plan_options* opt) {
     if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
-    int forced_per_item = 0, forced_split_q = 0;
+    int forced_per_item = 0, forced_split_q = 0, forced_skew_pm = 0;
     if (opt) {
         if (opt->struct_size != static_cast<int>(sizeof(ctis_plan_options)))
             return fail(CTIS_ERR_INVALID_ARG, "ctis_plan_options.struct_size mismatch");
@@ -1474,8 +1526,11 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
             return fail(CTIS_ERR_INVALID_ARG, "item_overhead_q out of range");
         if (opt->tasks_per_item > 0 && opt->item_overhead_q > 0)
             return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item and item_overhead_q are exclusive");
+        if (opt->cta_skew_permille < 0 || opt->cta_skew_permille > 900)
+            return fail(CTIS_ERR_INVALID_ARG, "cta_skew_permille out of range [0, 900]");
         forced_per_item = opt->tasks_per_item;
         forced_split_q = opt->item_overhead_q;
+        forced_skew_pm = opt->cta_skew_permille;
     }
     *out = nullptr;
     if (a < 1 || alpha < 1 || w < 1 || gamma < 1 || xi < 1)
@@ -1517,6 +1572,7 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     P->u_copies = gather_input_copies(false, dtype);
     P->forced_per_item = forced_per_item;
     P->forced_split_q = forced_split_q;
+    P->forced_skew_pm = forced_skew_pm;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
@@ -1569,6 +1625,8 @@ int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
     info->adj_load_milli = static_cast<int64_t>(P->adj.max_warp_load * 1000.0);
     info->fwd_split_q = P->fwd.split_q;
     info->adj_split_q = P->adj.split_q;
+    info->fwd_skew_pm = P->fwd.skew_pm;
+    info->adj_skew_pm = P->adj.skew_pm;
     return CTIS_OK;
 }
 
@@ -1775,6 +1833,8 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     p.out_f32 = hf_dev;
     p.out_pitch = P->gamma;
     p.out_plane_stride = 0;
+    rc = zero_raw_output(p, st);
+    if (rc) return rc;
     CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
     return CTIS_OK;
 }
@@ -1875,7 +1935,9 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     };
 
     // ---- k EM updates (Eq. 2) from f0 or ones, keeping every iterate
-    rc = f0_dev ? scatter_f(P, f0_dev, kDtypeF32, 0.f, st) : scatter_f(P, nullptr, kDtypeF32, 1.f, st);
+    rc = zero_u(P, st);
+    if (!rc)
+        rc = f0_dev ? scatter_f(P, f0_dev, kDtypeF32, 0.f, st) : scatter_f(P, nullptr, kDtypeF32, 1.f, st);
     if (rc) return rc;
     GatherParams pf = base_params(P, P->fwd);
     pf.mode = kEpiRatio;
@@ -2127,18 +2189,22 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
     // candidates: the model's choice, chunks of 16..192 tasks (longest-first),
     // and the balanced split with item overheads of 0.5..6 tasks
     struct Cand {
-        int chunk, split_q;
+        int chunk, split_q, skew_pm;
     };
-    std::vector<Cand> cands{{0, 0}};
-    for (int c : {16, 24, 32, 48, 64, 96, 128, 192}) cands.push_back({c, 0});
-    for (int q : {2, 4, 8, 12, 16, 24}) cands.push_back({0, q});
+    std::vector<Cand> cands{{0, 0, 0}};
+    for (int c : {16, 24, 32, 48, 64, 96, 128, 192}) cands.push_back({c, 0, 0});
+    for (int q : {2, 4, 8, 12, 16, 24}) cands.push_back({0, q, 0});
+    for (int skew : {100, 200, 300}) {   // the CTA priority skew, on the likeliest shapes
+        for (int c : {64, 96, 128}) cands.push_back({c, 0, skew});
+        for (int q : {12, 16, 20}) cands.push_back({0, q, skew});
+    }
     int result = CTIS_OK;
     for (ProjTables* T : {&P->fwd, &P->adj}) {
         const bool forward = T == &P->fwd;
         float best_ms = -1.f;
-        Cand best{0, 0};
+        Cand best{0, 0, 0};
         for (const Cand& c : cands) {
-            schedule(*T, T->n_warps, c.chunk, c.split_q);
+            schedule(*T, T->n_warps, c.chunk, c.split_q, c.skew_pm);
             if (c.chunk != 0 && T->per_item != c.chunk) continue;
             result = reupload(*T);
             for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
@@ -2152,11 +2218,11 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
             if (result) break;
             if (best_ms < 0.f || ms < best_ms) {
                 best_ms = ms;
-                best = {T->per_item, T->split_q};
+                best = {T->per_item, T->split_q, T->skew_pm};
             }
         }
         if (result) break;
-        schedule(*T, T->n_warps, best.chunk, best.split_q);
+        schedule(*T, T->n_warps, best.chunk, best.split_q, best.skew_pm);
         result = reupload(*T);
         if (result) break;
     }

@@ -13,8 +13,10 @@ from tests.helpers import floored_rel, problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-CANDIDATES = ({("chunk", c) for c in (16, 24, 32, 48, 64, 96, 128, 192)}
-              | {("split", q) for q in (2, 4, 8, 12, 16, 24)})
+CANDIDATES = ({("chunk", c, 0) for c in (16, 24, 32, 48, 64, 96, 128, 192)}
+              | {("split", q, 0) for q in (2, 4, 8, 12, 16, 24)}
+              | {("chunk", c, s) for c in (64, 96, 128) for s in (100, 200, 300)}
+              | {("split", q, s) for q in (12, 16, 20) for s in (100, 200, 300)})
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +66,9 @@ def test_autotune_full_size_stays_within_tolerance_of_untuned():
 
 
 @pytest.mark.parametrize("opts", [dict(tasks_per_item=24), dict(item_overhead_q=2),
-                                  dict(item_overhead_q=24)])
+                                  dict(item_overhead_q=24),
+                                  dict(tasks_per_item=16, cta_skew_permille=300),
+                                  dict(item_overhead_q=4, cta_skew_permille=500)])
 def test_forced_schedules_match_oracle(opts):
     """Every schedule form (chunks assigned longest first; the balanced split,
     whose runs cut tiles into chunks on consecutive CTAs) gives the EM
@@ -75,7 +79,8 @@ def test_forced_schedules_match_oracle(opts):
         ref, _ = O.mlem(H, g, wl.k)
         with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, **opts) as plan:
             kind = "chunk" if "tasks_per_item" in opts else "split"
-            assert all(s[0] == kind for s in plan.schedules())
+            skew = opts.get("cta_skew_permille", 0)
+            assert all(s[0] == kind and s[2] == skew for s in plan.schedules())
             gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
             got, _ = plan.reconstruct(gt, k=wl.k, init="ones")
             plan.check()
@@ -90,3 +95,5 @@ def test_schedule_options_are_exclusive():
     with pytest.raises(CtisError):
         Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), tasks_per_item=16,
              item_overhead_q=4)
+    with pytest.raises(CtisError):
+        Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), cta_skew_permille=901)
