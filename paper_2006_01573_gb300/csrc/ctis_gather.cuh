@@ -424,7 +424,8 @@ __device__ __forceinline__ void load_row(const T* p, int n_valid, bool aligned, 
 // writes the C-aligned group [col0, col0 + C) of that copy with one vector
 // store; the values come from this lane and its left neighbours (warp
 // shuffles, same lane row). Groups cut by the tile edge, and the q values
-// that spill past the tile's right edge, are written element by element.
+// that spill past the tile's right edge, are written as aligned 8- and
+// 4-byte pieces in a full float32 tile, element by element otherwise.
 template <typename T, int C, int LX>
 __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int ncopies, bool active,
                                              int tx, int tile_cols, const float (&v)[C]) {
@@ -440,6 +441,49 @@ __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int 
 #pragma unroll
         for (int j = 0; j < C; ++j) left[d - 1][j] = __shfl_up_sync(0xffffffffu, v[j], d);
     if (!active) return;
+    if constexpr (sizeof(T) == 4 && C == 4) {
+        // A full float32 tile (the common case; uniform over the warp): the
+        // groups that straddle the tile's edges are written as aligned
+        // 8- and 4-byte pieces instead of element by element.
+        if (tile_cols == LX * C) {
+#pragma unroll
+            for (int q = 0; q < NCMAX; ++q) {
+                if (q >= ncopies) break;
+                T* dst = row + q * copy_stride;
+                float a[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) a[j] = j >= q ? v[j - q] : left[0][j - q + C];
+                if (q == 0 || tx >= 1) {
+                    DBG_CHECK_RANGE(dst + col0, C);
+                    Vec<T, C>::store(dst + col0, a);
+                } else if (q == 1) {   // left edge: columns 1..3 of the group
+                    DBG_CHECK_RANGE(dst + 1, 3);
+                    dst[1] = v[0];
+                    *reinterpret_cast<float2*>(dst + 2) = make_float2(v[1], v[2]);
+                } else if (q == 2) {
+                    DBG_CHECK_RANGE(dst + 2, 2);
+                    *reinterpret_cast<float2*>(dst + 2) = make_float2(v[0], v[1]);
+                } else {
+                    DBG_CHECK_RANGE(dst + 3, 1);
+                    dst[3] = v[0];
+                }
+                // right edge: the last q source columns land past the tile
+                if (q >= 1 && tx == LX - 1) {
+                    T* sp = dst + LX * C;
+                    DBG_CHECK_RANGE(sp, q);
+                    if (q == 1) {
+                        sp[0] = v[3];
+                    } else if (q == 2) {
+                        *reinterpret_cast<float2*>(sp) = make_float2(v[2], v[3]);
+                    } else {
+                        *reinterpret_cast<float2*>(sp) = make_float2(v[1], v[2]);
+                        sp[2] = v[3];
+                    }
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < NCMAX; ++q) {
         if (q >= ncopies) break;
