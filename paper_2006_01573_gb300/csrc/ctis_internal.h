@@ -118,7 +118,11 @@ struct GatherParams {
     // workspace
     float* scratch;            // partial tiles, [slots][TX*TY]
     int* tickets;              // [n_tiles], zero between launches
-    int* counters;             // [3] error flag (others unused)
+    int* counters;             // [3] error flag, [8 + f] frame f's statistics ticket
+    // placement probe: when set, each CTA writes its SM id to smid_out[CTA],
+    // stays resident ~30 us (so the grid is placed as a real launch is) and
+    // returns without touching anything else
+    int* smid_out;
     double* tile_stats;        // [n_tiles][kNumStats] written by kEpiRatio with_stats
 };
 

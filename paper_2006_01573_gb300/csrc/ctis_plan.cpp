@@ -19,6 +19,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -96,6 +97,7 @@ struct ProjTables {
     int per_item = 0;              // chunk size of the longest-first schedule (0: split)
     int split_q = 0;               // balanced split: item overhead in quarter tasks (0: chunks)
     int skew_pm = 0;               // CTA priority skew of the schedule (permille)
+    std::vector<int> block_sm;     // SM of each CTA in a launch of this grid (probed; may be empty)
     int n_warps = 0;
     double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
@@ -289,19 +291,50 @@ void make_items(ProjTables& T, const std::vector<int>& tile_task_begin, int per_
     }
 }
 
-// Writes the CTAs' item lists in order of decreasing estimated load (ties:
-// original order). The SM's warp schedulers favour the warps of the CTAs that
-// became resident first (the lower block indices), so those run their tasks
-// faster while all CTAs are active; the heaviest lists go to them.
+// Writes the CTAs' item lists. The SM's warp schedulers favour the warps of
+// the CTAs that became resident first (the lower block indices), so those run
+// their tasks faster while all CTAs are active, and an SM finishes with its
+// last CTA. Without a placement map the lists go to the CTAs in order of
+// decreasing estimated load (ties: original order). With the probed map of
+// CTAs to SMs, the lists, heaviest first, go to the SM with the least load
+// that still has a free CTA (ties: lower SM id), so the SMs' totals are
+// balanced, and each SM's lists go to its CTAs heaviest first in block order.
+// Either way every list runs exactly once: the map only decides which CTA.
 void place_ctas(ProjTables& T, const std::vector<std::vector<int>>& per_cta,
                 const std::vector<double>& load) {
-    std::vector<int> ord(per_cta.size());
+    const int n = static_cast<int>(per_cta.size());
+    std::vector<int> ord(n);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return load[x] > load[y]; });
+    std::vector<int> list_of(n);   // block -> list
+    if (static_cast<int>(T.block_sm.size()) == n) {
+        std::map<int, std::vector<int>> blocks;   // SM -> its blocks, ascending
+        for (int b = 0; b < n; ++b) blocks[T.block_sm[b]].push_back(b);
+        struct Sm {
+            std::vector<int> blocks, lists;
+            double load = 0.0;
+        };
+        std::vector<Sm> sms;
+        for (auto& kv : blocks) sms.push_back({kv.second, {}, 0.0});
+        for (int l : ord) {
+            int best = -1;
+            for (int k = 0; k < static_cast<int>(sms.size()); ++k) {
+                if (sms[k].lists.size() >= sms[k].blocks.size()) continue;
+                if (best < 0 || sms[k].load < sms[best].load - 1e-9) best = k;
+            }
+            sms[best].lists.push_back(l);   // lists arrive heaviest first
+            sms[best].load += load[l];
+        }
+        for (const Sm& sm : sms)
+            for (size_t k = 0; k < sm.blocks.size(); ++k) list_of[sm.blocks[k]] = sm.lists[k];
+    } else {
+        for (int b = 0; b < n; ++b) list_of[b] = ord[b];
+    }
     T.cta_begin.assign(1, 0);
     T.cta_items.clear();
-    for (int c : ord) {
-        T.cta_items.insert(T.cta_items.end(), per_cta[c].begin(), per_cta[c].end());
+    for (int b = 0; b < n; ++b) {
+        const std::vector<int>& items = per_cta[list_of[b]];
+        T.cta_items.insert(T.cta_items.end(), items.begin(), items.end());
         T.cta_begin.push_back(static_cast<int>(T.cta_items.size()));
     }
 }
@@ -898,6 +931,31 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     return CTIS_OK;
 }
 
+// Replaces the device copies of a projector's work lists after a new
+// schedule (and grows the chunk scratch when the schedule needs more).
+int reupload_tables(ctis_plan* P, ProjTables& T) {
+    cudaFree(T.d_tasks);
+    cudaFree(T.d_warp_begin);
+    cudaFree(T.d_witems);
+    T.d_tasks = nullptr;
+    T.d_warp_begin = nullptr;
+    T.d_witems = nullptr;
+    int r = upload(P, &T.d_tasks, T.tasks);
+    if (!r) r = upload(P, &T.d_warp_begin, T.warp_begin);
+    if (!r) r = upload(P, &T.d_witems, T.witems);
+    if (r) return r;
+    const int64_t need = T.scratch_slots * T.tile_w * T.tile_h;
+    if (need > P->scratch_capacity) {
+        cudaFree(P->d_scratch);
+        P->d_scratch = nullptr;
+        P->scratch_capacity = 0;
+        r = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch), sizeof(float) * need);
+        if (r) return r;
+        P->scratch_capacity = need;
+    }
+    return CTIS_OK;
+}
+
 int check_plan(const ctis_plan* P) {
     if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
     int cur = -1;
@@ -978,6 +1036,44 @@ int enqueue_adjoint(const ctis_plan* P, GatherParams p, cudaStream_t st) {
                       gather_window_rows(false, P->K, P->dtype));
     if (rc) return rc;
     CTIS_CUDA(gather_launch(false, P->K, P->dtype, win, p, st));
+    return CTIS_OK;
+}
+
+// Records which SM each CTA of the projector's launch lands on: one launch of
+// the EM kernel itself (same resources, so the same placement) in probe mode.
+// The map is only a scheduling hint; on any failure it is left empty.
+void probe_placement(ctis_plan* P, ProjTables& T, bool forward) {
+    T.block_sm.clear();
+    const int n = T.n_warps / T.nw;
+    int* d = nullptr;
+    if (n <= 0 || cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    GatherParams p = base_params(P, T);
+    p.mode = forward ? kEpiRatio : kEpiUpdate;   // the EM loop's instantiations
+    p.smid_out = d;
+    const int rc = forward ? enqueue_forward(P, p, nullptr) : enqueue_adjoint(P, p, nullptr);
+    std::vector<int> h(n, -1);
+    if (rc == CTIS_OK && cudaMemcpy(h.data(), d, sizeof(int) * n, cudaMemcpyDeviceToHost) == cudaSuccess) {
+        bool ok = true;
+        for (int v : h) ok = ok && v >= 0 && v < 4096;
+        if (ok) T.block_sm = std::move(h);
+    }
+    cudaGetLastError();
+    cudaFree(d);
+}
+
+// Probes both projectors' placements and, when the maps came back, lays the
+// work lists out again with them (same schedule parameters) and re-uploads.
+int place_by_probe(ctis_plan* P) {
+    for (ProjTables* T : {&P->fwd, &P->adj}) {
+        probe_placement(P, *T, T == &P->fwd);
+        if (T->block_sm.empty()) continue;
+        schedule(*T, T->n_warps, T->per_item, T->split_q, T->skew_pm);
+        const int rc = reupload_tables(P, *T);
+        if (rc) return rc;
+    }
     return CTIS_OK;
 }
 
@@ -1584,6 +1680,11 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
         return cuda_fail(e, "no usable CUDA device");
     }
     int rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
+    if (!rc) rc = place_by_probe(P);
+    if (!rc) {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e, "placing the work lists");
+    }
     if (rc) {
         destroy(P);
         return rc;
@@ -2141,28 +2242,7 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
             return cuda_fail(e, "cudaEventCreate");
         }
     }
-    auto reupload = [&](ProjTables& T) -> int {
-        cudaFree(T.d_tasks);
-        cudaFree(T.d_warp_begin);
-        cudaFree(T.d_witems);
-        T.d_tasks = nullptr;
-        T.d_warp_begin = nullptr;
-        T.d_witems = nullptr;
-        int r = upload(P, &T.d_tasks, T.tasks);
-        if (!r) r = upload(P, &T.d_warp_begin, T.warp_begin);
-        if (!r) r = upload(P, &T.d_witems, T.witems);
-        if (r) return r;
-        const int64_t need = T.scratch_slots * T.tile_w * T.tile_h;
-        if (need > P->scratch_capacity) {
-            cudaFree(P->d_scratch);
-            P->d_scratch = nullptr;
-            P->scratch_capacity = 0;
-            r = dmalloc(P, reinterpret_cast<void**>(&P->d_scratch), sizeof(float) * need);
-            if (r) return r;
-            P->scratch_capacity = need;
-        }
-        return CTIS_OK;
-    };
+    auto reupload = [&](ProjTables& T) -> int { return reupload_tables(P, T); };
     // the EM launches (ratio with statistics; update) on the candidate tables
     auto run = [&](bool forward) -> int {
         if (forward) {
