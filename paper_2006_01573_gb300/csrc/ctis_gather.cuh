@@ -624,46 +624,52 @@ __device__ __forceinline__ void load_stats(const double* src, double (&d)[kNumSt
     d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
 }
 
-// Float64 sum over the warp of four values per lane, as a reduce-scatter
+// Sum over the warp of four float32 values per lane, as a reduce-scatter
 // (fixed tree, same on every run): the first two levels halve the set of
 // values a lane carries (lanes with bit 4 clear keep values 0 and 1, the
-// others 2 and 3; then bit 3 picks one of the two), the last three add
-// within groups of eight lanes. Six float64 additions per lane instead of
-// twenty; lane l ends with the total of value l >> 3 (all eight lanes of a
-// group hold it).
-__device__ __forceinline__ double warp_sum4(const double (&v)[kNumStats], int lane) {
+// others 2 and 3; then bit 3 picks one of the two) in float32, so each lane
+// holds a float32 sum of four lanes' values; that is widened to float64 and
+// the last three levels add within groups of eight lanes. One conversion and
+// three float64 additions per lane (float64 runs at 1/64 of the float32
+// rate here); lane l ends with the total of value l >> 3 (all eight lanes of
+// a group hold it).
+__device__ __forceinline__ double warp_sum4(const float (&v)[kNumStats], int lane) {
     static_assert(kNumStats == 4, "four values per lane");
     const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-    const double k0 = hi16 ? v[2] : v[0], k1 = hi16 ? v[3] : v[1];
-    const double s0 = hi16 ? v[0] : v[2], s1 = hi16 ? v[1] : v[3];
-    const double a0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
-    const double a1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
-    double m = (hi8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi8 ? a0 : a1, 8);
+    const float k0 = hi16 ? v[2] : v[0], k1 = hi16 ? v[3] : v[1];
+    const float s0 = hi16 ? v[0] : v[2], s1 = hi16 ? v[1] : v[3];
+    const float a0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+    const float a1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+    const float m32 = (hi8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi8 ? a0 : a1, 8);
+    double m = static_cast<double>(m32);
 #pragma unroll
     for (int off = 4; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
     return m;
 }
 
-// Statistics of one finished tile: each warp's per-lane float32 sums (32
-// elements each) widened to float64 and added by warp_sum4, then the CTA's
-// warps' values added in warp order (lanes 0..3 of warp 0, one value each),
-// which store the tile's four values. The frame totals are added later, in
-// fixed order, by reduce_frame_slice (at the start of the next launch in
-// stream order), so no fence or atomic sits on the tile's path.
-template <int NW, int THREADS>
-__device__ __forceinline__ void store_tile_stats(const GatherParams& p, int tile_idx,
-                                                 const float (&stat)[kNumStats], int warp, int lane,
+// Statistics of one finished tile, per warp: the warp's sum (warp_sum4) of
+// its lanes' float32 sums goes to tstat[warp][0..3] in shared memory. The
+// CTA's warps' values are added later, in warp order, by flush_tile_stats,
+// after the next CTA barrier (no barrier of its own on the tile's path); the
+// frame totals are added in fixed order by reduce_frame_slice at the start
+// of the next launch in stream order.
+__device__ __forceinline__ void store_tile_stats(const float (&stat)[kNumStats], int warp, int lane,
                                                  double* tstat) {
-    double d[kNumStats];
-#pragma unroll
-    for (int q = 0; q < kNumStats; ++q) d[q] = static_cast<double>(stat[q]);
-    const double tot = warp_sum4(d, lane);
+    const double tot = warp_sum4(stat, lane);
     if ((lane & 7) == 0) tstat[warp * kNumStats + (lane >> 3)] = tot;
-    cta_barrier(THREADS);
+}
+
+// Lanes 0..3 of warp 0 add the NW warps' values of `tile` in warp order and
+// store the tile's four statistics. Called by every warp after a CTA barrier
+// that follows all warps' store_tile_stats for the tile, and before the
+// barrier after which they may write tstat again.
+template <int NW>
+__device__ __forceinline__ void flush_tile_stats(const GatherParams& p, int tile, int warp,
+                                                 int lane, const double* tstat) {
     if (warp == 0 && lane < kNumStats) {
         double t = tstat[lane];
         for (int w = 1; w < NW; ++w) t += tstat[w * kNumStats + lane];
-        __stcg(p.tile_stats + (long long)tile_idx * kNumStats + lane, t);
+        __stcg(p.tile_stats + (long long)tile * kNumStats + lane, t);
     }
 }
 
@@ -797,6 +803,10 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
 #pragma unroll
     for (int j = 0; j < G::NS; ++j) issue_next();
 
+    // kEpiRatio with statistics: the tile whose per-warp sums wait in tstat
+    // for the CTA combine after the next barrier (-1: none; uniform)
+    int stats_tile = -1;
+    double* tstat = reinterpret_cast<double*>(smem_raw + G::TSTAT_OFF);
     for (int ii = ib; ii < ie; ++ii) {
         const WorkItem it = next_it;
         if (ii + 1 < ie) next_it = p.items[ii + 1];   // prefetch; used next item
@@ -944,6 +954,12 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             }
         }
         cta_barrier(G::THREADS);
+        if constexpr (MODE == kEpiRatio) {
+            if (stats_tile >= 0) {   // the previous finished tile's statistics
+                flush_tile_stats<G::NW>(p, stats_tile, warp, lane, tstat);
+                stats_tile = -1;
+            }
+        }
         float ve[ER][C];
 #pragma unroll
         for (int o = 0; o < ER; ++o) {
@@ -1012,11 +1028,17 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
             epilogue<G, TF, MODE, ER>(p, it, tx, ty, warp * ER, ve, ein, stat);
             if constexpr (MODE == kEpiRatio) {
-                if (p.with_stats)   // uniform over the launch: every warp takes the barrier
-                    store_tile_stats<G::NW, G::THREADS>(
-                        p, it.tile, stat, warp, lane,
-                        reinterpret_cast<double*>(smem_raw + G::TSTAT_OFF));
+                if (p.with_stats) {   // uniform over the launch
+                    store_tile_stats(stat, warp, lane, tstat);
+                    stats_tile = it.tile;
+                }
             }
+        }
+    }
+    if constexpr (MODE == kEpiRatio) {
+        if (stats_tile >= 0) {   // the last finished tile's statistics
+            cta_barrier(G::THREADS);
+            flush_tile_stats<G::NW>(p, stats_tile, warp, lane, tstat);
         }
     }
 
