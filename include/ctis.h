@@ -111,6 +111,44 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
                         const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
                         const float* psf_val, int dtype, const ctis_plan_options* opt);
 
+/* Host-only view of the tables a plan would build (no device is touched):
+ * for one projector (forward != 0: FPA tiles x spot clusters, Eqs. 8 and 12;
+ * else voxel tiles x the clusters of their wavelength, Eq. 14), the PSF is
+ * merged and clustered as ctis_plan_create does, and the work lists are built
+ * and scheduled (options as in ctis_plan_options) over n_ctas persistent CTAs
+ * of info.warps_per_cta warps. block_sm: NULL, or [n_ctas] the SM id of each
+ * CTA (as the plan's placement probe reports; ids in [0, 4096)). The outputs
+ * are host arrays sized from info (fill info first with all arrays NULL,
+ * then call again); any array may be NULL:
+ *   clusters      [3 * clusters]  (s, X, Y): wavelength and FPA origin of each
+ *                                 K x K spot cluster
+ *   tile_xyp      [3 * tiles]     (x0, y0, plane) of each output tile
+ *   tile_task_ptr [tiles + 1]     CSR offsets of the tiles' tasks
+ *   task_cluster  [tasks]         the cluster of each task, tile order
+ *   warp_begin    [warps + 1]     each warp's range of work items
+ *   item_tile     [witems]        the tile of each warp's work item
+ *   item_chunk    [2 * witems]    (chunk index, chunks of the tile)
+ *   item_range    [2 * witems]    [begin, end) of the item's tasks, in tile
+ *                                 task order (warp w of a CTA runs the w-th
+ *                                 part of the CTA's item)
+ * Errors: those of ctis_plan_create (except device ones); CTIS_ERR_INVALID_ARG
+ * for a bad n_ctas, block_sm or info. */
+typedef struct {
+    int struct_size;       /* sizeof(ctis_tables_info), set by the caller */
+    int64_t clusters, cluster_k, tiles, tasks, witems, warps, warps_per_cta;
+    int64_t tile_w, tile_h;
+    int64_t chunk, split_q, skew_pm;   /* the schedule, as in ctis_plan_info */
+    int64_t load_milli;                /* estimated latest CTA, tasks per warp x1000 */
+} ctis_tables_info;
+
+int ctis_tables_inspect(int a, int alpha, int w, int gamma, int xi, const int32_t* psf_ptr,
+                        const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, int dtype,
+                        const ctis_plan_options* opt, int forward, int n_ctas,
+                        const int32_t* block_sm, ctis_tables_info* info, int32_t* clusters,
+                        int32_t* tile_xyp, int32_t* tile_task_ptr, int32_t* task_cluster,
+                        int32_t* warp_begin, int32_t* item_tile, int32_t* item_chunk,
+                        int32_t* item_range);
+
 /* Release the plan and its device memory (synchronises the device first).
  * NULL is accepted. */
 int ctis_plan_destroy(ctis_plan* plan);

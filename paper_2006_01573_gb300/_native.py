@@ -27,7 +27,7 @@ EXPORTED = (
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
-    "ctis_plan_autotune",
+    "ctis_plan_autotune", "ctis_tables_inspect",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -45,6 +45,12 @@ class PlanInfo(ctypes.Structure):
         "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
         "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q", "fwd_skew_pm",
         "adj_skew_pm")]
+
+
+class TablesInfo(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int)] + [(name, ctypes.c_int64) for name in (
+        "clusters", "cluster_k", "tiles", "tasks", "witems", "warps", "warps_per_cta", "tile_w",
+        "tile_h", "chunk", "split_q", "skew_pm", "load_milli")]
 
 
 class PlanOptions(ctypes.Structure):
@@ -87,6 +93,9 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
         "ctis_unrolled_nll_grad": (I, [P, VP, VP, I, VP, VP, VP, VP]),
+        "ctis_tables_inspect": (I, [I, I, I, I, I, i32p, i32p, i32p, f32p, I,
+                                    ctypes.POINTER(PlanOptions), I, I, i32p,
+                                    ctypes.POINTER(TablesInfo)] + [i32p] * 8),
         "ctis_status_string": (ctypes.c_char_p, [I]),
         "ctis_last_error": (ctypes.c_char_p, []),
     }
@@ -115,6 +124,45 @@ def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def tables_inspect(a, alpha, w, gamma, xi, psf, forward: bool, n_ctas: int, dtype: str = "f32",
+                   block_sm=None, tasks_per_item: int = 0, item_overhead_q: int = 0,
+                   cta_skew_permille: int = 0) -> dict:
+    """Host-only view of one projector's work lists and schedule
+    (ctis_tables_inspect; no device needed). Returns the info fields and the
+    arrays as numpy int32 arrays."""
+    lib = load()
+    ptr, _ = _arr(psf[0], np.int32)
+    x, _ = _arr(psf[1], np.int32)
+    y, _ = _arr(psf[2], np.int32)
+    v, _ = _arr(psf[3], np.float32)
+    i32 = lambda arr: None if arr is None else arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
+                      int(cta_skew_permille))
+    bsm = None if block_sm is None else np.ascontiguousarray(block_sm, dtype=np.int32)
+    dt = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
+    info = TablesInfo(ctypes.sizeof(TablesInfo))
+    args = [a, alpha, w, gamma, xi, i32(ptr), i32(x), i32(y),
+            v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), dt, ctypes.byref(opt),
+            1 if forward else 0, int(n_ctas), i32(bsm), ctypes.byref(info)]
+    _check(lib.ctis_tables_inspect(*args, *([None] * 8)))
+    n = {f: int(getattr(info, f)) for f, _ in TablesInfo._fields_[1:]}
+    out = {
+        "cluster_sxy": np.zeros((n["clusters"], 3), np.int32),
+        "tile_xyp": np.zeros((n["tiles"], 3), np.int32),
+        "tile_task_ptr": np.zeros(n["tiles"] + 1, np.int32),
+        "task_cluster": np.zeros(n["tasks"], np.int32),
+        "warp_begin": np.zeros(n["warps"] + 1, np.int32),
+        "item_tile": np.zeros(n["witems"], np.int32),
+        "item_chunk": np.zeros((n["witems"], 2), np.int32),
+        "item_range": np.zeros((n["witems"], 2), np.int32),
+    }
+    _check(lib.ctis_tables_inspect(*args, *(i32(out[k]) for k in (
+        "cluster_sxy", "tile_xyp", "tile_task_ptr", "task_cluster", "warp_begin", "item_tile",
+        "item_chunk", "item_range"))))
+    out.update(n)
+    return out
 
 
 class Plan:

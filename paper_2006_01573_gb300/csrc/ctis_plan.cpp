@@ -98,6 +98,7 @@ struct ProjTables {
     int split_q = 0;               // balanced split: item overhead in quarter tasks (0: chunks)
     int skew_pm = 0;               // CTA priority skew of the schedule (permille)
     std::vector<int> block_sm;     // SM of each CTA in a launch of this grid (probed; may be empty)
+    std::vector<std::pair<int, int>> witem_src;   // each warp item's range in tile_tasks
     int n_warps = 0;
     double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
@@ -188,6 +189,7 @@ struct ctis_plan {
     int forced_per_item = 0;          // 0: chosen by schedule()
     int forced_split_q = 0;           // 0: chosen by schedule()
     int forced_skew_pm = 0;           // CTA priority skew of the model's schedule
+    int host_ctas = 0;                // > 0: host-only tables for this many CTAs (no device)
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -541,6 +543,7 @@ void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q, int sk
     T.split_q = split_q;
     T.skew_pm = skew_pm;
     T.witems.clear();
+    T.witem_src.clear();
     T.warp_begin.assign(1, 0);
     std::vector<TaskDesc> wt;
     wt.reserve(T.tile_tasks.size());
@@ -563,6 +566,7 @@ void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q, int sk
                 wt.insert(wt.end(), T.tile_tasks.begin() + tb, T.tile_tasks.begin() + te);
                 wi.task_end = static_cast<int>(wt.size());
                 T.witems.push_back(wi);
+                T.witem_src.push_back({tb, te});
             }
             T.warp_begin.push_back(static_cast<int>(T.witems.size()));
         }
@@ -789,14 +793,16 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                         (long long)k);
     const int64_t ncl = static_cast<int64_t>(P->clusters.size());
 
-    CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
-    CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
-    {
+    int warps_fwd = P->host_ctas * gather_warps_per_cta(true);
+    int warps_adj = P->host_ctas * gather_warps_per_cta(false);
+    if (P->host_ctas == 0) {
+        CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
+        CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
         int grad_blocks = 0;   // runs on the adjoint's work lists and warp count
         CTIS_CUDA(psf_grad_prepare(K, P->dtype, &grad_blocks));
+        warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta(true);
+        warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta(false);
     }
-    const int warps_fwd = P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta(true);
-    const int warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta(false);
 
     // ---- forward work lists: FPA tiles x clusters whose footprint meets them
     {
@@ -884,6 +890,8 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         T.tile_task_begin = std::move(begin);
         schedule(T, warps_adj, P->forced_per_item, P->forced_split_q, P->forced_skew_pm);
     }
+
+    if (P->host_ctas > 0) return CTIS_OK;   // host-only tables
 
     // ---- device buffers
     for (ProjTables* T : {&P->fwd, &P->adj}) {
@@ -1606,9 +1614,14 @@ int ctis_plan_create(ctis_plan** out, int a, int alpha, int w, int gamma, int xi
                                dtype, nullptr);
 }
 
-int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
-                        const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
-                        const float* psf_val, int dtype, const ctis_plan_options* opt) {
+}  // extern "C"
+
+namespace {
+
+// Validates the arguments of a plan and allocates it (host fields only).
+int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const int32_t* psf_ptr,
+             const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, int dtype,
+             const ctis_plan_options* opt) {
     if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
     int forced_per_item = 0, forced_split_q = 0, forced_skew_pm = 0;
     if (opt) {
@@ -1672,6 +1685,22 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
+    *out = P;
+    return CTIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
+                        const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
+                        const float* psf_val, int dtype, const ctis_plan_options* opt) {
+    if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ctis_plan* P = nullptr;
+    const int rc0 = new_plan(&P, a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val, dtype, opt);
+    if (rc0) return rc0;
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
@@ -1690,6 +1719,78 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
         return rc;
     }
     *out = P;
+    return CTIS_OK;
+}
+
+int ctis_tables_inspect(int a, int alpha, int w, int gamma, int xi, const int32_t* psf_ptr,
+                        const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, int dtype,
+                        const ctis_plan_options* opt, int forward, int n_ctas,
+                        const int32_t* block_sm, ctis_tables_info* info, int32_t* clusters,
+                        int32_t* tile_xyp, int32_t* tile_task_ptr, int32_t* task_cluster,
+                        int32_t* warp_begin, int32_t* item_tile, int32_t* item_chunk,
+                        int32_t* item_range) {
+    if (!info || info->struct_size != static_cast<int>(sizeof(ctis_tables_info)))
+        return fail(CTIS_ERR_INVALID_ARG, "info is NULL or its struct_size mismatches");
+    if (n_ctas < 1 || n_ctas > 1 << 16) return fail(CTIS_ERR_INVALID_ARG, "n_ctas out of range");
+    if (block_sm)
+        for (int b = 0; b < n_ctas; ++b)
+            if (block_sm[b] < 0 || block_sm[b] >= 4096)
+                return fail(CTIS_ERR_INVALID_ARG, "block_sm[%d] = %d out of range", b, block_sm[b]);
+    ctis_plan* P = nullptr;
+    int rc = new_plan(&P, a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val, dtype, opt);
+    if (rc) return rc;
+    P->host_ctas = n_ctas;
+    if (block_sm) {
+        (forward ? P->fwd : P->adj).block_sm.assign(block_sm, block_sm + n_ctas);
+    }
+    rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
+    if (rc) {
+        delete P;   // host-only: nothing on the device
+        return rc;
+    }
+    const ProjTables& T = forward ? P->fwd : P->adj;
+    info->clusters = static_cast<int64_t>(P->clusters.size());
+    info->cluster_k = P->K;
+    info->tiles = static_cast<int64_t>(T.tiles.size());
+    info->tasks = static_cast<int64_t>(T.tile_tasks.size());
+    info->witems = static_cast<int64_t>(T.witems.size());
+    info->warps = T.n_warps;
+    info->warps_per_cta = T.nw;
+    info->tile_w = T.tile_w;
+    info->tile_h = T.tile_h;
+    info->chunk = T.per_item;
+    info->split_q = T.split_q;
+    info->skew_pm = T.skew_pm;
+    info->load_milli = static_cast<int64_t>(T.max_warp_load * 1000.0);
+    if (clusters)
+        for (size_t c = 0; c < P->clusters.size(); ++c) {
+            clusters[3 * c] = P->clusters[c].s;
+            clusters[3 * c + 1] = P->clusters[c].X;
+            clusters[3 * c + 2] = P->clusters[c].Y;
+        }
+    if (tile_xyp)
+        for (size_t t = 0; t < T.tiles.size(); ++t) {
+            tile_xyp[3 * t] = T.tiles[t].x0;
+            tile_xyp[3 * t + 1] = T.tiles[t].y0;
+            tile_xyp[3 * t + 2] = T.tiles[t].plane;
+        }
+    if (tile_task_ptr) std::copy(T.tile_task_begin.begin(), T.tile_task_begin.end(), tile_task_ptr);
+    if (task_cluster)
+        for (size_t k = 0; k < T.tile_tasks.size(); ++k) task_cluster[k] = T.tile_tasks[k].cluster;
+    if (warp_begin) std::copy(T.warp_begin.begin(), T.warp_begin.end(), warp_begin);
+    for (size_t i = 0; i < T.witems.size(); ++i) {
+        const WorkItem& wi = T.witems[i];
+        if (item_tile) item_tile[i] = wi.tile;
+        if (item_chunk) {
+            item_chunk[2 * i] = wi.chunk_info >> 16;
+            item_chunk[2 * i + 1] = wi.chunk_info & 0xffff;
+        }
+        if (item_range) {
+            item_range[2 * i] = T.witem_src[i].first;
+            item_range[2 * i + 1] = T.witem_src[i].second;
+        }
+    }
+    delete P;
     return CTIS_OK;
 }
 

@@ -1,0 +1,189 @@
+"""Host logic of the plan, checked on the CPU (ctis_tables_inspect: the plan's
+table builder and schedulers without a device).
+
+The work lists are checked against definitions written out here: a forward
+task (FPA tile, spot cluster) exists exactly when the cluster's footprint
+(its K x K box swept over the a x alpha field stop, Eqs. 8 and 12) meets the
+tile; an adjoint voxel tile of wavelength s has one task per cluster of s
+(Eq. 14). Every schedule form must run every task exactly once, with the
+CTA's warps sharing each item and each tile's chunks numbered in order; the
+probed CTA-to-SM map may only change which CTA runs which list."""
+import numpy as np
+import pytest
+
+import synth
+from paper_2006_01573_gb300 import CtisError, tables_inspect
+
+RAGGED = synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7, "mask_spectra", 100.0, 3)
+K5 = synth.Workload("k5", 20, 24, 6, 120, 110, 3, 36.0, 1.2, 5, 1.2, "segmentation", 100.0, 3)
+WORKLOADS = [synth.TINY, RAGGED, K5, synth.MODEL_A]
+
+
+def _inspect(wl, forward, n_ctas, **kw):
+    return tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), forward,
+                          n_ctas, **kw)
+
+
+def _tile_tasks(t):
+    ptr = t["tile_task_ptr"]
+    return {tuple(t["tile_xyp"][i]): sorted(t["task_cluster"][ptr[i]:ptr[i + 1]].tolist())
+            for i in range(t["tiles"])}
+
+
+@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
+def test_clusters_cover_every_psf_nonzero(wl):
+    ptr, x, y, _ = synth.make_psf(wl)
+    t = _inspect(wl, True, 8)
+    K = t["cluster_k"]
+    cl = t["cluster_sxy"]
+    for s in range(wl.w):
+        mine = cl[cl[:, 0] == s]
+        for k in range(ptr[s], ptr[s + 1]):
+            inside = ((mine[:, 1] <= x[k]) & (x[k] < mine[:, 1] + K)
+                      & (mine[:, 2] <= y[k]) & (y[k] < mine[:, 2] + K))
+            assert inside.any(), (s, x[k], y[k])
+    # every cluster box holds at least one nonzero of its wavelength
+    for s, X, Y in cl:
+        xs, ys = x[ptr[s]:ptr[s + 1]], y[ptr[s]:ptr[s + 1]]
+        assert np.any((X <= xs) & (xs < X + K) & (Y <= ys) & (ys < Y + K))
+
+
+@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
+def test_forward_tasks_are_the_footprint_overlaps(wl):
+    t = _inspect(wl, True, 8)
+    K, TW, TH = t["cluster_k"], t["tile_w"], t["tile_h"]
+    expect = {}
+    for c, (s, X, Y) in enumerate(t["cluster_sxy"]):
+        x0, x1 = X, X + wl.a + K - 1          # footprint [x0, x1) x [y0, y1)
+        y0, y1 = Y, Y + wl.alpha + K - 1
+        for ty in range(0, wl.xi, TH):
+            for tx in range(0, wl.gamma, TW):
+                if tx < x1 and x0 < tx + TW and ty < y1 and y0 < ty + TH:
+                    expect.setdefault((tx, ty, 0), []).append(c)
+    got = _tile_tasks(t)
+    assert got == {k: sorted(v) for k, v in expect.items()}   # no tile without a task
+
+
+@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
+def test_adjoint_tasks_are_the_clusters_of_the_plane(wl):
+    t = _inspect(wl, False, 8)
+    TW, TH = t["tile_w"], t["tile_h"]
+    cl = t["cluster_sxy"]
+    expect = {}
+    for s in range(wl.w):
+        of_s = sorted(np.nonzero(cl[:, 0] == s)[0].tolist())
+        for ty in range(0, wl.alpha, TH):
+            for tx in range(0, wl.a, TW):
+                expect[(tx, ty, s)] = of_s
+    assert _tile_tasks(t) == expect
+
+
+def _check_schedule(t):
+    """Every task once; CTA warps share items; chunks numbered in order."""
+    nw, wb = t["warps_per_cta"], t["warp_begin"]
+    ptr = t["tile_task_ptr"]
+    covered = np.zeros(t["tasks"], np.int64)
+    chunks = {}
+    lists = []
+    for cta in range(t["warps"] // nw):
+        ws = range(cta * nw, (cta + 1) * nw)
+        counts = {wb[w + 1] - wb[w] for w in ws}
+        assert len(counts) == 1, "the CTA's warps walk parallel lists"
+        items = []
+        for k in range(counts.pop()):
+            idx = [wb[w] + k for w in ws]
+            tiles = {t["item_tile"][i] for i in idx}
+            chk = {tuple(t["item_chunk"][i]) for i in idx}
+            assert len(tiles) == 1 and len(chk) == 1
+            tile, (chunk, nch) = tiles.pop(), chk.pop()
+            rs = [tuple(t["item_range"][i]) for i in idx]
+            for a, b in zip(rs, rs[1:]):      # warp w runs the w-th consecutive part
+                assert a[1] == b[0]
+            b0, e0 = rs[0][0], rs[-1][1]
+            assert ptr[tile] <= b0 <= e0 <= ptr[tile + 1]
+            covered[b0:e0] += 1
+            chunks.setdefault(tile, []).append((chunk, nch, b0, e0))
+            items.append((tile, chunk, b0, e0))
+        lists.append(tuple(items))
+    assert np.all(covered == 1), "every task runs exactly once"
+    assert set(chunks) == set(range(t["tiles"])), "every tile is an item"
+    for tile, cs in chunks.items():
+        cs.sort()
+        nch = cs[0][1]
+        assert [c[0] for c in cs] == list(range(nch)) and all(c[1] == nch for c in cs)
+        assert cs[0][2] == ptr[tile] and cs[-1][3] == ptr[tile + 1]
+        for a, b in zip(cs, cs[1:]):          # chunk order is task order
+            assert a[3] == b[2]
+    return lists
+
+
+SCHEDULES = [dict(), dict(tasks_per_item=16), dict(tasks_per_item=256), dict(item_overhead_q=2),
+             dict(item_overhead_q=24), dict(tasks_per_item=32, cta_skew_permille=300),
+             dict(item_overhead_q=8, cta_skew_permille=500)]
+
+
+def _sm_map(n_ctas, per_sm, seed):
+    """A CTA-to-SM map with per_sm CTAs on each SM, SM ids in a shuffled order."""
+    nsm = n_ctas // per_sm
+    ids = np.random.default_rng(seed).permutation(4 * nsm)[:nsm]
+    return np.array([ids[b % nsm] for b in range(n_ctas)], np.int32)
+
+
+@pytest.mark.parametrize("opts", SCHEDULES, ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()) or "model")
+@pytest.mark.parametrize("forward", [True, False], ids=["fwd", "adj"])
+def test_every_schedule_runs_every_task_once(opts, forward):
+    for wl, n_ctas in ((synth.TINY, 8), (RAGGED, 12), (synth.MODEL_A, 64)):
+        t = _inspect(wl, forward, n_ctas, **opts)
+        _check_schedule(t)
+        if "tasks_per_item" in opts:
+            assert t["chunk"] == opts["tasks_per_item"] and t["split_q"] == 0
+        if "item_overhead_q" in opts:
+            assert t["split_q"] == opts["item_overhead_q"] and t["chunk"] == 0
+        assert t["skew_pm"] == opts.get("cta_skew_permille", 0)
+
+
+@pytest.mark.parametrize("opts", [dict(tasks_per_item=64), dict(item_overhead_q=12)],
+                         ids=["chunks", "split"])
+def test_sm_map_only_moves_lists_between_ctas(opts):
+    wl = synth.REALISTIC
+    base = _check_schedule(_inspect(wl, True, 608, **opts))
+    for seed, per_sm in ((1, 4), (2, 4), (3, 3)):   # 3 per SM: an uneven, unexpected map
+        sm = _sm_map(608, per_sm, seed)
+        mapped = _check_schedule(_inspect(wl, True, 608, block_sm=sm, **opts))
+        assert sorted(mapped) == sorted(base)
+
+
+def test_sm_map_balances_the_sms():
+    """With the map, the lists (longest first) go to the least-loaded SM:
+    the SMs' task totals are closer than with the map-blind placement."""
+    wl = synth.REALISTIC
+    sm = _sm_map(608, 4, 7)
+
+    def sm_totals(t):
+        nw, wb = t["warps_per_cta"], t["warp_begin"]
+        tot = {}
+        for cta in range(t["warps"] // nw):
+            n = sum(int(r[1] - r[0]) for w in range(cta * nw, (cta + 1) * nw)
+                    for r in t["item_range"][wb[w]:wb[w + 1]])
+            tot[sm[cta]] = tot.get(sm[cta], 0) + n
+        return np.array(list(tot.values()))
+
+    for forward in (True, False):
+        blind = sm_totals(_inspect(wl, forward, 608, tasks_per_item=96))
+        aware = sm_totals(_inspect(wl, forward, 608, tasks_per_item=96, block_sm=sm))
+        assert blind.sum() == aware.sum()
+        assert aware.max() - aware.min() <= blind.max() - blind.min()
+        assert aware.max() <= 1.1 * aware.mean()
+
+
+def test_inspect_rejects_bad_arguments():
+    wl = synth.TINY
+    psf = synth.make_psf(wl)
+    with pytest.raises(CtisError):
+        tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 0)
+    with pytest.raises(CtisError):
+        tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 4,
+                       block_sm=np.array([0, 1, 4096, 2], np.int32))
+    with pytest.raises(CtisError):
+        tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 4, tasks_per_item=16,
+                       item_overhead_q=4)
