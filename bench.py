@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and autograd forms")
+    ap.add_argument("--schedule", default=None,
+                    help="skip the autotuner and use these schedules, 'FWD,ADJ' with each "
+                         "'chunk:TASKS:SKEW' or 'split:OVERHEAD_Q:SKEW' (SKEW in permille), "
+                         "e.g. a bench line's config.schedule.spec")
     return ap.parse_args()
 
 
@@ -251,7 +255,13 @@ def run_ours(args, wl, k):
     hf = plan.forward(torch.from_numpy(f_true).to(dev))
     g_host, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, seed)
     g = torch.from_numpy(g_host).to(dev)
-    tuned = plan.autotune(g)                      # schedule autotuner (plan setup)
+    if args.schedule:                             # a given schedule (e.g. to profile one)
+        for forward, spec in zip((True, False), args.schedule.split(",")):
+            kind, value, skew = spec.split(":")
+            plan.set_schedule(forward, (kind, int(value), int(skew)))
+        tuned = plan.schedules()
+    else:
+        tuned = plan.autotune(g)                  # schedule autotuner (plan setup)
     info = plan.info()
     f = torch.empty((wl.w, wl.alpha, wl.a), device=dev, dtype=torch.float32)
     stats = torch.empty((k + 1, 4), device=dev, dtype=torch.float64)
@@ -382,7 +392,8 @@ def run_ours(args, wl, k):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "stats": "float64 flux/loglik/resid per iteration",
                    "schedule": {"forward": schedule_name(tuned[0]), "adjoint": schedule_name(tuned[1]),
-                                "chosen_by": "ctis_plan_autotune"}},
+                                "spec": ",".join(f"{k}:{v}:{sk}" for k, v, sk in tuned),
+                                "chosen_by": "--schedule" if args.schedule else "ctis_plan_autotune"}},
         "voxel_updates_per_s": value * wl.m,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,

@@ -300,6 +300,15 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
  * bits between schedules (partial sums are grouped differently). */
 int ctis_plan_autotune(ctis_plan* plan, const float* g_dev, void* stream);
 
+/* Reschedules one projector's work lists (forward != 0: the forward) as the
+ * options of ctis_plan_options would: tasks_per_item > 0 chunks assigned
+ * longest first, item_overhead_q > 0 the balanced split (exclusive), both 0
+ * the model's choice; cta_skew_permille in [0, 900]. Reapplies a schedule the
+ * autotuner chose (ctis_plan_get_info reports it). Synchronous; drops the
+ * plan's cached graphs. */
+int ctis_plan_set_schedule(ctis_plan* plan, int forward, int tasks_per_item, int item_overhead_q,
+                           int cta_skew_permille);
+
 /* Wait for the plan's work on `stream`, then report (and clear) any device-side
  * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
 int ctis_plan_check(const ctis_plan* plan, void* stream);

@@ -27,7 +27,7 @@ EXPORTED = (
     "ctis_index_map", "ctis_forward", "ctis_adjoint", "ctis_reconstruct", "ctis_plan_check",
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
-    "ctis_plan_autotune", "ctis_tables_inspect",
+    "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "ctis_plan_set_values": (I, [P, f32p]),
         "ctis_plan_autotune": (I, [P, VP, VP]),
+        "ctis_plan_set_schedule": (I, [P, I, I, I, I]),
         "ctis_reconstruct_batched": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
                                          ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
@@ -336,6 +337,16 @@ class Plan:
         self._check_fpa(g)
         _check(load().ctis_plan_autotune(self._h, ctypes.c_void_p(g.data_ptr()), _stream(stream)))
         return self.schedules()
+
+    def set_schedule(self, forward: bool, sched):
+        """Reschedule one projector: ``sched`` is ``(kind, value, skew)`` as
+        ``schedules()`` reports it (kind "chunk" or "split"; value 0 with
+        kind "chunk": the model's choice)."""
+        kind, value, skew = sched
+        if kind not in ("chunk", "split"):
+            raise ValueError(f"schedule kind must be 'chunk' or 'split', got {kind!r}")
+        chunk, split = (int(value), 0) if kind == "chunk" else (0, int(value))
+        _check(load().ctis_plan_set_schedule(self._h, 1 if forward else 0, chunk, split, int(skew)))
 
     def schedules(self):
         """The projectors' work schedules ``(forward, adjoint)``, each

@@ -939,6 +939,19 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     return CTIS_OK;
 }
 
+// The work lists are about to change: drops the cached graphs and the batch
+// state built on the old ones (the caller has synchronised the device).
+void drop_table_users(ctis_plan* P) {
+    if (P->gexec) {
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+        P->gkey = GraphKey{};
+    }
+    drop_batched_graph_of(P);
+    free_batch(P->batch);
+    P->batch = nullptr;
+}
+
 // Replaces the device copies of a projector's work lists after a new
 // schedule (and grows the chunk scratch when the schedule needs more).
 int reupload_tables(ctis_plan* P, ProjTables& T) {
@@ -2315,21 +2328,35 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
     return CTIS_OK;
 }
 
+int ctis_plan_set_schedule(ctis_plan* P, int forward, int tasks_per_item, int item_overhead_q,
+                           int cta_skew_permille) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (tasks_per_item < 0 || tasks_per_item > 1 << 20)
+        return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item out of range");
+    if (item_overhead_q < 0 || item_overhead_q > 1 << 16)
+        return fail(CTIS_ERR_INVALID_ARG, "item_overhead_q out of range");
+    if (tasks_per_item > 0 && item_overhead_q > 0)
+        return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item and item_overhead_q are exclusive");
+    if (cta_skew_permille < 0 || cta_skew_permille > 900)
+        return fail(CTIS_ERR_INVALID_ARG, "cta_skew_permille out of range [0, 900]");
+    CTIS_CUDA(cudaDeviceSynchronize());
+    drop_table_users(P);
+    ProjTables& T = forward ? P->fwd : P->adj;
+    schedule(T, T.n_warps, tasks_per_item, item_overhead_q, cta_skew_permille);
+    rc = reupload_tables(P, T);
+    if (rc) return rc;
+    CTIS_CUDA(cudaDeviceSynchronize());
+    return CTIS_OK;
+}
+
 int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
     int rc = check_plan(P);
     if (rc) return rc;
     if (!g_dev) return fail(CTIS_ERR_INVALID_ARG, "g_dev is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CTIS_CUDA(cudaDeviceSynchronize());
-    // the tables change: drop everything built on the old ones
-    if (P->gexec) {
-        cudaGraphExecDestroy(P->gexec);
-        P->gexec = nullptr;
-        P->gkey = GraphKey{};
-    }
-    drop_batched_graph_of(P);
-    free_batch(P->batch);
-    P->batch = nullptr;
+    drop_table_users(P);
     // realistic operands: f = 1 in the datacube copies, g in the FPA copies
     rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
     if (!rc) rc = scatter_u(P, g_dev, st);

@@ -97,3 +97,29 @@ def test_schedule_options_are_exclusive():
              item_overhead_q=4)
     with pytest.raises(CtisError):
         Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), cta_skew_permille=901)
+
+
+def test_set_schedule_reapplies_a_schedule():
+    """A schedule set on a plan is the one it reports, and the plan's
+    reconstructions stay within the parity bounds and bit-reproducible."""
+    wl = synth.TINY
+    geom, psf, H, _, g = problem(wl)
+    ref, _ = O.mlem(H, g, wl.k)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        for fwd, adj in ((("chunk", 16, 300), ("split", 8, 0)), (("split", 4, 100), ("chunk", 24, 0))):
+            plan.set_schedule(True, fwd)
+            plan.set_schedule(False, adj)
+            assert plan.schedules() == (fwd, adj)
+            a, _ = plan.reconstruct(gt, k=wl.k, init="ones")
+            a = a.clone()
+            b, _ = plan.reconstruct(gt, k=wl.k, init="ones")
+            plan.check()
+            assert torch.equal(a, b)
+            got = b.cpu().numpy().ravel()
+            assert floored_rel(got, ref) <= wl.k * 1e-5
+        with pytest.raises(ValueError):
+            plan.set_schedule(True, ("lpt", 16, 0))
+        from paper_2006_01573_gb300 import CtisError
+        with pytest.raises(CtisError):
+            plan.set_schedule(True, ("chunk", 16, 901))
