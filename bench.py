@@ -57,6 +57,20 @@ def parse_args():
     return ap.parse_args()
 
 
+def aggregate_over_ranks(total_ms, total_e2e, steps, k, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` replicas that each ran `steps` steps of
+    k EM iterations: the job's time is the slowest rank's (max over ranks),
+    its work all ranks' iterations. Returns (value, e2e value, job ms, job e2e
+    ms); every rank gets the same numbers."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([total_ms, total_e2e], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, total_e2e = float(t[0]), float(t[1])
+    iters = steps * k * world
+    return iters / (total_ms / 1e3), iters / (total_e2e / 1e3), total_ms, total_e2e
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -350,15 +364,8 @@ def run_ours(args, wl, k):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
 
-    total_ms = sum(step_ms)
-    total_e2e = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([total_ms, total_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, total_e2e = float(t[0]), float(t[1])
-    iters = args.steps * k * world
-    value = iters / (total_ms / 1e3)
-    e2e_value = iters / (total_e2e / 1e3)
+    value, e2e_value, total_ms, total_e2e = aggregate_over_ranks(
+        sum(step_ms), sum(e2e_ms), args.steps, k, world, dist, dev)
 
     # ---- roofline of the dominant kernel (per-launch, from the timed steps)
     nnz_h = info["nnz"] * wl.a * wl.alpha          # nonzeros of H = FMAs per projection
