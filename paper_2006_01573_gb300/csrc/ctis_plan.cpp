@@ -491,16 +491,15 @@ double split_items(ProjTables& T, int n_ctas, double e, int skew_pm) {
     return max_load;
 }
 
+void layout_warps(ProjTables& T);
+
 // Picks the work schedule: `forced_split_q` > 0 forces the balanced split
 // with a per-item overhead of forced_split_q / 4 tasks, `forced` > 0 the
 // longest-first assignment of chunks of at most `forced` tasks; otherwise the
 // candidate (chunk sizes, and the balanced split with the model's item
 // overhead) with the smallest estimate of the latest CTA. CTA speeds follow
-// the priority skew skew_pm (permille; see cta_speed). Then lays out, for
-// every warp, its part of each of its CTA's items: warp w of a CTA runs tasks
-// [b + w*n/NW, b + (w+1)*n/NW) of an item of n tasks; the warps' item lists
-// are parallel (same tiles, same order) and every warp's tasks are stored
-// contiguously.
+// the priority skew skew_pm (permille; see cta_speed). Then lays out the
+// warps' lists (layout_warps).
 void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q, int skew_pm) {
     const std::vector<int>& begin = T.tile_task_begin;
     const int nw = T.nw;
@@ -542,6 +541,16 @@ void schedule(ProjTables& T, int n_warps, int forced, int forced_split_q, int sk
     }
     T.split_q = split_q;
     T.skew_pm = skew_pm;
+    layout_warps(T);
+}
+
+// Lays out, for every warp, its part of each of its CTA's items (from
+// cta_begin / cta_items): warp w of a CTA runs tasks [b + w*n/NW,
+// b + (w+1)*n/NW) of an item of n tasks; the warps' item lists are parallel
+// (same tiles, same order) and every warp's tasks are stored contiguously.
+void layout_warps(ProjTables& T) {
+    const int nw = T.nw;
+    const int n_ctas = static_cast<int>(T.cta_begin.size()) - 1;
     T.witems.clear();
     T.witem_src.clear();
     T.warp_begin.assign(1, 0);
@@ -1263,6 +1272,7 @@ struct BatchTables {
     int* d_warp_begin = nullptr;
     int n_warps = 0;
     int n_tiles = 0;
+    int64_t scratch_slots = 0;   // chunk partial-sum slots of the joint schedule
 };
 
 struct BatchState {
@@ -1310,46 +1320,70 @@ void free_batch(BatchState* B) {
     delete B;
 }
 
-// The plan's work lists repeated for F frames, warp by warp (each warp keeps
-// its items and runs them once per frame; its tasks stay contiguous).
+// The work lists of F frames, scheduled as one problem. The joint tiles are
+// frame f's tiles f*T + t (so tickets and tile statistics stay frame-major),
+// their tasks the plan's with frame f's planes (forward: datacube planes
+// f*w + s of the copies) or rows (adjoint: rows f*xi + y of the tall FPA),
+// and the joint items are the plan's items (same tiles, chunks and task
+// ranges) of every frame, assigned longest first over the CTAs with the
+// plan's priority skew and CTA-to-SM map. Each tile is therefore summed
+// exactly as in a single-frame call (bit-identical results), while small
+// frames no longer give every warp a few tasks per frame.
 int replicate(ctis_plan* P, const ProjTables& T, bool forward, int F, BatchTables& B) {
-    std::vector<WorkItem> wi;
-    std::vector<TaskDesc> wt;
-    std::vector<int> wb{0};
-    wi.reserve(T.witems.size() * F);
-    wt.reserve(T.tasks.size() * F);
+    ProjTables J;
+    J.nw = T.nw;
+    J.tile_w = T.tile_w;
+    J.tile_h = T.tile_h;
+    J.block_sm = T.block_sm;
+    J.n_warps = T.n_warps;
     const int ntiles = static_cast<int>(T.tiles.size());
-    for (int wp = 0; wp < T.n_warps; ++wp) {
-        for (int f = 0; f < F; ++f)
-            for (int i = T.warp_begin[wp]; i < T.warp_begin[wp + 1]; ++i) {
-                WorkItem it = T.witems[i];
-                const int tb = static_cast<int>(wt.size());
-                for (int t = it.task_begin; t < it.task_end; ++t) {
-                    TaskDesc d = T.tasks[t];
-                    if (forward) {   // copies' plane q*w + s -> q*(F*w) + f*w + s
-                        const int q = d.plane / P->w, sw = d.plane % P->w;
-                        d.plane = q * (F * P->w) + f * P->w + sw;
-                    } else {         // window rows of frame f on the tall FPA
-                        d.wy += f * P->xi;
-                    }
-                    wt.push_back(d);
-                }
-                it.task_begin = tb;
-                it.task_end = static_cast<int>(wt.size());
-                it.tile += f * ntiles;
-                it.scratch_base += static_cast<int>(f * T.scratch_slots);
-                it.plane = forward ? f : f * P->w + it.plane;
-                wi.push_back(it);
-            }
-        wb.push_back(static_cast<int>(wi.size()));
-    }
-    if (static_cast<int64_t>(wt.size()) > (int64_t{1} << 31) - 1)
+    const int64_t ntasks = static_cast<int64_t>(T.tile_tasks.size());
+    if (ntasks * F > (int64_t{1} << 31) - 1 || static_cast<int64_t>(ntiles) * F > (int64_t{1} << 30))
         return fail(CTIS_ERR_UNSUPPORTED, "too many frames for one batch");
-    B.n_warps = T.n_warps;
+    J.tiles.reserve(static_cast<size_t>(ntiles) * F);
+    J.tile_tasks.reserve(static_cast<size_t>(ntasks) * F);
+    J.tile_task_begin.assign(1, 0);
+    for (int f = 0; f < F; ++f)
+        for (int t = 0; t < ntiles; ++t) {
+            TileDesc td = T.tiles[t];
+            td.plane = forward ? f : f * P->w + td.plane;
+            if (td.nchunks > 1) td.scratch_base += static_cast<int>(f * T.scratch_slots);
+            J.tiles.push_back(td);
+            for (int k = T.tile_task_begin[t]; k < T.tile_task_begin[t + 1]; ++k) {
+                TaskDesc d = T.tile_tasks[k];
+                if (forward) {   // copies' plane q*w + s -> q*(F*w) + f*w + s
+                    const int q = d.plane / P->w, sw = d.plane % P->w;
+                    d.plane = q * (F * P->w) + f * P->w + sw;
+                } else {         // window rows of frame f on the tall FPA
+                    d.wy += f * P->xi;
+                }
+                J.tile_tasks.push_back(d);
+            }
+            J.tile_task_begin.push_back(static_cast<int>(J.tile_tasks.size()));
+        }
+    J.items.reserve(T.items.size() * F);
+    for (int f = 0; f < F; ++f)
+        for (const ItemDesc& it : T.items) {
+            ItemDesc j = it;
+            j.tile = f * ntiles + it.tile;
+            j.task_begin = static_cast<int>(it.task_begin + f * ntasks);
+            j.task_end = static_cast<int>(it.task_end + f * ntasks);
+            J.items.push_back(j);
+        }
+    J.scratch_slots = T.scratch_slots * F;
+    assign_ctas(J, J.n_warps / J.nw, T.skew_pm);
+    // each CTA runs its items frame by frame, so the CTAs move through the
+    // frames together and the frames in flight stay in L2
+    for (size_t c = 0; c + 1 < J.cta_begin.size(); ++c)
+        std::stable_sort(J.cta_items.begin() + J.cta_begin[c], J.cta_items.begin() + J.cta_begin[c + 1],
+                         [&](int x, int y) { return J.items[x].tile / ntiles < J.items[y].tile / ntiles; });
+    layout_warps(J);
+    B.n_warps = J.n_warps;
     B.n_tiles = ntiles * F;
-    int rc = upload(P, &B.d_witems, wi);
-    if (!rc) rc = upload(P, &B.d_tasks, wt);
-    if (!rc) rc = upload(P, &B.d_warp_begin, wb);
+    B.scratch_slots = J.scratch_slots;
+    int rc = upload(P, &B.d_witems, J.witems);
+    if (!rc) rc = upload(P, &B.d_tasks, J.tasks);
+    if (!rc) rc = upload(P, &B.d_warp_begin, J.warp_begin);
     return rc;
 }
 
@@ -1384,14 +1418,14 @@ int ensure_batch(ctis_plan* P, int F, int k) {
     B->u_copy_stride = static_cast<int64_t>(P->g_pitch) * P->xi * F;
     const size_t fbytes = es * static_cast<size_t>(B->f_copy_stride) * P->f_copies;
     const size_t ubytes = sizeof(float) * static_cast<size_t>(B->u_copy_stride) * P->u_copies;
-    const int64_t scratch = std::max(P->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
-                                     P->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
+    const int64_t scratch = std::max(B->fwd.scratch_slots * P->fwd.tile_w * P->fwd.tile_h,
+                                     B->adj.scratch_slots * P->adj.tile_w * P->adj.tile_h);
     const size_t tpf = P->fwd.tiles.size();
     const size_t ntick = std::max(tpf * F, P->adj.tiles.size() * F);
     rc = dmalloc(P, &B->d_fwork, fbytes);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_u), ubytes);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_scratch),
-                          sizeof(float) * static_cast<size_t>(scratch) * F);
+                          sizeof(float) * static_cast<size_t>(scratch));
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tickets), sizeof(int) * ntick);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_counters), sizeof(int) * (8 + F));
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&B->d_tile_stats),
