@@ -294,7 +294,8 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
  * and keeps the fastest. Candidates: the plan's model choice, work items of
  * at most 16..192 cluster tasks assigned longest first, and the balanced
  * split with item overheads of 2..24 quarter tasks, some of them also with
- * CTA priority skews of 100..300 permille (ctis_plan_options). Synchronous; overwrites the plan's internal copies
+ * CTA priority skews of 100..300 permille (ctis_plan_options); the four
+ * fastest of a first pass are timed again, interleaved, before the choice. Synchronous; overwrites the plan's internal copies
  * and drops its cached graphs (the next ctis_reconstruct re-captures).
  * Results stay deterministic for a given schedule but may differ in the last
  * bits between schedules (partial sums are grouped differently). */

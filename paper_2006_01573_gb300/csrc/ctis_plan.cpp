@@ -2443,27 +2443,45 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
     int result = CTIS_OK;
     for (ProjTables* T : {&P->fwd, &P->adj}) {
         const bool forward = T == &P->fwd;
-        float best_ms = -1.f;
-        Cand best{0, 0, 0};
-        for (const Cand& c : cands) {
+        // milliseconds per launch of candidate c over `reps` launches (after
+        // two warm-up launches); < 0 when something failed (result is set)
+        auto time_cand = [&](const Cand& c, int reps) -> float {
             schedule(*T, T->n_warps, c.chunk, c.split_q, c.skew_pm);
-            if (c.chunk != 0 && T->per_item != c.chunk) continue;
             result = reupload(*T);
             for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
             cudaError_t e = result ? cudaSuccess : cudaEventRecord(e0, st);
-            for (int r = 0; r < 5 && !result && e == cudaSuccess; ++r) result = run(forward);
+            for (int r = 0; r < reps && !result && e == cudaSuccess; ++r) result = run(forward);
             if (!result && e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (!result && e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (!result && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (!result && e != cudaSuccess) result = cuda_fail(e, "timing a candidate schedule");
-            if (result) break;
-            if (best_ms < 0.f || ms < best_ms) {
-                best_ms = ms;
-                best = {T->per_item, T->split_q, T->skew_pm};
-            }
+            return result ? -1.f : ms / reps;
+        };
+        // a first pass over all candidates, then the four fastest again,
+        // interleaved over three rounds of 10 launches, to keep the timing
+        // noise out of the choice
+        std::vector<std::pair<float, Cand>> timed;
+        for (const Cand& c : cands) {
+            const float ms = time_cand(c, 5);
+            if (ms < 0.f) break;
+            timed.push_back({ms, {T->per_item, T->split_q, T->skew_pm}});
         }
         if (result) break;
+        std::stable_sort(timed.begin(), timed.end(),
+                         [](const auto& x, const auto& y) { return x.first < y.first; });
+        timed.resize(std::min<size_t>(timed.size(), 4));
+        std::vector<float> total(timed.size(), 0.f);
+        for (int round = 0; round < 3 && !result; ++round)
+            for (size_t i = 0; i < timed.size() && !result; ++i) {
+                const float ms = time_cand(timed[i].second, 10);
+                if (ms >= 0.f) total[i] += ms;
+            }
+        if (result) break;
+        size_t bi = 0;
+        for (size_t i = 1; i < timed.size(); ++i)
+            if (total[i] < total[bi]) bi = i;
+        const Cand best = timed[bi].second;
         schedule(*T, T->n_warps, best.chunk, best.split_q, best.skew_pm);
         result = reupload(*T);
         if (result) break;
