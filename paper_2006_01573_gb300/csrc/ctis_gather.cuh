@@ -135,6 +135,16 @@ struct Elem<float> {
         const float4 v = *reinterpret_cast<const float4*>(p);
         out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
     }
+    // the first N (< 4) elements of a 16-byte chunk, with 8- and 4-byte loads
+    template <int N>
+    __device__ static __forceinline__ void load_part(const float* p, float* out) {
+        static_assert(N > 0 && N < 4, "a partial chunk");
+        if constexpr (N >= 2) {
+            const float2 v = *reinterpret_cast<const float2*>(p);
+            out[0] = v.x; out[1] = v.y;
+        }
+        if constexpr (N % 2 == 1) out[N - 1] = p[N - 1];
+    }
     __device__ static __forceinline__ float load(const float* p) { return *p; }
     __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
     // weight stored as a duplicated pair (w, w)
@@ -149,6 +159,22 @@ struct Elem<__nv_bfloat16> {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            out[2 * q] = __uint_as_float(w[q] << 16);
+            out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+        }
+    }
+    // the first N (even, < 8) elements of a 16-byte chunk, with 8- and 4-byte loads
+    template <int N>
+    __device__ static __forceinline__ void load_part(const __nv_bfloat16* p, float* out) {
+        static_assert(N > 0 && N < 8 && N % 2 == 0, "a partial chunk of bfloat16 pairs");
+        uint32_t w[N / 2];
+        if constexpr (N >= 4) {
+            const uint2 v = *reinterpret_cast<const uint2*>(p);
+            w[0] = v.x; w[1] = v.y;
+        }
+        if constexpr (N % 4 == 2) w[N / 2 - 1] = reinterpret_cast<const uint32_t*>(p)[N / 2 - 1];
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
             out[2 * q] = __uint_as_float(w[q] << 16);
             out[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
         }
@@ -217,24 +243,35 @@ struct Geo {
 // ---------------------------------------------------------------------------
 // per-lane correlation of one staged window
 // ---------------------------------------------------------------------------
+// The C + K - 1 elements of one window row a lane uses, from its first
+// (16-byte aligned) element: whole 16-byte chunks, then the rest with 8- and
+// 4-byte loads. Loading only what is used keeps the shared-memory traffic of
+// the inner loop, which competes with the FMAs, at its minimum (6 of 8
+// float32 for C = 4, K = 3).
+template <class G, typename TIn>
+__device__ __forceinline__ void load_row_elems(const TIn* rowp, float (&raw)[G::C + G::K - 1]) {
+    constexpr int NE = G::C + G::K - 1, EPC = G::EPC;
+    constexpr int NFULL = NE / EPC, NREST = NE - NFULL * EPC;
+#pragma unroll
+    for (int q = 0; q < NFULL; ++q) Elem<TIn>::load_chunk(rowp + q * EPC, raw + q * EPC);
+    if constexpr (NREST > 0) Elem<TIn>::template load_part<NREST>(rowp + NFULL * EPC, raw + NFULL * EPC);
+}
+
 // acc[o][c] += sum_{dy,dx} w[dy][dx] * win[o + dy][c + dx]
 // `win` points at this lane's first element (window row ty*R, column tx*C).
-// Windows are chunk-aligned (shifted copies), so each row is a few 16-byte
-// loads; the even-offset operand pairs of the packed FMAs come straight from
-// them and the odd-offset pairs are formed once per row.
+// Windows are chunk-aligned (shifted copies), so each row is a few aligned
+// loads (load_row_elems); the even-offset operand pairs of the packed FMAs
+// come straight from them and the odd-offset pairs are formed once per row.
 template <class G, typename TIn>
 __device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const TIn* win,
                                           const float2 (&w2)[G::K * G::K]) {
-    constexpr int K = G::K, C = G::C, R = G::R, EPC = G::EPC;
-    constexpr int NE = C + K - 1;                 // elements used per row
-    constexpr int NCH = (NE + EPC - 1) / EPC;
-    constexpr int NP = NCH * EPC / 2;             // even-offset pairs loaded
+    constexpr int K = G::K, C = G::C, R = G::R;
+    constexpr int NE = C + K - 1;                 // elements used per row (even)
+    constexpr int NP = NE / 2;                    // even-offset pairs
 #pragma unroll
     for (int i = 0; i < R + K - 1; ++i) {
-        const TIn* rowp = win + i * G::BXW;
-        float raw[NCH * EPC];
-#pragma unroll
-        for (int q = 0; q < NCH; ++q) Elem<TIn>::load_chunk(rowp + q * EPC, raw + q * EPC);
+        float raw[NE];
+        load_row_elems<G, TIn>(win + i * G::BXW, raw);
         float2 ev[NP], od[NP - 1];
 #pragma unroll
         for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
@@ -266,16 +303,13 @@ __device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const T
 template <class G, typename TIn>
 __device__ __forceinline__ void correlate_grad(float2 (&acc)[G::K * G::K], const TIn* win,
                                                const float2 (&fp)[G::R][G::C / 2]) {
-    constexpr int K = G::K, C = G::C, R = G::R, EPC = G::EPC;
+    constexpr int K = G::K, C = G::C, R = G::R;
     constexpr int NE = C + K - 1;
-    constexpr int NCH = (NE + EPC - 1) / EPC;
-    constexpr int NP = NCH * EPC / 2;
+    constexpr int NP = NE / 2;
 #pragma unroll
     for (int i = 0; i < R + K - 1; ++i) {
-        const TIn* rowp = win + i * G::BXW;
-        float raw[NCH * EPC];
-#pragma unroll
-        for (int q = 0; q < NCH; ++q) Elem<TIn>::load_chunk(rowp + q * EPC, raw + q * EPC);
+        float raw[NE];
+        load_row_elems<G, TIn>(win + i * G::BXW, raw);
         float2 ev[NP], od[NP - 1];
 #pragma unroll
         for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
