@@ -31,7 +31,10 @@ are promoted exactly. Readings of points the paper leaves open:
   in the datacube (the index map pairs the fast FPA axis with the fast
   field-stop axis);
 * boundary: every shifted nonzero must stay on the FPA (checked by
-  :func:`check_bounds`); then the circulant form of Eq. 7 and the 2-D shift agree;
+  :func:`check_bounds`); then the circulant form of Eq. 7 and the 2-D shift agree.
+  The optional clip reading (``boundary="clip"``) keeps the physical 2-D shift
+  and drops the shifted nonzeros that leave the FPA (the light is lost), so
+  ``h`` then varies from voxel to voxel;
 * ``u_i = 0`` where ``(Hf)_i = 0`` and ``f_j = 0`` where ``h_j = 0`` (Eq. 2 leaves
   both divisions undefined);
 * duplicate PSF entries at one FPA position add up (H is a sum of responses);
@@ -93,8 +96,10 @@ class OutOfBounds(ValueError):
     pass
 
 
-def check_bounds(geom: Geometry, psf) -> None:
-    """Reject a PSF whose shifted copies would leave the FPA.
+def check_bounds(geom: Geometry, psf, boundary: str = "reject") -> None:
+    """Reject a PSF whose shifted copies would leave the FPA (``boundary=
+    "reject"``); with ``boundary="clip"`` such nonzeros are allowed and the
+    projectors drop the shifted positions off the FPA.
 
     Column j = (p, r, s) of H holds the calibration image of wavelength s shifted
     by (p, r) (Sec. 2). Every shifted nonzero must satisfy ``0 <= x + p < gamma``
@@ -105,6 +110,10 @@ def check_bounds(geom: Geometry, psf) -> None:
     ptr, x, y, _ = psf
     if len(ptr) != geom.w + 1:
         raise ValueError("psf_ptr must have w+1 entries")
+    if boundary not in ("reject", "clip"):
+        raise ValueError(boundary)
+    if boundary == "clip":
+        return
     x = np.asarray(x, dtype=np.int64)
     y = np.asarray(y, dtype=np.int64)
     if x.size and (x.min() < 0 or y.min() < 0 or
@@ -113,9 +122,9 @@ def check_bounds(geom: Geometry, psf) -> None:
         raise OutOfBounds("PSF nonzero shifted off the FPA")
 
 
-def merge_psf(geom: Geometry, psf) -> Taps:
+def merge_psf(geom: Geometry, psf, boundary: str = "reject") -> Taps:
     """Sort each wavelength's nonzeros by (y, x) and add up duplicates (float64)."""
-    check_bounds(geom, psf)
+    check_bounds(geom, psf, boundary)
     ptr, x, y, v = psf
     ptr = np.asarray(ptr, dtype=np.int64)
     S, X, Y, V, P = [], [], [], [], [0]
@@ -124,15 +133,15 @@ def merge_psf(geom: Geometry, psf) -> Taps:
         xs = np.asarray(x[lo:hi], dtype=np.int64)
         ys = np.asarray(y[lo:hi], dtype=np.int64)
         vs = np.asarray(v[lo:hi], dtype=np.float64)
-        key = ys * geom.gamma + xs
-        uniq, inv = np.unique(key, return_inverse=True)
-        acc = np.zeros(uniq.size)
-        np.add.at(acc, inv, vs)
-        S.append(np.full(uniq.size, s, dtype=np.int64))
-        X.append(uniq % geom.gamma)
-        Y.append(uniq // geom.gamma)
+        yx = np.stack([ys, xs], axis=1).reshape(-1, 2)
+        uniq, inv = np.unique(yx, axis=0, return_inverse=True)   # sorted by (y, x)
+        acc = np.zeros(len(uniq))
+        np.add.at(acc, np.asarray(inv).ravel(), vs)
+        S.append(np.full(len(uniq), s, dtype=np.int64))
+        X.append(uniq[:, 1])
+        Y.append(uniq[:, 0])
         V.append(acc)
-        P.append(P[-1] + uniq.size)
+        P.append(P[-1] + len(uniq))
     cat = lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt)
     return Taps(cat(S, np.int64), cat(X, np.int64), cat(Y, np.int64),
                 cat(V, np.float64), np.asarray(P, dtype=np.int64))
@@ -156,7 +165,8 @@ class BlockH:
     Each block ``H_s`` (n x l, CSR, float64) is built straight from Sec. 2:
     column ``r*a + p`` is the calibration image of wavelength s shifted by
     (p, r), i.e. nonzero ``(x_k, y_k, v_k)`` lands in row
-    ``(x_k + p) + gamma*(y_k + r)``.
+    ``(x_k + p) + gamma*(y_k + r)``. A shifted nonzero off the FPA (possible
+    only under the clip reading) is dropped.
     """
 
     def __init__(self, geom: Geometry, taps: Taps, wavelengths=None):
@@ -168,12 +178,15 @@ class BlockH:
         col = (R * a + P).ravel()
         shift = (P + ga * R).ravel()
         self.blocks = {}
+        Pf, Rf = P.ravel(), R.ravel()
         for s in self.wavelengths:
             xs, ys, vs = taps.of(s)
-            base = xs + ga * ys
-            rows = (base[:, None] + shift[None, :]).ravel()
-            cols = np.broadcast_to(col[None, :], (xs.size, col.size)).ravel()
-            vals = np.broadcast_to(vs[:, None], (xs.size, col.size)).ravel()
+            px = xs[:, None] + Pf[None, :]
+            py = ys[:, None] + Rf[None, :]
+            on = (px >= 0) & (px < ga) & (py >= 0) & (py < geom.xi)
+            rows = (px + ga * py)[on]
+            cols = np.broadcast_to(col[None, :], on.shape)[on]
+            vals = np.broadcast_to(vs[:, None], on.shape)[on]
             self.blocks[s] = sp.csr_matrix((vals, (rows, cols)), shape=(geom.n, geom.ell))
 
     def forward(self, f: np.ndarray) -> np.ndarray:
@@ -203,8 +216,8 @@ class BlockH:
         return sp.hstack([self.blocks[s] for s in range(self.geom.w)]).tocsr()
 
 
-def build_H(geom: Geometry, psf, wavelengths=None) -> BlockH:
-    return BlockH(geom, merge_psf(geom, psf), wavelengths)
+def build_H(geom: Geometry, psf, wavelengths=None, boundary: str = "reject") -> BlockH:
+    return BlockH(geom, merge_psf(geom, psf, boundary), wavelengths)
 
 
 def ratio(g: np.ndarray, q: np.ndarray) -> np.ndarray:
@@ -308,7 +321,9 @@ def adjoint_at(geom: Geometry, taps: Taps, u: np.ndarray, s_idx, ps, rs) -> np.n
     out = np.zeros(len(s_idx))
     for t, (s, p, r) in enumerate(zip(s_idx, ps, rs)):
         tx, ty, tv = taps.of(int(s))
-        out[t] = np.dot(u[ty + r, tx + p], tv)
+        x, y = tx + p, ty + r
+        on = (x >= 0) & (x < geom.gamma) & (y >= 0) & (y < geom.xi)   # off the FPA: dropped
+        out[t] = np.dot(u[y[on], x[on]], tv[on])
     return out
 
 
@@ -408,7 +423,11 @@ def psf_value_grad(geom: Geometry, taps: Taps, f: np.ndarray, gy: np.ndarray) ->
     out = np.zeros(taps.v.size)
     for t in range(taps.v.size):
         s, x, y = int(taps.s[t]), int(taps.x[t]), int(taps.y[t])
-        out[t] = np.sum(f[s] * gy[y:y + geom.alpha, x:x + geom.a])
+        # the part of the shifted field stop on the FPA (all of it unless clipped)
+        p0, p1 = max(0, -x), min(geom.a, geom.gamma - x)
+        r0, r1 = max(0, -y), min(geom.alpha, geom.xi - y)
+        if p0 < p1 and r0 < r1:
+            out[t] = np.sum(f[s, r0:r1, p0:p1] * gy[y + r0:y + r1, x + p0:x + p1])
     return out
 
 

@@ -381,3 +381,86 @@ def test_em_step_stored_with_exact_store_is_em_step():
     assert np.array_equal(O.em_step_stored(H, g, f, lambda z: z), O.em_step(H, g, f))
     stored = O.em_step_stored(H, g, f, lambda z: O.round_bf16(z.astype(np.float32)))
     assert np.array_equal(stored, O.round_bf16(O.em_step(H, g, f).astype(np.float32)))
+
+
+# --- the clip boundary reading (shifted nonzeros off the FPA are dropped) -------
+
+CLIP_GEOM = (4, 3, 2, 9, 8)
+# nonzeros spilling over every FPA edge, a duplicate, and one wholly off the FPA
+CLIP_PSF = (np.array([0, 4, 9], np.int32),
+            np.array([-2, 7, 3, 1, -1, 5, 5, 20, 6], np.int32),
+            np.array([1, 6, 2, -2, -1, 0, 0, 3, 7], np.int32),
+            np.array([0.5, 1.5, 1.0, 0.25, 0.7, 0.3, 0.2, 2.0, 0.9], np.float32))
+
+
+def _clip_bruteforce_dense(geom, psf):
+    """H by four nested loops over wavelengths, nonzeros and field-stop pixels,
+    keeping a term only when its shifted pixel is on the FPA."""
+    ptr, x, y, v = psf
+    D = np.zeros((geom.n, geom.m))
+    for s in range(geom.w):
+        for k in range(int(ptr[s]), int(ptr[s + 1])):
+            for r in range(geom.alpha):
+                for p in range(geom.a):
+                    X, Y = int(x[k]) + p, int(y[k]) + r
+                    if 0 <= X < geom.gamma and 0 <= Y < geom.xi:
+                        D[X + geom.gamma * Y, s * geom.ell + r * geom.a + p] += float(v[k])
+    return D
+
+
+def test_clip_reading_matches_bruteforce_and_reject_refuses_it():
+    geom = _geom(*CLIP_GEOM)
+    with pytest.raises(O.OutOfBounds):
+        O.build_H(geom, CLIP_PSF)
+    H = O.build_H(geom, CLIP_PSF, boundary="clip")
+    D = _clip_bruteforce_dense(geom, CLIP_PSF)
+    assert np.array_equal(H.as_csr().toarray(), D)
+    # h = column sums: smaller at the voxels whose light partly leaves the FPA
+    assert np.allclose(H.h(), D.sum(axis=0))
+    assert len(np.unique(H.h()[:geom.ell])) > 1
+
+
+def test_clip_reading_is_the_reject_reading_when_nothing_leaves():
+    geom = _geom(4, 3, 2, 10, 9)
+    psf = _tiny_psf(geom, 5, 43, dup=2)
+    a = O.build_H(geom, psf).as_csr().toarray()
+    b = O.build_H(geom, psf, boundary="clip").as_csr().toarray()
+    assert np.array_equal(a, b)
+    assert np.allclose(a, O.dense_H(geom, psf))
+
+
+def test_clip_pointwise_evaluators_and_psf_grad():
+    geom = _geom(*CLIP_GEOM)
+    taps = O.merge_psf(geom, CLIP_PSF, "clip")
+    H = O.BlockH(geom, taps)
+    D = _clip_bruteforce_dense(geom, CLIP_PSF)
+    f = synth.random_positive(geom.m, 61).astype(np.float64)
+    u = synth.random_positive(geom.n, 62).astype(np.float64)
+    xs, ys = np.meshgrid(np.arange(geom.gamma), np.arange(geom.xi))
+    assert _rel(O.forward_at(geom, taps, f, xs.ravel(), ys.ravel()), D @ f) < 1e-14
+    s, r, p = np.unravel_index(np.arange(geom.m), (geom.w, geom.alpha, geom.a))
+    assert _rel(O.adjoint_at(geom, taps, u, s, p, r), D.T @ u) < 1e-14
+    # d <u, H f> / d v_t against the derivative of the brute-force H
+    grad = O.psf_value_grad(geom, taps, f, u)
+    for t in range(taps.v.size):
+        ptr = np.zeros(geom.w + 1, np.int32)
+        ptr[int(taps.s[t]) + 1:] = 1
+        Dt = _clip_bruteforce_dense(geom, (ptr, taps.x[t:t + 1], taps.y[t:t + 1],
+                                           np.ones(1, np.float32)))
+        assert abs(grad[t] - u @ (Dt @ f)) <= 1e-12 * max(1.0, abs(grad[t]))
+
+
+def test_clip_em_invariants():
+    """Under clipping h varies per voxel; EM still conserves the flux
+    sum_j h_j f_j^(t+1) = sum of g over the support of H f^(t), and keeps f >= 0."""
+    geom = _geom(*CLIP_GEOM)
+    H = O.build_H(geom, CLIP_PSF, boundary="clip")
+    g = synth.random_positive(geom.n, 63).astype(np.float64) * 50
+    f = np.ones(geom.m)
+    h = H.h()
+    for _ in range(5):
+        q = H.forward(f)
+        f_next = O.em_step(H, g, f)
+        assert np.all(f_next >= 0)
+        assert abs(np.dot(h, f_next) - g[q > 0].sum()) <= 1e-9 * g.sum()
+        f = f_next
