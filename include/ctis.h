@@ -59,6 +59,13 @@ typedef enum {
 /* Storage type of the datacube f and of the PSF values inside a plan. */
 enum { CTIS_F32 = 0, CTIS_BF16 = 1 };
 
+/* FPA boundary reading (ctis_plan_options.boundary). Eq. 7's circulant would
+ * wrap a shifted nonzero past the FPA edge into another row; a physical shift
+ * loses it. REJECT (default): every shifted nonzero must stay on the FPA, so
+ * both readings agree. CLIP: the physical reading: shifted nonzeros off the
+ * FPA are dropped (lost light), and h = H^T 1 then varies per voxel. */
+enum { CTIS_BOUNDARY_REJECT = 0, CTIS_BOUNDARY_CLIP = 1 };
+
 /* ctis_reconstruct flags. Without an INIT flag, f_dev holds the initial guess. */
 enum {
     CTIS_INIT_ONES = 1,  /* f^(1) = 1 (Algorithm 1)                     */
@@ -103,7 +110,9 @@ typedef struct {
                               linearly from 1 + skew to 1 - skew over the block
                               indices (the SM's warp schedulers favour the CTAs
                               resident first); 0 = equal speeds                 */
-    int reserved[4];       /* must be 0                                          */
+    int boundary;          /* CTIS_BOUNDARY_REJECT (0) or CTIS_BOUNDARY_CLIP;
+                              CLIP accepts PSF coordinates in [-2^24, 2^24)     */
+    int reserved[3];       /* must be 0                                          */
 } ctis_plan_options;
 
 /* ctis_plan_create with options; opt may be NULL (all defaults). */
@@ -170,14 +179,18 @@ typedef struct {
     int64_t fwd_split_q, adj_split_q;      /* balanced split's item overhead in
                                               quarter tasks; 0 = chunk schedule */
     int64_t fwd_skew_pm, adj_skew_pm;      /* CTA priority skew of the schedule  */
+    int64_t boundary;                      /* CTIS_BOUNDARY_*                    */
 } ctis_plan_info;
 
 int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
 
 /* Copy the merged PSF table to host arrays: for each merged nonzero, sorted by
  * (s, y, x), its wavelength, FPA coordinates and value (as stored: float32, or
- * bfloat16 widened to float32), plus h[w] (float32 as used by the update).
- * Arrays must hold info.nnz entries (h: w entries). Any pointer may be NULL. */
+ * bfloat16 widened to float32), plus h[w] (float32 as used by the update;
+ * under CTIS_BOUNDARY_CLIP the per-wavelength sum of the values, which the
+ * voxels whose light partly leaves the FPA do not reach: their h is
+ * H^T 1 per voxel). Arrays must hold info.nnz entries (h: w entries). Any
+ * pointer may be NULL. */
 int ctis_plan_export_taps(const ctis_plan* plan, int32_t* s, int32_t* x, int32_t* y,
                           float* val, float* h);
 
@@ -284,7 +297,8 @@ int ctis_psf_grad(const ctis_plan* plan, const void* f_dev, const float* r_dev,
  *   dependence of h = H^T 1 on v), df0_dev = dL/df0 when not NULL (float32).
  * The iterates are checkpointed (the plan keeps (k+1)*m float32 of workspace,
  * grown on demand); the backward pass recomputes each step's projections.
- * float32 plans only (CTIS_ERR_UNSUPPORTED otherwise); 0 <= k <= 4096. */
+ * float32 plans with CTIS_BOUNDARY_REJECT only (CTIS_ERR_UNSUPPORTED
+ * otherwise); 0 <= k <= 4096. */
 int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_dev, int k,
                            double* nll_dev, float* dval_dev, float* df0_dev, void* stream);
 

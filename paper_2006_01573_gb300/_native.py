@@ -15,6 +15,8 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctis.so")
 
 CTIS_F32, CTIS_BF16 = 0, 1
+CTIS_BOUNDARY_REJECT, CTIS_BOUNDARY_CLIP = 0, 1
+_BOUNDARY = {"reject": CTIS_BOUNDARY_REJECT, "clip": CTIS_BOUNDARY_CLIP}
 CTIS_INIT_ONES, CTIS_INIT_HTG = 1, 2
 NSTATS = 4
 STAT_NAMES = ("flux_hf", "flux_g", "loglik", "resid2")
@@ -44,7 +46,7 @@ class PlanInfo(ctypes.Structure):
         "fwd_tiles", "fwd_tasks", "fwd_items", "adj_tiles", "adj_tasks", "adj_items",
         "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
         "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q", "fwd_skew_pm",
-        "adj_skew_pm")]
+        "adj_skew_pm", "boundary")]
 
 
 class TablesInfo(ctypes.Structure):
@@ -56,7 +58,7 @@ class TablesInfo(ctypes.Structure):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("tasks_per_item", ctypes.c_int),
                 ("item_overhead_q", ctypes.c_int), ("cta_skew_permille", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("boundary", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 def load(path: str = LIB_PATH):
@@ -129,7 +131,7 @@ def _stream(stream):
 
 def tables_inspect(a, alpha, w, gamma, xi, psf, forward: bool, n_ctas: int, dtype: str = "f32",
                    block_sm=None, tasks_per_item: int = 0, item_overhead_q: int = 0,
-                   cta_skew_permille: int = 0) -> dict:
+                   cta_skew_permille: int = 0, boundary: str = "reject") -> dict:
     """Host-only view of one projector's work lists and schedule
     (ctis_tables_inspect; no device needed). Returns the info fields and the
     arrays as numpy int32 arrays."""
@@ -140,7 +142,7 @@ def tables_inspect(a, alpha, w, gamma, xi, psf, forward: bool, n_ctas: int, dtyp
     v, _ = _arr(psf[3], np.float32)
     i32 = lambda arr: None if arr is None else arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
-                      int(cta_skew_permille))
+                      int(cta_skew_permille), _BOUNDARY[boundary])
     bsm = None if block_sm is None else np.ascontiguousarray(block_sm, dtype=np.int32)
     dt = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
     info = TablesInfo(ctypes.sizeof(TablesInfo))
@@ -176,7 +178,7 @@ class Plan:
     """
 
     def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0,
-                 item_overhead_q: int = 0, cta_skew_permille: int = 0):
+                 item_overhead_q: int = 0, cta_skew_permille: int = 0, boundary: str = "reject"):
         lib = load()
         ptr, _ = _arr(psf[0], np.int32)
         x, _ = _arr(psf[1], np.int32)
@@ -188,7 +190,7 @@ class Plan:
         handle = ctypes.c_void_p()
         i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
-                          int(cta_skew_permille))
+                          int(cta_skew_permille), _BOUNDARY[boundary])
         _check(lib.ctis_plan_create_ex(ctypes.byref(handle), a, alpha, w, gamma, xi, i32(ptr),
                                        i32(x), i32(y),
                                        v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),

@@ -633,8 +633,21 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
                                      (long long)(row_ok ? y : 0) * p.f_pitch + it.x0;
             float fv[C];
             if (p.mode == kEpiUpdate) {   // ein: f_in of this row (loaded by the caller)
+                if (p.h_vox) {            // clipped boundary: h per voxel
+                    const float* hp = p.h_vox +
+                                      ((long long)(it.plane % p.h_vox_planes) * p.out_h +
+                                       (row_ok ? y : 0)) * p.out_w + it.x0 + col0;
+                    float hv[C];
+                    load_row<float, C>(hp, row_ok ? n_valid : 0,
+                                       (p.out_w % 4) == 0 && (reinterpret_cast<uintptr_t>(hp) & 15) == 0,
+                                       hv);
 #pragma unroll
-                for (int c = 0; c < C; ++c) fv[c] = ein[o][c] * v[o][c] * rh;
+                    for (int c = 0; c < C; ++c)
+                        fv[c] = hv[c] != 0.f ? ein[o][c] * v[o][c] * (1.0f / hv[c]) : 0.f;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) fv[c] = ein[o][c] * v[o][c] * rh;
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) fv[c] = v[o][c];

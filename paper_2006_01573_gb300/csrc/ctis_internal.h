@@ -107,7 +107,11 @@ struct GatherParams {
     long long f_plane_stride;
     long long f_copy_stride;
     int f_copies;
-    const float* h;            // [w]
+    const float* h;            // [w] (planes f*w + s in a batch)
+    // CTIS_BOUNDARY_CLIP: h per voxel, [w][out_h][out_w] (null otherwise); a
+    // batch's planes f*w + s use h_vox plane (f*w + s) % h_vox_planes
+    const float* h_vox;
+    int h_vox_planes;
     // kEpiRatio: write 1 - g / value instead of g / value (0 where value == 0)
     int ratio_one_minus;
     // kEpiGrad: f_in is the dense datacube [w][alpha][a] (out_w = a,

@@ -190,6 +190,8 @@ struct ctis_plan {
     int forced_split_q = 0;           // 0: chosen by schedule()
     int forced_skew_pm = 0;           // CTA priority skew of the model's schedule
     int host_ctas = 0;                // > 0: host-only tables for this many CTAs (no device)
+    bool clip = false;                // CTIS_BOUNDARY_CLIP: shifted nonzeros off the FPA dropped
+    float* d_hvox = nullptr;          // clip: h = H^T 1 per voxel [w][alpha][a]
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -248,6 +250,7 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_counters);
     cudaFree(P->d_tile_stats);
     cudaFree(P->d_red_part);
+    cudaFree(P->d_hvox);
     cudaFree(P->d_tap_slot);
     cudaFree(P->d_tap_s);
     cudaFree(P->d_grad_part);
@@ -651,7 +654,7 @@ int write_values(ctis_plan* P, bool allocate) {
 // Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
 // every shifted copy of every nonzero must stay on the FPA).
 int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
-                 const int32_t* psf_x, const int32_t* psf_y, const float* psf_val) {
+                 const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, bool clip) {
     const int64_t nnz_in = psf_ptr[w];
     for (int64_t k = 0; k < nnz_in; ++k) {
         const float v = psf_val[k];
@@ -659,6 +662,13 @@ int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
             return fail(CTIS_ERR_INVALID_ARG, "psf_val[%lld] = %g is not finite and >= 0",
                         (long long)k, (double)v);
         const int64_t x = psf_x[k], y = psf_y[k];
+        if (clip) {   // any position; the shifted copies off the FPA are dropped
+            if (x < -(int64_t{1} << 24) || x >= (int64_t{1} << 24) || y < -(int64_t{1} << 24) ||
+                y >= (int64_t{1} << 24))
+                return fail(CTIS_ERR_INVALID_ARG, "PSF nonzero %lld at (%lld, %lld) out of range",
+                            (long long)k, (long long)x, (long long)y);
+            continue;
+        }
         if (x < 0 || y < 0 || x + a - 1 >= ga || y + al - 1 >= xi)
             return fail(CTIS_ERR_OUT_OF_BOUNDS,
                         "PSF nonzero %lld at (%lld, %lld) leaves the %dx%d FPA when shifted "
@@ -666,6 +676,11 @@ int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
                         (long long)k, (long long)x, (long long)y, ga, xi, a, al);
     }
     return CTIS_OK;
+}
+
+// A map key for an FPA position, unique for any coordinates in [-2^31, 2^31).
+int64_t pos_key(int64_t x, int64_t y) {
+    return static_cast<int64_t>((static_cast<uint64_t>(y) << 32) ^ static_cast<uint32_t>(x));
 }
 
 int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
@@ -724,13 +739,12 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     for (int s = 0; s < w; ++s) {
         std::unordered_map<int64_t, int64_t> at;
         for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k)
-            at[static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
+            at[pos_key(P->tap_x[k], P->tap_y[k])] = k;
         for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k) {
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int64_t x = P->tap_x[k] + dx, y = P->tap_y[k] + dy;
-                    if (x < 0 || y < 0 || x >= ga || y >= xi) continue;
-                    auto it = at.find(y * ga + x);
+                    auto it = at.find(pos_key(x, y));
                     if (it != at.end()) {
                         const int64_t r1 = find(k), r2 = find(it->second);
                         if (r1 != r2) parent[std::max(r1, r2)] = std::min(r1, r2);
@@ -775,7 +789,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     for (int s = 0; s < w; ++s) {
         std::unordered_map<int64_t, int64_t> at;
         for (int64_t k = s_begin[s]; k < s_begin[s + 1]; ++k)
-            at[static_cast<int64_t>(P->tap_y[k]) * ga + P->tap_x[k]] = k;
+            at[pos_key(P->tap_x[k], P->tap_y[k])] = k;
         for (const Box& b : boxes) {
             if (b.s != s) continue;
             for (int by = b.y0; by <= b.y1; by += K)
@@ -785,7 +799,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                         for (int dx = 0; dx < K; ++dx) {
                             const int64_t x = bx + dx, y = by + dy;
                             if (x > b.x1 || y > b.y1) continue;
-                            auto it = at.find(y * ga + x);
+                            auto it = at.find(pos_key(x, y));
                             if (it == at.end() || P->tap_slot[it->second] >= 0) continue;
                             mine.emplace_back(it->second, dy * K + dx);
                         }
@@ -823,10 +837,14 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
         for (int64_t c = 0; c < ncl; ++c) {
             const Cluster& cl = P->clusters[c];
-            const int tx0 = cl.X / TX, tx1 = std::min(ntx - 1, (cl.X + fw - 1) / TX);
-            const int ty0 = cl.Y / TY, ty1 = std::min(nty - 1, (cl.Y + fh - 1) / TY);
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx)
+            // the footprint's tiles on the FPA (under clipping it may reach
+            // past any edge, or miss the FPA altogether)
+            const int64_t tx0 = std::max<int64_t>(0, floor_div(cl.X, TX));
+            const int64_t tx1 = std::min<int64_t>(ntx - 1, floor_div(int64_t{cl.X} + fw - 1, TX));
+            const int64_t ty0 = std::max<int64_t>(0, floor_div(cl.Y, TY));
+            const int64_t ty1 = std::min<int64_t>(nty - 1, floor_div(int64_t{cl.Y} + fh - 1, TY));
+            for (int64_t ty = ty0; ty <= ty1; ++ty)
+                for (int64_t tx = tx0; tx <= tx1; ++tx)
                     per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));
         }
         // Tiles no footprint meets hold H f = 0 whatever f is: they are left out
@@ -885,6 +903,10 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
                         const Cluster& cl = P->clusters[c];
                         const int64_t px = static_cast<int64_t>(cl.X) + td.x0;
                         const int64_t py = static_cast<int64_t>(cl.Y) + td.y0;
+                        // clipped boundary: a window wholly off the FPA adds nothing
+                        if (P->clip && (px >= ga || py >= xi || px + TX + K - 1 <= 0 ||
+                                        py + TY + K - 1 <= 0))
+                            continue;
                         const int64_t q = floor_mod(-px, P->u_copies);
                         TaskDesc t;
                         t.wx = static_cast<int>(px + q);
@@ -1030,6 +1052,8 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.counters = P->d_counters;
     p.tile_stats = P->d_tile_stats;
     p.h = P->d_h;
+    p.h_vox = P->d_hvox;
+    p.h_vox_planes = P->w;
     return p;
 }
 
@@ -1142,12 +1166,13 @@ int scatter_f(const ctis_plan* P, const void* src, int src_dtype, float value, c
     return CTIS_OK;
 }
 
-// Fills the FPA copies from a dense float32 caller image.
-int scatter_u(const ctis_plan* P, const float* src, cudaStream_t st) {
+// Fills the FPA copies from a dense float32 caller image (value everywhere
+// when src is NULL).
+int scatter_u(const ctis_plan* P, const float* src, cudaStream_t st, float value = 0.f) {
     CTIS_CUDA(launch_scatter_copies(kDtypeF32, P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch,
                                     P->u_copy_stride, src, kDtypeF32, P->gamma,
                                     static_cast<int64_t>(P->gamma) * P->xi, P->gamma, P->xi, 1,
-                                    0.f, st));
+                                    value, st));
     return CTIS_OK;
 }
 
@@ -1173,6 +1198,32 @@ void set_f_copies(const ctis_plan* P, GatherParams& p) {
 // the stream is being captured).
 int record(ctis_plan* P, int idx, cudaStream_t st) {
     CTIS_CUDA(cudaEventRecordWithFlags(P->events[idx], st, cudaEventRecordExternal));
+    return CTIS_OK;
+}
+
+// CTIS_BOUNDARY_CLIP: h = H^T 1 per voxel (Eq. 2's normaliser; the light of
+// voxels near the field stop's edges partly leaves the FPA), as the adjoint
+// of an all-ones FPA image: the copies hold 1 on the FPA and 0 around it.
+int compute_hvox(ctis_plan* P, cudaStream_t st) {
+    if (!P->clip) return CTIS_OK;
+    if (!P->d_hvox) {
+        const int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_hvox), sizeof(float) * P->m);
+        if (rc) return rc;
+    }
+    int rc = zero_u(P, st);
+    if (!rc) rc = scatter_u(P, nullptr, st, 1.0f);
+    if (rc) return rc;
+    GatherParams p = base_params(P, P->adj);
+    p.mode = kEpiRaw;
+    p.out_w = P->a;
+    p.out_h = P->alpha;
+    p.out_f32 = P->d_hvox;
+    p.out_pitch = P->a;
+    p.out_plane_stride = static_cast<long long>(P->a) * P->alpha;
+    p.h_vox = nullptr;
+    rc = enqueue_adjoint(P, p, st);
+    if (rc) return rc;
+    CTIS_CUDA(cudaStreamSynchronize(st));
     return CTIS_OK;
 }
 
@@ -1465,6 +1516,8 @@ GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward)
     p.counters = B->d_counters;
     p.tile_stats = B->d_tile_stats;
     p.h = B->d_h;
+    p.h_vox = P->d_hvox;
+    p.h_vox_planes = P->w;
     return p;
 }
 
@@ -1670,7 +1723,7 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
              const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, int dtype,
              const ctis_plan_options* opt) {
     if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
-    int forced_per_item = 0, forced_split_q = 0, forced_skew_pm = 0;
+    int forced_per_item = 0, forced_split_q = 0, forced_skew_pm = 0, boundary = 0;
     if (opt) {
         if (opt->struct_size != static_cast<int>(sizeof(ctis_plan_options)))
             return fail(CTIS_ERR_INVALID_ARG, "ctis_plan_options.struct_size mismatch");
@@ -1684,6 +1737,9 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
             return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item and item_overhead_q are exclusive");
         if (opt->cta_skew_permille < 0 || opt->cta_skew_permille > 900)
             return fail(CTIS_ERR_INVALID_ARG, "cta_skew_permille out of range [0, 900]");
+        if (opt->boundary != CTIS_BOUNDARY_REJECT && opt->boundary != CTIS_BOUNDARY_CLIP)
+            return fail(CTIS_ERR_INVALID_ARG, "boundary must be CTIS_BOUNDARY_REJECT or _CLIP");
+        boundary = opt->boundary;
         forced_per_item = opt->tasks_per_item;
         forced_split_q = opt->item_overhead_q;
         forced_skew_pm = opt->cta_skew_permille;
@@ -1709,7 +1765,8 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     if ((int64_t)psf_ptr[w] * 8 > (int64_t)1 << 31)
         return fail(CTIS_ERR_UNSUPPORTED, "too many PSF nonzeros");
     {
-        const int rc = validate_psf(a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val);
+        const int rc = validate_psf(a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val,
+                                    boundary == CTIS_BOUNDARY_CLIP);
         if (rc) return rc;
     }
 
@@ -1729,6 +1786,7 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     P->forced_per_item = forced_per_item;
     P->forced_split_q = forced_split_q;
     P->forced_skew_pm = forced_skew_pm;
+    P->clip = boundary == CTIS_BOUNDARY_CLIP;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
@@ -1757,6 +1815,7 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     }
     int rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
     if (!rc) rc = place_by_probe(P);
+    if (!rc) rc = compute_hvox(P, nullptr);
     if (!rc) {
         const cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = cuda_fail(e, "placing the work lists");
@@ -1876,6 +1935,7 @@ int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
     info->adj_split_q = P->adj.split_q;
     info->fwd_skew_pm = P->fwd.skew_pm;
     info->adj_skew_pm = P->adj.skew_pm;
+    info->boundary = P->clip ? CTIS_BOUNDARY_CLIP : CTIS_BOUNDARY_REJECT;
     return CTIS_OK;
 }
 
@@ -2102,7 +2162,9 @@ int ctis_plan_set_values(ctis_plan* P, const float* vals) {
     for (size_t k = 0; k < nnz; ++k)
         P->tap_v[k] = P->dtype == kDtypeBF16 ? bf16_bits_to_float(to_bf16_bits(vals[k])) : vals[k];
     compute_h(P);
-    return write_values(P, false);
+    rc = write_values(P, false);
+    if (!rc) rc = compute_hvox(P, nullptr);
+    return rc;
 }
 
 int ctis_psf_grad(const ctis_plan* P, const void* f_dev, const float* r_dev, float* dval_dev,
@@ -2122,6 +2184,9 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     if (rc) return rc;
     if (P->dtype != kDtypeF32)
         return fail(CTIS_ERR_UNSUPPORTED, "the unrolled EM gradient needs a float32 plan");
+    if (P->clip)
+        return fail(CTIS_ERR_UNSUPPORTED,
+                    "the unrolled EM gradient needs CTIS_BOUNDARY_REJECT (h per wavelength)");
     if (!g_dev || !nll_dev || !dval_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
     if (k < 0 || k > 4096) return fail(CTIS_ERR_INVALID_ARG, "k must be in [0, 4096]");
     const int64_t m = P->m, n = P->n;

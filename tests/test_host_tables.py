@@ -17,10 +17,21 @@ from paper_2006_01573_gb300 import CtisError, tables_inspect
 RAGGED = synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7, "mask_spectra", 100.0, 3)
 K5 = synth.Workload("k5", 20, 24, 6, 120, 110, 3, 36.0, 1.2, 5, 1.2, "segmentation", 100.0, 3)
 WORKLOADS = [synth.TINY, RAGGED, K5, synth.MODEL_A]
+# clipped boundary: the PSF shifted so that some orders spill past FPA edges
+CLIPPED = [(RAGGED, (-9, 4)), (synth.MODEL_A, (-40, 35)), (K5, (30, -20))]
 
 
-def _inspect(wl, forward, n_ctas, **kw):
-    return tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), forward,
+def _psf(wl, shift=None):
+    ptr, x, y, v = synth.make_psf(wl)
+    if shift is not None:
+        x, y = x + shift[0], y + shift[1]
+    return ptr, x, y, v
+
+
+def _inspect(wl, forward, n_ctas, shift=None, **kw):
+    if shift is not None:
+        kw["boundary"] = "clip"
+    return tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, _psf(wl, shift), forward,
                           n_ctas, **kw)
 
 
@@ -30,10 +41,18 @@ def _tile_tasks(t):
             for i in range(t["tiles"])}
 
 
-@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
-def test_clusters_cover_every_psf_nonzero(wl):
-    ptr, x, y, _ = synth.make_psf(wl)
-    t = _inspect(wl, True, 8)
+CASES = [(wl, None) for wl in WORKLOADS] + CLIPPED
+
+
+def _case_id(c):
+    return c[0].name + ("" if c[1] is None else f"_clip{c[1][0]}_{c[1][1]}")
+
+
+@pytest.mark.parametrize("case", CASES, ids=_case_id)
+def test_clusters_cover_every_psf_nonzero(case):
+    wl, shift = case
+    ptr, x, y, _ = _psf(wl, shift)
+    t = _inspect(wl, True, 8, shift)
     K = t["cluster_k"]
     cl = t["cluster_sxy"]
     for s in range(wl.w):
@@ -48,9 +67,12 @@ def test_clusters_cover_every_psf_nonzero(wl):
         assert np.any((X <= xs) & (xs < X + K) & (Y <= ys) & (ys < Y + K))
 
 
-@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
-def test_forward_tasks_are_the_footprint_overlaps(wl):
-    t = _inspect(wl, True, 8)
+@pytest.mark.parametrize("case", CASES, ids=_case_id)
+def test_forward_tasks_are_the_footprint_overlaps(case):
+    """A forward task exists exactly when the cluster's footprint meets an FPA
+    tile (under clipping only its part on the FPA counts)."""
+    wl, shift = case
+    t = _inspect(wl, True, 8, shift)
     K, TW, TH = t["cluster_k"], t["tile_w"], t["tile_h"]
     expect = {}
     for c, (s, X, Y) in enumerate(t["cluster_sxy"]):
@@ -64,17 +86,24 @@ def test_forward_tasks_are_the_footprint_overlaps(wl):
     assert got == {k: sorted(v) for k, v in expect.items()}   # no tile without a task
 
 
-@pytest.mark.parametrize("wl", WORKLOADS, ids=lambda w: w.name)
-def test_adjoint_tasks_are_the_clusters_of_the_plane(wl):
-    t = _inspect(wl, False, 8)
-    TW, TH = t["tile_w"], t["tile_h"]
+@pytest.mark.parametrize("case", CASES, ids=_case_id)
+def test_adjoint_tasks_are_the_clusters_of_the_plane(case):
+    """A voxel tile of wavelength s lists the clusters of s; under clipping
+    only those whose window (tile plus the K - 1 halo, at the cluster's
+    offset) meets the FPA."""
+    wl, shift = case
+    t = _inspect(wl, False, 8, shift)
+    TW, TH, K = t["tile_w"], t["tile_h"], t["cluster_k"]
     cl = t["cluster_sxy"]
     expect = {}
     for s in range(wl.w):
-        of_s = sorted(np.nonzero(cl[:, 0] == s)[0].tolist())
         for ty in range(0, wl.alpha, TH):
             for tx in range(0, wl.a, TW):
-                expect[(tx, ty, s)] = of_s
+                expect[(tx, ty, s)] = sorted(
+                    c for c in np.nonzero(cl[:, 0] == s)[0].tolist()
+                    if shift is None or (cl[c, 1] + tx < wl.gamma and cl[c, 2] + ty < wl.xi and
+                                         cl[c, 1] + tx + TW + K - 1 > 0 and
+                                         cl[c, 2] + ty + TH + K - 1 > 0))
     assert _tile_tasks(t) == expect
 
 
@@ -174,6 +203,14 @@ def test_sm_map_balances_the_sms():
         assert blind.sum() == aware.sum()
         assert aware.max() - aware.min() <= blind.max() - blind.min()
         assert aware.max() <= 1.1 * aware.mean()
+
+
+def test_clip_is_needed_for_a_psf_that_leaves_the_fpa():
+    wl, shift = CLIPPED[0]
+    with pytest.raises(CtisError):
+        tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, _psf(wl, shift), True, 8)
+    t = _inspect(wl, True, 8, shift)
+    _check_schedule(t)
 
 
 def test_inspect_rejects_bad_arguments():
