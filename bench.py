@@ -421,6 +421,7 @@ def run_ours(args, wl, k):
     }
     line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value)}
     if world == 1 and not args.no_forms:
+        line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
         line["forms"]["batched"] = batched_form(args, flush, stream)
         line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
@@ -465,6 +466,31 @@ def bf16_form(args, wl, k, psf, g, f32_result, flush, stream, f32_value):
     plan.close()
     return {"value": value, "unit": "it/s", "steps": steps, "vs_f32": value / f32_value,
             "rel_l2_vs_f32_after_k": err, "dtype": "bf16 storage, f32 accumulate"}
+
+
+def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=10):
+    """The paper's own (WBH) form of the projectors, on the same workload and
+    g: k EM updates with cuFFT transforms of length n and this project's
+    spectral multiply-accumulate and index maps (Eqs. 11, 13, 14, 17). Its
+    iterations/s, the ratio to the gather path, and its distance from the
+    gather reconstruction after k iterations (both from ones)."""
+    import torch
+    from paper_2006_01573_gb300 import Plan
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+    f = torch.empty(f32_result.shape, device=g.device)
+    for _ in range(max(1, args.warmup)):
+        plan.fft_reconstruct(g, k, f=f.fill_(1.0))
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    total = _timed_steps(lambda: plan.fft_reconstruct(g, k, f=f.fill_(1.0)), steps, flush, stream)
+    ref, _ = plan.reconstruct(g, k, init="ones")
+    plan.check()
+    err = float(torch.linalg.vector_norm(f.double() - ref.double()) / torch.linalg.vector_norm(ref.double()))
+    plan.close()
+    value = steps * k / (total / 1e3)
+    return {"value": value, "unit": "it/s", "k": k, "steps": steps, "vs_gather": value / f32_value,
+            "rel_l2_vs_gather_after_k": err,
+            "form": "cuFFT R2C/C2R of length n per wavelength + spectral MAC (float32)"}
 
 
 def _timed_steps(fn, steps, flush, stream):

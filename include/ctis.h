@@ -324,6 +324,24 @@ int ctis_plan_autotune(ctis_plan* plan, const float* g_dev, void* stream);
 int ctis_plan_set_schedule(ctis_plan* plan, int forward, int tasks_per_item, int item_overhead_q,
                            int cta_skew_permille);
 
+/* The paper's own (WBH) form of the projectors, for comparison with the
+ * gather path: H_s = C_s E with C_s the length-n circulant whose first column
+ * is the calibration image c_s (Eq. 7), so H f = F^-1 sum_s d_s (.) F E f_s
+ * (Eqs. 11, 13) and H^T u = E^T stack_s F^-1 (conj(d_s) (.) F u) (Eqs. 14,
+ * 17), d_s = F c_s, F the length-n real-to-complex transform (cuFFT, float32).
+ * Built on the first call (w x (n/2+1) complex spectra and as many work
+ * vectors, ~3 w n float32 of device memory). float32 plans with
+ * CTIS_BOUNDARY_REJECT only (CTIS_ERR_UNSUPPORTED otherwise). Calls on one
+ * plan share its workspace: issue them on one stream.
+ *   ctis_fft_forward:     hf_dev (n) = H f_dev (m), dense layouts as ctis_forward.
+ *   ctis_fft_adjoint:     out_dev (m) = H^T r_dev (n).
+ *   ctis_fft_reconstruct: k EM updates (Eq. 2, Algorithm 1) of f_dev in place,
+ *                         from ones with CTIS_INIT_ONES, else from f_dev. */
+int ctis_fft_forward(ctis_plan* plan, const float* f_dev, float* hf_dev, void* stream);
+int ctis_fft_adjoint(ctis_plan* plan, const float* r_dev, float* out_dev, void* stream);
+int ctis_fft_reconstruct(ctis_plan* plan, const float* g_dev, float* f_dev, int k, int flags,
+                         void* stream);
+
 /* Wait for the plan's work on `stream`, then report (and clear) any device-side
  * failure recorded by its kernels: CTIS_OK or CTIS_ERR_TIMEOUT. */
 int ctis_plan_check(const ctis_plan* plan, void* stream);

@@ -30,6 +30,7 @@ EXPORTED = (
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
+    "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
         "ctis_plan_set_values": (I, [P, f32p]),
         "ctis_plan_autotune": (I, [P, VP, VP]),
         "ctis_plan_set_schedule": (I, [P, I, I, I, I]),
+        "ctis_fft_forward": (I, [P, VP, VP, VP]),
+        "ctis_fft_adjoint": (I, [P, VP, VP, VP]),
+        "ctis_fft_reconstruct": (I, [P, VP, VP, I, I, VP]),
         "ctis_reconstruct_batched": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
                                          ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
@@ -339,6 +343,41 @@ class Plan:
         self._check_fpa(g)
         _check(load().ctis_plan_autotune(self._h, ctypes.c_void_p(g.data_ptr()), _stream(stream)))
         return self.schedules()
+
+    # -- the paper's FFT form (comparison path) ------------------------------------
+    def fft_forward(self, f, out=None, stream=None):
+        """``H f`` by the paper's FFT form (Eqs. 11, 13); float32 plans."""
+        import torch
+        self._check_cube(f, torch.float32)
+        out = out if out is not None else torch.empty((self.xi, self.gamma), device=f.device)
+        _check(load().ctis_fft_forward(self._h, ctypes.c_void_p(f.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def fft_adjoint(self, r, out=None, stream=None):
+        """``H^T r`` by the paper's FFT form (Eqs. 14, 17); float32 plans."""
+        import torch
+        self._check_fpa(r)
+        out = out if out is not None else torch.empty((self.w, self.alpha, self.a), device=r.device)
+        _check(load().ctis_fft_adjoint(self._h, ctypes.c_void_p(r.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def fft_reconstruct(self, g, k: int, f=None, stream=None):
+        """k EM updates with the FFT-form projectors (Algorithm 1), from ones
+        or from ``f`` (float32, updated in place); returns f."""
+        import torch
+        self._check_fpa(g)
+        flags = 0
+        if f is None:
+            f = torch.empty((self.w, self.alpha, self.a), device=g.device)
+            flags = CTIS_INIT_ONES
+        else:
+            self._check_cube(f, torch.float32)
+        _check(load().ctis_fft_reconstruct(self._h, ctypes.c_void_p(g.data_ptr()),
+                                           ctypes.c_void_p(f.data_ptr()), int(k), flags,
+                                           _stream(stream)))
+        return f
 
     def set_schedule(self, forward: bool, sched):
         """Reschedule one projector: ``sched`` is ``(kind, value, skew)`` as

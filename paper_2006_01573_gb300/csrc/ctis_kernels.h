@@ -107,4 +107,16 @@ cudaError_t launch_add(float* out, const float* x, const float* y, long long n,
                        cudaStream_t stream);
 cudaError_t launch_negate(double* out, const double* in, cudaStream_t stream);
 
+// The paper's FFT form of the projectors (ctis_fft.cu): H_s = C_s E with
+// circulant C_s (Eqs. 7, 11, 13, 14, 17), the transforms by cuFFT.
+// calib_host: [w][n] float32 calibration images c_s; h_host: [w].
+struct FftForm;
+cudaError_t fft_form_create(FftForm** out, int a, int alpha, int w, int gamma, int xi,
+                            const float* calib_host, const float* h_host);
+void fft_form_destroy(FftForm* F);
+cudaError_t fft_form_forward(FftForm* F, const float* f, float* hf, cudaStream_t st);
+cudaError_t fft_form_adjoint(FftForm* F, const float* u, float* out, cudaStream_t st);
+cudaError_t fft_form_reconstruct(FftForm* F, const float* g, float* f, float* u_work, int k,
+                                 bool init_ones, cudaStream_t st);
+
 }  // namespace ctis

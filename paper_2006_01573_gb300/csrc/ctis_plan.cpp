@@ -192,6 +192,8 @@ struct ctis_plan {
     int host_ctas = 0;                // > 0: host-only tables for this many CTAs (no device)
     bool clip = false;                // CTIS_BOUNDARY_CLIP: shifted nonzeros off the FPA dropped
     float* d_hvox = nullptr;          // clip: h = H^T 1 per voxel [w][alpha][a]
+    FftForm* fft = nullptr;           // the paper's FFT form, built on first use
+    float* d_fft_u = nullptr;         // its EM ratio [n]
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -251,6 +253,8 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_tile_stats);
     cudaFree(P->d_red_part);
     cudaFree(P->d_hvox);
+    fft_form_destroy(P->fft);
+    cudaFree(P->d_fft_u);
     cudaFree(P->d_tap_slot);
     cudaFree(P->d_tap_s);
     cudaFree(P->d_grad_part);
@@ -2148,6 +2152,68 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     return CTIS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Builds the plan's FFT form on first use: the calibration images c_s of the
+// merged nonzeros (as stored), d_s = F c_s, h per wavelength.
+int ensure_fft(ctis_plan* P) {
+    if (P->fft) return CTIS_OK;
+    if (P->clip)
+        return fail(CTIS_ERR_UNSUPPORTED,
+                    "the FFT form needs CTIS_BOUNDARY_REJECT (Eq. 7's circulant wraps)");
+    if (P->dtype != kDtypeF32) return fail(CTIS_ERR_UNSUPPORTED, "the FFT form needs a float32 plan");
+    const int64_t n = P->n;
+    std::vector<float> calib(static_cast<size_t>(n) * P->w, 0.f);
+    for (size_t k = 0; k < P->tap_v.size(); ++k)
+        calib[static_cast<size_t>(P->tap_s[k]) * n + P->tap_x[k] +
+              static_cast<int64_t>(P->gamma) * P->tap_y[k]] += P->tap_v[k];
+    int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_fft_u), sizeof(float) * n);
+    if (rc) return rc;
+    CTIS_CUDA(fft_form_create(&P->fft, P->a, P->alpha, P->w, P->gamma, P->xi, calib.data(),
+                              P->h.data()));
+    return CTIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctis_fft_forward(ctis_plan* P, const float* f_dev, float* hf_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!f_dev || !hf_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    rc = ensure_fft(P);
+    if (rc) return rc;
+    CTIS_CUDA(fft_form_forward(P->fft, f_dev, hf_dev, static_cast<cudaStream_t>(stream)));
+    return CTIS_OK;
+}
+
+int ctis_fft_adjoint(ctis_plan* P, const float* r_dev, float* out_dev, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!r_dev || !out_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    rc = ensure_fft(P);
+    if (rc) return rc;
+    CTIS_CUDA(fft_form_adjoint(P->fft, r_dev, out_dev, static_cast<cudaStream_t>(stream)));
+    return CTIS_OK;
+}
+
+int ctis_fft_reconstruct(ctis_plan* P, const float* g_dev, float* f_dev, int k, int flags,
+                         void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!g_dev || !f_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    if (k < 0) return fail(CTIS_ERR_INVALID_ARG, "k must be >= 0");
+    if (flags & ~CTIS_INIT_ONES) return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    rc = ensure_fft(P);
+    if (rc) return rc;
+    CTIS_CUDA(fft_form_reconstruct(P->fft, g_dev, f_dev, P->d_fft_u, k, (flags & CTIS_INIT_ONES) != 0,
+                                   static_cast<cudaStream_t>(stream)));
+    return CTIS_OK;
+}
+
 int ctis_plan_set_values(ctis_plan* P, const float* vals) {
     int rc = check_plan(P);
     if (rc) return rc;
@@ -2164,6 +2230,8 @@ int ctis_plan_set_values(ctis_plan* P, const float* vals) {
     compute_h(P);
     rc = write_values(P, false);
     if (!rc) rc = compute_hvox(P, nullptr);
+    fft_form_destroy(P->fft);   // rebuilt from the new values on its next use
+    P->fft = nullptr;
     return rc;
 }
 

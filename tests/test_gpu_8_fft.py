@@ -1,0 +1,103 @@
+"""GPU checks of the paper's own FFT form of the projectors (ctis_fft_*:
+H_s = C_s E with circulant C_s, Eqs. 7, 11, 13, 14, 17; cuFFT in float32)
+against the FP64 oracle and against the gather projectors.
+
+Tolerance: a float32 real transform of length n carries a normwise rounding
+error of order eps * log2(n) (eps = 2^-24; log2 n <= 20 here), and a
+projection chains a forward and an inverse transform around a sum over w
+spectra; so the bound is stated normwise: max |a - b| <= 2e-5 * max |b|
+(~8 eps log2 n), where the gather path's per-pixel bound does not apply to
+pixels far below the maximum."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle as O
+import synth
+from paper_2006_01573_gb300 import CtisError, Plan
+from tests.helpers import geometry, problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+RAGGED = synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7, "mask_spectra", 500.0, 6)
+K5 = synth.Workload("k5", 20, 24, 6, 120, 110, 3, 36.0, 1.2, 5, 1.2, "segmentation", 800.0, 6)
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _normwise(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("wl", [synth.TINY, RAGGED, K5, synth.MODEL_A], ids=lambda w: w.name)
+def test_fft_projectors_match_the_oracle_and_the_gather(wl):
+    geom = geometry(wl)
+    psf = synth.make_psf(wl)
+    H = O.build_H(geom, psf)
+    f = synth.random_positive((wl.w, wl.alpha, wl.a), 81)
+    r = synth.random_positive((wl.xi, wl.gamma), 82)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        ft, rt = torch.from_numpy(f).cuda(), torch.from_numpy(r).cuda()
+        hf = plan.fft_forward(ft).cpu().numpy()
+        ht = plan.fft_adjoint(rt).cpu().numpy()
+        hf_g = plan.forward(ft).cpu().numpy()
+        ht_g = plan.adjoint(rt).cpu().numpy()
+        plan.check()
+    ref_f, ref_t = H.forward(f.ravel()), H.adjoint(r.ravel())
+    assert _normwise(hf, ref_f) <= TOL
+    assert _normwise(ht, ref_t) <= TOL
+    assert _normwise(hf, hf_g) <= TOL and _normwise(ht, ht_g) <= TOL
+
+
+def test_fft_form_also_matches_the_oracle_fft_form():
+    """The oracle's own float64 FFT form (pinned to the sparse H) as a second
+    reference for the transform arithmetic."""
+    wl = RAGGED
+    geom = geometry(wl)
+    psf = synth.make_psf(wl)
+    f = synth.random_positive((wl.w, wl.alpha, wl.a), 83)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        hf = plan.fft_forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert _normwise(hf, O.fft_forward(geom, psf, f.ravel())) <= TOL
+
+
+@pytest.mark.parametrize("wl", [synth.TINY, RAGGED], ids=lambda w: w.name)
+def test_fft_em_iterations_match_the_oracle(wl):
+    """k EM updates (Algorithm 1) with the FFT projectors: relative L2 of the
+    iterate within sqrt(k) times the projector bound."""
+    geom, psf, H, _, g = problem(wl)
+    k = wl.k
+    ref, _ = O.mlem(H, g, k)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        f = plan.fft_reconstruct(torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda(), k)
+        plan.check()
+        got = f.cpu().numpy().ravel()
+    assert rel_l2(got, ref) <= 2 * TOL * math.sqrt(k)
+    # from a given iterate: one more update equals the oracle's step
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        f0 = torch.from_numpy(ref.astype(np.float32).reshape(wl.w, wl.alpha, wl.a)).cuda()
+        f1 = plan.fft_reconstruct(torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda(), 1, f=f0)
+        step = O.em_step(H, g, ref.astype(np.float32).astype(np.float64))
+    assert rel_l2(f1.cpu().numpy().ravel(), step) <= 2 * TOL
+
+
+def test_fft_form_needs_reject_boundary_and_float32():
+    wl = RAGGED
+    psf = synth.make_psf(wl)
+    ptr, x, y, v = psf
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, (ptr, x - 9, y + 4, v), boundary="clip") as p:
+        with pytest.raises(CtisError):
+            p.fft_forward(torch.ones((wl.w, wl.alpha, wl.a), device="cuda"))
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16") as p:
+        with pytest.raises(CtisError):
+            p.fft_adjoint(torch.ones((wl.xi, wl.gamma), device="cuda"))
