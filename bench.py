@@ -54,6 +54,10 @@ def parse_args():
                     help="skip the autotuner and use these schedules, 'FWD,ADJ' with each "
                          "'chunk:TASKS:SKEW' or 'split:OVERHEAD_Q:SKEW' (SKEW in permille), "
                          "e.g. a bench line's config.schedule.spec")
+    ap.add_argument("--crossover", default=None, metavar="OUT_JSON",
+                    help="instead of the bench line: sweep the spot size on the realistic "
+                         "geometry, time the gather and the FFT form per EM iteration, write "
+                         "the table to OUT_JSON and print a one-line summary")
     return ap.parse_args()
 
 
@@ -589,9 +593,83 @@ def autograd_form(args, flush, stream, k=10):
             "grad_entries": int(info["nnz"])}
 
 
+CROSSOVER_SPOTS = (3, 5, 7, 9, 11, 13, 15, 17, 21)
+
+
+def run_crossover(args, spots=CROSSOVER_SPOTS, k_gather=20, k_fft=5):
+    """Gather vs the paper's FFT form as the PSF densifies: the realistic
+    geometry (128x128x64 -> 1024^2, 5x5 orders) with square spots of side S
+    (S^2 nonzeros per order, Gaussian sigma 0.8 S / 3, so 25 S^2 per
+    calibration image). Per S: microseconds per EM iteration of each form
+    (gather with its float64 statistics, autotuned; FFT without), L2
+    flushed between timed runs, and the relative L2 distance of the two
+    iterates after k_fft iterations. The gather's work grows with the
+    nonzeros, the FFT form's does not; the crossover is where the two
+    times meet, interpolated linearly in nnz between the bracketing sizes."""
+    import torch
+    import synth
+    from paper_2006_01573_gb300 import Plan
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    steps = max(1, min(args.steps, 3))
+    rows = []
+    for S in spots:
+        wl = synth.REALISTIC.with_(name=f"realistic_spot{S}", spot=S, sigma=0.8 * S / 3)
+        psf = synth.make_psf(wl)
+        plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+        hf = plan.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
+        g_host, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, wl.seed)
+        g = torch.from_numpy(g_host).cuda()
+        plan.autotune(g)
+        f = torch.empty((wl.w, wl.alpha, wl.a), device="cuda")
+        st = torch.empty((k_gather + 1, 4), device="cuda", dtype=torch.float64)
+        gather = lambda: plan.reconstruct(g, k_gather, f=f, init="ones", stats=st)
+        ff = torch.empty_like(f)
+        fft = lambda: plan.fft_reconstruct(g, k_fft, f=ff.fill_(1.0))
+        for _ in range(max(1, args.warmup)):
+            gather()
+            fft()
+        torch.cuda.synchronize()
+        t_g = _timed_steps(gather, steps, flush, stream) / steps / k_gather * 1e3
+        t_f = _timed_steps(fft, steps, flush, stream) / steps / k_fft * 1e3
+        ref, _ = plan.reconstruct(g, k_fft, init="ones")
+        plan.check()
+        err = float(torch.linalg.vector_norm(ff.double() - ref.double()) /
+                    torch.linalg.vector_norm(ref.double()))
+        info = plan.info()
+        rows.append({"spot": S, "nnz_per_image": int(info["nnz"]) // wl.w,
+                     "cluster_k": int(info["cluster_k"]), "gather_us_per_it": t_g,
+                     "fft_us_per_it": t_f, "fft_over_gather": t_f / t_g,
+                     "rel_l2_fft_vs_gather_after_k": err})
+        plan.close()
+        del f, ff, g, hf
+        torch.cuda.empty_cache()
+    cross = None
+    for a, b in zip(rows, rows[1:]):
+        da = a["gather_us_per_it"] - a["fft_us_per_it"]
+        db = b["gather_us_per_it"] - b["fft_us_per_it"]
+        if da <= 0 < db:
+            t = -da / (db - da)
+            cross = a["nnz_per_image"] + t * (b["nnz_per_image"] - a["nnz_per_image"])
+            break
+    out = {"workload": "realistic 128x128x64 -> 1024^2, 5x5 orders, spot S x S",
+           "k_gather": k_gather, "k_fft": k_fft, "steps": steps,
+           "l2": "flushed between timed runs (256 MiB write)",
+           "rows": rows, "crossover_nnz_per_image": cross}
+    with open(args.crossover, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps({"crossover_nnz_per_image": cross,
+                      "points": [(r["nnz_per_image"], round(r["gather_us_per_it"], 1),
+                                  round(r["fft_us_per_it"], 1)) for r in rows]}), flush=True)
+
+
 def main():
     args = parse_args()
     import synth
+    if args.crossover:
+        run_crossover(args)
+        return
     wl = synth.WORKLOADS[args.workload]
     k = args.k if args.k is not None else wl.k
     if args.impl == "reference":

@@ -130,7 +130,8 @@ struct FftForm {
     cufftComplex* D = nullptr;   // [w][beta] d_s = F c_s
     cufftComplex* X = nullptr;   // [w][beta] spectra of the w vectors
     cufftComplex* S = nullptr;   // [beta]
-    float* v = nullptr;          // [w][n] real vectors
+    float* v = nullptr;          // [w][n] v_s = E f_s: zero off the embedded positions
+    float* z = nullptr;          // [w][n] the adjoint's inverse transforms
     float* q = nullptr;          // [n]
     float* hd = nullptr;         // [w] h per wavelength
 };
@@ -153,6 +154,7 @@ void fft_form_destroy(FftForm* F) {
     cudaFree(F->X);
     cudaFree(F->S);
     cudaFree(F->v);
+    cudaFree(F->z);
     cudaFree(F->q);
     cudaFree(F->hd);
     delete F;
@@ -175,6 +177,7 @@ cudaError_t fft_form_create(FftForm** out, int a, int alpha, int w, int gamma, i
     if (e == cudaSuccess) e = cudaMalloc(&F->X, sizeof(cufftComplex) * beta * w);
     if (e == cudaSuccess) e = cudaMalloc(&F->S, sizeof(cufftComplex) * beta);
     if (e == cudaSuccess) e = cudaMalloc(&F->v, sizeof(float) * n * w);
+    if (e == cudaSuccess) e = cudaMalloc(&F->z, sizeof(float) * n * w);
     if (e == cudaSuccess) e = cudaMalloc(&F->q, sizeof(float) * n);
     if (e == cudaSuccess) e = cudaMalloc(&F->hd, sizeof(float) * w);
     int nn = static_cast<int>(n);
@@ -195,6 +198,10 @@ cudaError_t fft_form_create(FftForm** out, int a, int alpha, int w, int gamma, i
         e = cudaMemcpy(F->v, calib_host, sizeof(float) * n * w, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(F->hd, h_host, sizeof(float) * w, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cufft_err(cufftExecR2C(F->r2c_w, F->v, F->D));
+    // v then holds only E f_s: the embedding rewrites the same positions
+    // every time and nothing else writes v (an out-of-place real-to-complex
+    // transform leaves its input as it was)
+    if (e == cudaSuccess) e = cudaMemset(F->v, 0, sizeof(float) * n * w);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         fft_form_destroy(F);
@@ -207,8 +214,7 @@ cudaError_t fft_form_create(FftForm** out, int a, int alpha, int w, int gamma, i
 // raw = n * H f (no 1/n yet), into F->q.
 static cudaError_t forward_raw(FftForm* F, const float* f, cudaStream_t st) {
     const long long n = F->n, beta = F->beta, m = (long long)F->a * F->alpha * F->w;
-    cudaError_t e = cudaMemsetAsync(F->v, 0, sizeof(float) * n * F->w, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     embed_kernel<<<blocks_for(m), kThreads, 0, st>>>(F->v, f, F->a, F->alpha, F->w, F->gamma, n);
     e = cufft_err(cufftSetStream(F->r2c_w, st));
     if (e == cudaSuccess) e = cufft_err(cufftExecR2C(F->r2c_w, F->v, F->X));
@@ -220,7 +226,7 @@ static cudaError_t forward_raw(FftForm* F, const float* f, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// F->v = n * stack_s C_s^T u (no 1/n yet).
+// F->z = n * stack_s C_s^T u (no 1/n yet).
 static cudaError_t adjoint_raw(FftForm* F, const float* u, cudaStream_t st) {
     const long long beta = F->beta;
     cudaError_t e = cufft_err(cufftSetStream(F->r2c_1, st));
@@ -228,7 +234,7 @@ static cudaError_t adjoint_raw(FftForm* F, const float* u, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     expand_kernel<<<blocks_for(beta * F->w), kThreads, 0, st>>>(F->X, F->D, F->S, F->w, beta);
     e = cufft_err(cufftSetStream(F->c2r_w, st));
-    if (e == cudaSuccess) e = cufft_err(cufftExecC2R(F->c2r_w, F->X, F->v));
+    if (e == cudaSuccess) e = cufft_err(cufftExecC2R(F->c2r_w, F->X, F->z));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -244,7 +250,7 @@ cudaError_t fft_form_adjoint(FftForm* F, const float* u, float* out, cudaStream_
     cudaError_t e = adjoint_raw(F, u, st);
     if (e != cudaSuccess) return e;
     const long long m = (long long)F->a * F->alpha * F->w;
-    crop_kernel<<<blocks_for(m), kThreads, 0, st>>>(out, F->v, F->a, F->alpha, F->w, F->gamma, F->n,
+    crop_kernel<<<blocks_for(m), kThreads, 0, st>>>(out, F->z, F->a, F->alpha, F->w, F->gamma, F->n,
                                                     1.0f / float(F->n));
     return cudaGetLastError();
 }
@@ -261,7 +267,7 @@ cudaError_t fft_form_reconstruct(FftForm* F, const float* g, float* f, float* u_
         ratio_kernel<<<blocks_for(F->n), kThreads, 0, st>>>(u_work, g, F->q, F->n, float(F->n));
         e = adjoint_raw(F, u_work, st);
         if (e != cudaSuccess) return e;
-        update_kernel<<<blocks_for(m), kThreads, 0, st>>>(f, F->v, F->hd, F->a, F->alpha, F->w,
+        update_kernel<<<blocks_for(m), kThreads, 0, st>>>(f, F->z, F->hd, F->a, F->alpha, F->w,
                                                           F->gamma, F->n, 1.0f / float(F->n));
     }
     return cudaGetLastError();

@@ -101,3 +101,27 @@ def test_fft_form_needs_reject_boundary_and_float32():
     with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16") as p:
         with pytest.raises(CtisError):
             p.fft_adjoint(torch.ones((wl.xi, wl.gamma), device="cuda"))
+
+
+def test_fft_calls_in_sequence_are_independent():
+    """The embedded vectors are written only at the embedded positions and
+    reused across calls, and the adjoint has its own output buffers: a
+    forward after other forwards and adjoints equals the same forward alone,
+    bit for bit, and the oracle."""
+    wl = RAGGED
+    geom = geometry(wl)
+    psf = synth.make_psf(wl)
+    f1 = synth.random_positive((wl.w, wl.alpha, wl.a), 84)
+    f2 = synth.random_positive((wl.w, wl.alpha, wl.a), 85)
+    r = synth.random_positive((wl.xi, wl.gamma), 86)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        t1, t2, tr = (torch.from_numpy(x).cuda() for x in (f1, f2, r))
+        first = plan.fft_forward(t1).clone()
+        plan.fft_adjoint(tr)
+        second = plan.fft_forward(t2)
+        plan.fft_adjoint(tr)
+        again = plan.fft_forward(t1)
+        plan.check()
+        assert torch.equal(first, again)
+    H = O.build_H(geom, psf)
+    assert _normwise(second.cpu().numpy(), H.forward(f2.ravel())) <= TOL
