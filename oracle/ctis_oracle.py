@@ -34,7 +34,10 @@ are promoted exactly. Readings of points the paper leaves open:
   :func:`check_bounds`); then the circulant form of Eq. 7 and the 2-D shift agree.
   The optional clip reading (``boundary="clip"``) keeps the physical 2-D shift
   and drops the shifted nonzeros that leave the FPA (the light is lost), so
-  ``h`` then varies from voxel to voxel;
+  ``h`` then varies from voxel to voxel; the wrap reading (``boundary="wrap"``)
+  is Eq. 7 taken literally: row ``(x + p + gamma (y + r)) mod n``, so a
+  shifted nonzero past the right edge re-enters at the left of the next FPA
+  row and one past the last row re-enters at the top;
 * ``u_i = 0`` where ``(Hf)_i = 0`` and ``f_j = 0`` where ``h_j = 0`` (Eq. 2 leaves
   both divisions undefined);
 * duplicate PSF entries at one FPA position add up (H is a sum of responses);
@@ -86,6 +89,7 @@ class Taps:
     y: np.ndarray
     v: np.ndarray
     ptr: np.ndarray   # [w+1] start of each wavelength's taps
+    wrap: bool = False   # boundary "wrap": shifted positions taken mod n (Eq. 7)
 
     def of(self, s: int):
         lo, hi = int(self.ptr[s]), int(self.ptr[s + 1])
@@ -99,7 +103,9 @@ class OutOfBounds(ValueError):
 def check_bounds(geom: Geometry, psf, boundary: str = "reject") -> None:
     """Reject a PSF whose shifted copies would leave the FPA (``boundary=
     "reject"``); with ``boundary="clip"`` such nonzeros are allowed and the
-    projectors drop the shifted positions off the FPA.
+    projectors drop the shifted positions off the FPA; with ``boundary=
+    "wrap"`` every nonzero must lie on the FPA (it is an entry of the length-n
+    first column ``c_s`` of Eq. 7) and its shifted copies wrap mod n.
 
     Column j = (p, r, s) of H holds the calibration image of wavelength s shifted
     by (p, r) (Sec. 2). Every shifted nonzero must satisfy ``0 <= x + p < gamma``
@@ -110,12 +116,17 @@ def check_bounds(geom: Geometry, psf, boundary: str = "reject") -> None:
     ptr, x, y, _ = psf
     if len(ptr) != geom.w + 1:
         raise ValueError("psf_ptr must have w+1 entries")
-    if boundary not in ("reject", "clip"):
+    if boundary not in ("reject", "clip", "wrap"):
         raise ValueError(boundary)
     if boundary == "clip":
         return
     x = np.asarray(x, dtype=np.int64)
     y = np.asarray(y, dtype=np.int64)
+    if boundary == "wrap":
+        if x.size and (x.min() < 0 or y.min() < 0 or x.max() >= geom.gamma or
+                       y.max() >= geom.xi):
+            raise OutOfBounds("PSF nonzero off the FPA (c_s has n entries)")
+        return
     if x.size and (x.min() < 0 or y.min() < 0 or
                    x.max() + geom.a - 1 >= geom.gamma or
                    y.max() + geom.alpha - 1 >= geom.xi):
@@ -144,7 +155,7 @@ def merge_psf(geom: Geometry, psf, boundary: str = "reject") -> Taps:
         P.append(P[-1] + len(uniq))
     cat = lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt)
     return Taps(cat(S, np.int64), cat(X, np.int64), cat(Y, np.int64),
-                cat(V, np.float64), np.asarray(P, dtype=np.int64))
+                cat(V, np.float64), np.asarray(P, dtype=np.int64), boundary == "wrap")
 
 
 def index_map(geom: Geometry) -> np.ndarray:
@@ -166,7 +177,8 @@ class BlockH:
     column ``r*a + p`` is the calibration image of wavelength s shifted by
     (p, r), i.e. nonzero ``(x_k, y_k, v_k)`` lands in row
     ``(x_k + p) + gamma*(y_k + r)``. A shifted nonzero off the FPA (possible
-    only under the clip reading) is dropped.
+    only under the clip reading) is dropped; under the wrap reading the row is
+    taken mod n instead (Eq. 7's circulant).
     """
 
     def __init__(self, geom: Geometry, taps: Taps, wavelengths=None):
@@ -183,8 +195,12 @@ class BlockH:
             xs, ys, vs = taps.of(s)
             px = xs[:, None] + Pf[None, :]
             py = ys[:, None] + Rf[None, :]
-            on = (px >= 0) & (px < ga) & (py >= 0) & (py < geom.xi)
-            rows = (px + ga * py)[on]
+            if taps.wrap:
+                on = np.ones(px.shape, dtype=bool)
+                rows = ((px + ga * py) % geom.n).ravel()
+            else:
+                on = (px >= 0) & (px < ga) & (py >= 0) & (py < geom.xi)
+                rows = (px + ga * py)[on]
             cols = np.broadcast_to(col[None, :], on.shape)[on]
             vals = np.broadcast_to(vs[:, None], on.shape)[on]
             self.blocks[s] = sp.csr_matrix((vals, (rows, cols)), shape=(geom.n, geom.ell))
@@ -306,8 +322,12 @@ def forward_at(geom: Geometry, taps: Taps, f: np.ndarray, xs, ys) -> np.ndarray:
     out = np.zeros(xs.size)
     for s in range(geom.w):
         tx, ty, tv = taps.of(s)
-        p = xs[:, None] - tx[None, :]
-        r = ys[:, None] - ty[None, :]
+        if taps.wrap:   # the one offset d = p + gamma r with i = tap + d (mod n)
+            d = (xs[:, None] + geom.gamma * ys[:, None] - tx[None, :] - geom.gamma * ty[None, :]) % geom.n
+            p, r = d % geom.gamma, d // geom.gamma
+        else:
+            p = xs[:, None] - tx[None, :]
+            r = ys[:, None] - ty[None, :]
         ok = (p >= 0) & (p < geom.a) & (r >= 0) & (r < geom.alpha)
         vals = np.where(ok, f[s][np.clip(r, 0, geom.alpha - 1), np.clip(p, 0, geom.a - 1)], 0.0)
         out += vals @ tv
@@ -322,6 +342,9 @@ def adjoint_at(geom: Geometry, taps: Taps, u: np.ndarray, s_idx, ps, rs) -> np.n
     for t, (s, p, r) in enumerate(zip(s_idx, ps, rs)):
         tx, ty, tv = taps.of(int(s))
         x, y = tx + p, ty + r
+        if taps.wrap:
+            out[t] = np.dot(u.ravel()[(x + geom.gamma * y) % geom.n], tv)
+            continue
         on = (x >= 0) & (x < geom.gamma) & (y >= 0) & (y < geom.xi)   # off the FPA: dropped
         out[t] = np.dot(u[y[on], x[on]], tv[on])
     return out
@@ -362,10 +385,14 @@ def _calibration_column(geom: Geometry, taps: Taps, s: int) -> np.ndarray:
     return c
 
 
-def fft_forward(geom: Geometry, psf, f: np.ndarray) -> np.ndarray:
+def fft_forward(geom: Geometry, psf, f: np.ndarray, boundary: str = "reject") -> np.ndarray:
     """Eq. 13: ``g = F^-1 sum_i d_i * (F v_i)`` with ``d_i = F c_i`` and
-    ``v_i = E f_i`` placed by the Sec. 3 index map (real FFT of length n)."""
-    taps = merge_psf(geom, psf)
+    ``v_i = E f_i`` placed by the Sec. 3 index map (real FFT of length n).
+    The transform's product is circular, so this is the wrap reading; under
+    the reject rule the wrap never happens."""
+    if boundary == "clip":
+        raise ValueError("the FFT form has no clip reading")
+    taps = merge_psf(geom, psf, boundary)
     f = np.asarray(f, dtype=np.float64).ravel()
     imap = index_map(geom)
     v = np.zeros(geom.n * geom.w)
@@ -377,10 +404,12 @@ def fft_forward(geom: Geometry, psf, f: np.ndarray) -> np.ndarray:
     return np.fft.irfft(acc, n=geom.n)
 
 
-def fft_adjoint(geom: Geometry, psf, u: np.ndarray) -> np.ndarray:
+def fft_adjoint(geom: Geometry, psf, u: np.ndarray, boundary: str = "reject") -> np.ndarray:
     """Eqs. 14, 17: ``C_i^T u = F^-1(conj(d_i) * F u)``, then the transposed index
     map ``zeta = (I_w kron E)^T z`` gathers voxel values (Sec. 3)."""
-    taps = merge_psf(geom, psf)
+    if boundary == "clip":
+        raise ValueError("the FFT form has no clip reading")
+    taps = merge_psf(geom, psf, boundary)
     U = np.fft.rfft(np.asarray(u, dtype=np.float64).ravel())
     z = np.zeros(geom.n * geom.w)
     for s in range(geom.w):
@@ -421,6 +450,13 @@ def psf_value_grad(geom: Geometry, taps: Taps, f: np.ndarray, gy: np.ndarray) ->
     f = np.asarray(f, dtype=np.float64).reshape(geom.w, geom.alpha, geom.a)
     gy = np.asarray(gy, dtype=np.float64).reshape(geom.xi, geom.gamma)
     out = np.zeros(taps.v.size)
+    if taps.wrap:
+        P, R = np.meshgrid(np.arange(geom.a), np.arange(geom.alpha))   # [alpha][a]
+        flat = gy.ravel()
+        for t in range(taps.v.size):
+            s, x, y = int(taps.s[t]), int(taps.x[t]), int(taps.y[t])
+            out[t] = np.sum(f[s] * flat[(x + P + geom.gamma * (y + R)) % geom.n])
+        return out
     for t in range(taps.v.size):
         s, x, y = int(taps.s[t]), int(taps.x[t]), int(taps.y[t])
         # the part of the shifted field stop on the FPA (all of it unless clipped)
@@ -437,7 +473,7 @@ def poisson_nll(q: np.ndarray, g: np.ndarray) -> float:
 
 
 def with_values(taps: Taps, v: np.ndarray) -> Taps:
-    return Taps(taps.s, taps.x, taps.y, np.asarray(v, dtype=np.float64), taps.ptr)
+    return Taps(taps.s, taps.x, taps.y, np.asarray(v, dtype=np.float64), taps.ptr, taps.wrap)
 
 
 def unrolled_nll(geom: Geometry, taps: Taps, g: np.ndarray, f0: np.ndarray, k: int) -> float:

@@ -464,3 +464,109 @@ def test_clip_em_invariants():
         assert np.all(f_next >= 0)
         assert abs(np.dot(h, f_next) - g[q > 0].sum()) <= 1e-9 * g.sum()
         f = f_next
+
+
+# --- the wrap boundary reading (Eq. 7 taken literally: rows mod n) ---------------
+
+# nonzeros whose shifted copies pass the right edge, the last row, and both
+WRAP_PSF = (np.array([0, 4, 8], np.int32),
+            np.array([7, 2, 8, 0, 5, 5, 6, 1], np.int32),
+            np.array([1, 6, 7, 0, 5, 5, 2, 7], np.int32),
+            np.array([0.5, 1.5, 1.0, 0.25, 0.7, 0.3, 2.0, 0.9], np.float32))
+
+
+def _wrap_images(geom, psf):
+    """The PSF plus, for each nonzero (x, y), its images at (x - gamma, y + 1),
+    (x, y - xi) and (x - gamma, y + 1 - xi), wavelength by wavelength."""
+    ptr, x, y, v = psf
+    P, X, Y, V = [0], [], [], []
+    for s in range(geom.w):
+        lo, hi = int(ptr[s]), int(ptr[s + 1])
+        for dx, dy in ((0, 0), (-geom.gamma, 1), (0, -geom.xi), (-geom.gamma, 1 - geom.xi)):
+            X.append(x[lo:hi] + dx)
+            Y.append(y[lo:hi] + dy)
+            V.append(v[lo:hi])
+        P.append(P[-1] + 4 * (hi - lo))
+    return (np.array(P, np.int32), np.concatenate(X).astype(np.int32),
+            np.concatenate(Y).astype(np.int32), np.concatenate(V).astype(np.float32))
+
+
+def test_wrap_reading_is_the_literal_circulant_of_eq7():
+    """Under the wrap reading H equals the dense C_s E of Eqs. 5-7 (columns of
+    C_s are c_s rolled), for a PSF whose shifted copies pass every edge; the
+    reject rule refuses that PSF, and wrap refuses a nonzero off the FPA."""
+    geom = _geom(*CLIP_GEOM)
+    with pytest.raises(O.OutOfBounds):
+        O.build_H(geom, WRAP_PSF)
+    H = O.build_H(geom, WRAP_PSF, boundary="wrap")
+    np.testing.assert_allclose(H.as_csr().toarray(), O.dense_H(geom, WRAP_PSF), rtol=1e-15, atol=0)
+    ptr, x, y, v = WRAP_PSF
+    with pytest.raises(O.OutOfBounds):
+        O.build_H(geom, (ptr, np.where(np.arange(len(x)) == 3, 9, x).astype(np.int32), y, v),
+                  boundary="wrap")
+    # nothing is lost: h_j is the wavelength's total PSF value for every voxel
+    h = H.h().reshape(geom.w, geom.ell)
+    for s in range(geom.w):
+        assert np.allclose(h[s], float(np.sum(v[ptr[s]:ptr[s + 1]], dtype=np.float64)), rtol=1e-15)
+
+
+def test_wrap_reading_matches_the_fft_form():
+    """The FFT form (Eqs. 13, 17) is circular by construction: it equals the
+    wrap reading's sparse projectors."""
+    geom = _geom(*CLIP_GEOM)
+    H = O.build_H(geom, WRAP_PSF, boundary="wrap")
+    f = synth.random_positive(geom.m, 64).astype(np.float64)
+    u = synth.random_positive(geom.n, 65).astype(np.float64)
+    assert _rel(O.fft_forward(geom, WRAP_PSF, f, boundary="wrap"), H.forward(f)) < 1e-13
+    assert _rel(O.fft_adjoint(geom, WRAP_PSF, u, boundary="wrap"), H.adjoint(u)) < 1e-13
+    with pytest.raises(ValueError):
+        O.fft_forward(geom, WRAP_PSF, f, boundary="clip")
+
+
+def test_wrap_pointwise_evaluators_and_psf_grad():
+    geom = _geom(*CLIP_GEOM)
+    taps = O.merge_psf(geom, WRAP_PSF, "wrap")
+    D = O.dense_H(geom, WRAP_PSF)
+    f = synth.random_positive(geom.m, 66).astype(np.float64)
+    u = synth.random_positive(geom.n, 67).astype(np.float64)
+    xs, ys = np.meshgrid(np.arange(geom.gamma), np.arange(geom.xi))
+    assert _rel(O.forward_at(geom, taps, f, xs.ravel(), ys.ravel()), D @ f) < 1e-14
+    s, r, p = np.unravel_index(np.arange(geom.m), (geom.w, geom.alpha, geom.a))
+    assert _rel(O.adjoint_at(geom, taps, u, s, p, r), D.T @ u) < 1e-14
+    grad = O.psf_value_grad(geom, taps, f, u)
+    for t in range(taps.v.size):
+        ptr = np.zeros(geom.w + 1, np.int32)
+        ptr[int(taps.s[t]) + 1:] = 1
+        Dt = O.dense_H(geom, (ptr, taps.x[t:t + 1], taps.y[t:t + 1], np.ones(1, np.float32)))
+        assert abs(grad[t] - u @ (Dt @ f)) <= 1e-12 * max(1.0, abs(grad[t]))
+
+
+def test_wrap_is_the_clip_reading_of_the_psf_and_its_images():
+    """Each shifted copy (x + p, y + r) of a nonzero on the FPA re-enters at
+    exactly one of (x + p - gamma, y + r + 1), (x + p, y + r - xi) and
+    (x + p - gamma, y + r + 1 - xi) when it leaves, so the wrap reading is the
+    clip reading of the PSF together with those three images."""
+    for dims, psf in ((CLIP_GEOM, WRAP_PSF),
+                      ((3, 4, 3, 7, 6), synth.random_sparse_psf(3, 6, 6, 5, 91, duplicates=2)),
+                      ((5, 2, 2, 6, 9), synth.random_sparse_psf(2, 7, 5, 8, 92))):
+        geom = _geom(*dims)
+        a = O.build_H(geom, psf, boundary="wrap").as_csr().toarray()
+        b = O.build_H(geom, _wrap_images(geom, psf), boundary="clip").as_csr().toarray()
+        np.testing.assert_allclose(a, b, rtol=1e-15, atol=0)
+        np.testing.assert_allclose(a, O.dense_H(geom, psf), rtol=1e-15, atol=0)
+
+
+def test_wrap_em_invariants():
+    """With nothing lost, EM under the wrap reading conserves sum_j h_j f_j
+    (= the sum of g over the support of H f) and keeps f >= 0."""
+    geom = _geom(*CLIP_GEOM)
+    H = O.build_H(geom, WRAP_PSF, boundary="wrap")
+    g = synth.random_positive(geom.n, 68).astype(np.float64) * 50
+    f = np.ones(geom.m)
+    h = H.h()
+    for _ in range(5):
+        q = H.forward(f)
+        f_next = O.em_step(H, g, f)
+        assert np.all(f_next >= 0)
+        assert abs(np.dot(h, f_next) - g[q > 0].sum()) <= 1e-9 * g.sum()
+        f = f_next
