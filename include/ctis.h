@@ -63,8 +63,18 @@ enum { CTIS_F32 = 0, CTIS_BF16 = 1 };
  * wrap a shifted nonzero past the FPA edge into another row; a physical shift
  * loses it. REJECT (default): every shifted nonzero must stay on the FPA, so
  * both readings agree. CLIP: the physical reading: shifted nonzeros off the
- * FPA are dropped (lost light), and h = H^T 1 then varies per voxel. */
-enum { CTIS_BOUNDARY_REJECT = 0, CTIS_BOUNDARY_CLIP = 1 };
+ * FPA are dropped (lost light), and h = H^T 1 then varies per voxel. WRAP:
+ * Eq. 7 taken literally, for comparison: PSF nonzeros must lie on the FPA
+ * (c_s has n entries) and a shifted copy lands in row
+ * (x + p + gamma (y + r)) mod n, so one past the right edge re-enters at the
+ * left of the next FPA row and one past the last row at the top. The plan
+ * stores it as the CLIP reading of the PSF together with each nonzero's
+ * images at (x - gamma, y + 1), (x, y - xi) and (x - gamma, y + 1 - xi)
+ * (those whose shifted copies can meet the FPA): each shifted copy re-enters
+ * at exactly one of them. ctis_plan_export_taps then lists the images too,
+ * and ctis_plan_set_values and ctis_psf_grad return CTIS_ERR_UNSUPPORTED
+ * (an image must keep its original's value). */
+enum { CTIS_BOUNDARY_REJECT = 0, CTIS_BOUNDARY_CLIP = 1, CTIS_BOUNDARY_WRAP = 2 };
 
 /* ctis_reconstruct flags. Without an INIT flag, f_dev holds the initial guess. */
 enum {
@@ -110,8 +120,9 @@ typedef struct {
                               linearly from 1 + skew to 1 - skew over the block
                               indices (the SM's warp schedulers favour the CTAs
                               resident first); 0 = equal speeds                 */
-    int boundary;          /* CTIS_BOUNDARY_REJECT (0) or CTIS_BOUNDARY_CLIP;
-                              CLIP accepts PSF coordinates in [-2^24, 2^24)     */
+    int boundary;          /* CTIS_BOUNDARY_REJECT (0), _CLIP or _WRAP; CLIP
+                              accepts PSF coordinates in [-2^24, 2^24), WRAP
+                              those on the FPA                                  */
     int reserved[3];       /* must be 0                                          */
 } ctis_plan_options;
 
@@ -189,7 +200,8 @@ int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
  * bfloat16 widened to float32), plus h[w] (float32 as used by the update;
  * under CTIS_BOUNDARY_CLIP the per-wavelength sum of the values, which the
  * voxels whose light partly leaves the FPA do not reach: their h is
- * H^T 1 per voxel). Arrays must hold info.nnz entries (h: w entries). Any
+ * H^T 1 per voxel; under CTIS_BOUNDARY_WRAP the sum of the nonzeros on the
+ * FPA, which every voxel reaches). Arrays must hold info.nnz entries (h: w entries). Any
  * pointer may be NULL. */
 int ctis_plan_export_taps(const ctis_plan* plan, int32_t* s, int32_t* x, int32_t* y,
                           float* val, float* h);
@@ -277,7 +289,8 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
  * indexed in ctis_plan_export_taps order (merged, sorted by (s, y, x)). */
 
 /* Replace the plan's tap values (host float32[nnz], finite and >= 0),
- * rounded to the plan's dtype, and recompute h = H^T 1 (Eq. 2). Waits for all
+ * rounded to the plan's dtype, and recompute h = H^T 1 (Eq. 2); not under
+ * CTIS_BOUNDARY_WRAP (CTIS_ERR_UNSUPPORTED). Waits for all
  * device work first (queued kernels may read the old tables); the plan's
  * cached reconstruction graph stays valid and uses the new values. */
 int ctis_plan_set_values(ctis_plan* plan, const float* vals);
@@ -285,7 +298,8 @@ int ctis_plan_set_values(ctis_plan* plan, const float* vals);
 /* dval_dev[t] = sum_{p,r} f_s(p, r) * r(x_t + p, y_t + r): the gradient of
  * <r, H f> with respect to v_t (s = tap t's wavelength). f_dev: m elements of
  * the plan's dtype; r_dev: n float32; dval_dev: nnz float32. Sums are float32
- * in a fixed order (reproducible). */
+ * in a fixed order (reproducible). Not under CTIS_BOUNDARY_WRAP
+ * (CTIS_ERR_UNSUPPORTED). */
 int ctis_psf_grad(const ctis_plan* plan, const void* f_dev, const float* r_dev,
                   float* dval_dev, void* stream);
 
@@ -330,8 +344,10 @@ int ctis_plan_set_schedule(ctis_plan* plan, int forward, int tasks_per_item, int
  * (Eqs. 11, 13) and H^T u = E^T stack_s F^-1 (conj(d_s) (.) F u) (Eqs. 14,
  * 17), d_s = F c_s, F the length-n real-to-complex transform (cuFFT, float32).
  * Built on the first call (w x (n/2+1) complex spectra and as many work
- * vectors, ~3 w n float32 of device memory). float32 plans with
- * CTIS_BOUNDARY_REJECT only (CTIS_ERR_UNSUPPORTED otherwise). Calls on one
+ * vectors, ~4 w n float32 of device memory). float32 plans with
+ * CTIS_BOUNDARY_REJECT or _WRAP (the transform's product is circular: it is
+ * the WRAP reading, which REJECT's rule makes equal to the others);
+ * CTIS_ERR_UNSUPPORTED otherwise. Calls on one
  * plan share its workspace: issue them on one stream.
  *   ctis_fft_forward:     hf_dev (n) = H f_dev (m), dense layouts as ctis_forward.
  *   ctis_fft_adjoint:     out_dev (m) = H^T r_dev (n).

@@ -15,8 +15,9 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctis.so")
 
 CTIS_F32, CTIS_BF16 = 0, 1
-CTIS_BOUNDARY_REJECT, CTIS_BOUNDARY_CLIP = 0, 1
-_BOUNDARY = {"reject": CTIS_BOUNDARY_REJECT, "clip": CTIS_BOUNDARY_CLIP}
+CTIS_BOUNDARY_REJECT, CTIS_BOUNDARY_CLIP, CTIS_BOUNDARY_WRAP = 0, 1, 2
+_BOUNDARY = {"reject": CTIS_BOUNDARY_REJECT, "clip": CTIS_BOUNDARY_CLIP,
+             "wrap": CTIS_BOUNDARY_WRAP}
 CTIS_INIT_ONES, CTIS_INIT_HTG = 1, 2
 NSTATS = 4
 STAT_NAMES = ("flux_hf", "flux_g", "loglik", "resid2")

@@ -191,6 +191,8 @@ struct ctis_plan {
     int forced_skew_pm = 0;           // CTA priority skew of the model's schedule
     int host_ctas = 0;                // > 0: host-only tables for this many CTAs (no device)
     bool clip = false;                // CTIS_BOUNDARY_CLIP: shifted nonzeros off the FPA dropped
+    bool wrap = false;                // CTIS_BOUNDARY_WRAP: stored as the clip reading of the
+                                      // PSF and its wrapped images (clip is set too)
     float* d_hvox = nullptr;          // clip: h = H^T 1 per voxel [w][alpha][a]
     FftForm* fft = nullptr;           // the paper's FFT form, built on first use
     float* d_fft_u = nullptr;         // its EM ratio [n]
@@ -594,7 +596,11 @@ void layout_warps(ProjTables& T) {
 // values, rounded once to float32.
 void compute_h(ctis_plan* P) {
     std::vector<double> hs(P->w, 0.0);
-    for (size_t k = 0; k < P->tap_v.size(); ++k) hs[P->tap_s[k]] += static_cast<double>(P->tap_v[k]);
+    for (size_t k = 0; k < P->tap_v.size(); ++k) {
+        // under the wrap reading the images off the FPA repeat an original
+        if (P->wrap && (P->tap_x[k] < 0 || P->tap_y[k] < 0)) continue;
+        hs[P->tap_s[k]] += static_cast<double>(P->tap_v[k]);
+    }
     P->h.assign(P->w, 0.f);
     for (int s = 0; s < P->w; ++s) P->h[s] = static_cast<float>(hs[s]);
 }
@@ -655,10 +661,12 @@ int write_values(ctis_plan* P, bool allocate) {
     return CTIS_OK;
 }
 
-// Host-only validation of the PSF values and of the on-FPA rule (Sec. 2:
-// every shifted copy of every nonzero must stay on the FPA).
+// Host-only validation of the PSF values and of the boundary rule: under
+// REJECT every shifted copy of every nonzero must stay on the FPA (Sec. 2),
+// under WRAP every nonzero must lie on it (an entry of c_s, Eq. 7).
 int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
-                 const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, bool clip) {
+                 const int32_t* psf_x, const int32_t* psf_y, const float* psf_val, int boundary) {
+    const bool clip = boundary == CTIS_BOUNDARY_CLIP;
     const int64_t nnz_in = psf_ptr[w];
     for (int64_t k = 0; k < nnz_in; ++k) {
         const float v = psf_val[k];
@@ -671,6 +679,13 @@ int validate_psf(int a, int al, int w, int ga, int xi, const int32_t* psf_ptr,
                 y >= (int64_t{1} << 24))
                 return fail(CTIS_ERR_INVALID_ARG, "PSF nonzero %lld at (%lld, %lld) out of range",
                             (long long)k, (long long)x, (long long)y);
+            continue;
+        }
+        if (boundary == CTIS_BOUNDARY_WRAP) {
+            if (x < 0 || y < 0 || x >= ga || y >= xi)
+                return fail(CTIS_ERR_OUT_OF_BOUNDS,
+                            "PSF nonzero %lld at (%lld, %lld) is off the %dx%d FPA", (long long)k,
+                            (long long)x, (long long)y, ga, xi);
             continue;
         }
         if (x < 0 || y < 0 || x + a - 1 >= ga || y + al - 1 >= xi)
@@ -1319,8 +1334,10 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
 // F frames of one plan's geometry run as F more copies of its work lists, so
 // one launch per projector covers them all: every warp keeps its item list
 // and runs it once per frame. Frame f's datacube planes are planes f*w + s of
-// the copies, its FPA rows are rows f*xi + y of a tall FPA, and its tiles are
-// tiles f*T + t, each frame with its own partial-sum slots and statistics.
+// the copies, its FPA image in FPA copy q is plane q*F + f of the adjoint's
+// window map (so a window past the FPA's first or last row reads zeros, not
+// a neighbouring frame), and its tiles are tiles f*T + t, each frame with its
+// own partial-sum slots and statistics.
 struct BatchTables {
     WorkItem* d_witems = nullptr;
     TaskDesc* d_tasks = nullptr;
@@ -1334,7 +1351,7 @@ struct BatchState {
     int F = 0;
     BatchTables fwd, adj;
     void* d_fwork = nullptr;       // datacube copies, planes f*w + s
-    float* d_u = nullptr;          // FPA copies, rows f*xi + y
+    float* d_u = nullptr;          // FPA copies: copy q of frame f at (q*F + f) * xi rows
     float* d_scratch = nullptr;
     int* d_tickets = nullptr;
     int* d_counters = nullptr;     // [3] error flag, [8 + f] frame f's reduction ticket
@@ -1378,7 +1395,7 @@ void free_batch(BatchState* B) {
 // The work lists of F frames, scheduled as one problem. The joint tiles are
 // frame f's tiles f*T + t (so tickets and tile statistics stay frame-major),
 // their tasks the plan's with frame f's planes (forward: datacube planes
-// f*w + s of the copies) or rows (adjoint: rows f*xi + y of the tall FPA),
+// f*w + s of the copies; adjoint: FPA planes q*F + f of copy q),
 // and the joint items are the plan's items (same tiles, chunks and task
 // ranges) of every frame, assigned longest first over the CTAs with the
 // plan's priority skew and CTA-to-SM map. Each tile is therefore summed
@@ -1409,8 +1426,8 @@ int replicate(ctis_plan* P, const ProjTables& T, bool forward, int F, BatchTable
                 if (forward) {   // copies' plane q*w + s -> q*(F*w) + f*w + s
                     const int q = d.plane / P->w, sw = d.plane % P->w;
                     d.plane = q * (F * P->w) + f * P->w + sw;
-                } else {         // window rows of frame f on the tall FPA
-                    d.wy += f * P->xi;
+                } else {         // copy q's plane -> plane q*F + f of the frames' FPAs
+                    d.plane = d.plane * F + f;
                 }
                 J.tile_tasks.push_back(d);
             }
@@ -1538,8 +1555,9 @@ int batch_forward(const ctis_plan* P, const BatchState* B, GatherParams p, cudaS
 
 int batch_adjoint(const ctis_plan* P, const BatchState* B, GatherParams p, cudaStream_t st) {
     CUtensorMap win;
-    int rc = make_map(&win, B->d_u, kDtypeF32, P->gamma + P->u_copies - 1, P->xi * B->F,
-                      P->u_copies, P->g_pitch, B->u_copy_stride,
+    // copy q of frame f starts at (q*F + f) * xi * g_pitch (u_copy_stride = F * xi * g_pitch)
+    int rc = make_map(&win, B->d_u, kDtypeF32, P->gamma + P->u_copies - 1, P->xi,
+                      P->u_copies * B->F, P->g_pitch, static_cast<int64_t>(P->g_pitch) * P->xi,
                       gather_box_w(false, P->K, P->dtype), gather_window_rows(false, P->K, P->dtype));
     if (rc) return rc;
     CTIS_CUDA(gather_launch(false, P->K, P->dtype, win, p, st));
@@ -1741,8 +1759,10 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
             return fail(CTIS_ERR_INVALID_ARG, "tasks_per_item and item_overhead_q are exclusive");
         if (opt->cta_skew_permille < 0 || opt->cta_skew_permille > 900)
             return fail(CTIS_ERR_INVALID_ARG, "cta_skew_permille out of range [0, 900]");
-        if (opt->boundary != CTIS_BOUNDARY_REJECT && opt->boundary != CTIS_BOUNDARY_CLIP)
-            return fail(CTIS_ERR_INVALID_ARG, "boundary must be CTIS_BOUNDARY_REJECT or _CLIP");
+        if (opt->boundary != CTIS_BOUNDARY_REJECT && opt->boundary != CTIS_BOUNDARY_CLIP &&
+            opt->boundary != CTIS_BOUNDARY_WRAP)
+            return fail(CTIS_ERR_INVALID_ARG,
+                        "boundary must be CTIS_BOUNDARY_REJECT, _CLIP or _WRAP");
         boundary = opt->boundary;
         forced_per_item = opt->tasks_per_item;
         forced_split_q = opt->item_overhead_q;
@@ -1766,11 +1786,12 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
             return fail(CTIS_ERR_INVALID_ARG, "psf_ptr must be non-decreasing (at %d)", s);
     if (psf_ptr[w] > 0 && (!psf_x || !psf_y || !psf_val))
         return fail(CTIS_ERR_INVALID_ARG, "PSF arrays are NULL");
-    if ((int64_t)psf_ptr[w] * 8 > (int64_t)1 << 31)
+    // (the wrap reading stores up to four entries per nonzero)
+    if ((int64_t)psf_ptr[w] * (boundary == CTIS_BOUNDARY_WRAP ? 32 : 8) > (int64_t)1 << 31)
         return fail(CTIS_ERR_UNSUPPORTED, "too many PSF nonzeros");
     {
         const int rc = validate_psf(a, alpha, w, gamma, xi, psf_ptr, psf_x, psf_y, psf_val,
-                                    boundary == CTIS_BOUNDARY_CLIP);
+                                    boundary);
         if (rc) return rc;
     }
 
@@ -1790,12 +1811,52 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     P->forced_per_item = forced_per_item;
     P->forced_split_q = forced_split_q;
     P->forced_skew_pm = forced_skew_pm;
-    P->clip = boundary == CTIS_BOUNDARY_CLIP;
+    P->clip = boundary != CTIS_BOUNDARY_REJECT;
+    P->wrap = boundary == CTIS_BOUNDARY_WRAP;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
     *out = P;
     return CTIS_OK;
+}
+
+// The PSF the plan stores: the caller's, or under the wrap reading the
+// caller's together with, for each nonzero (x, y), its images at
+// (x - gamma, y + 1), (x, y - xi) and (x - gamma, y + 1 - xi) whose shifted
+// copies can meet the FPA. A shifted copy (x + p, y + r), p < a <= gamma,
+// r < alpha <= xi, of a nonzero on the FPA has row index
+// (x + p + gamma (y + r)) mod n (Eq. 7); when it leaves the FPA it re-enters
+// at exactly one image's shifted copy, so the clip reading of this PSF is the
+// wrap reading of the caller's.
+struct StoredPsf {
+    std::vector<int32_t> ptr, x, y;
+    std::vector<float> v;
+};
+
+StoredPsf wrap_images(const ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x,
+                      const int32_t* psf_y, const float* psf_val) {
+    const int ga = P->gamma, xi = P->xi;
+    StoredPsf out;
+    out.ptr.assign(1, 0);
+    for (int s = 0; s < P->w; ++s) {
+        for (int64_t k = psf_ptr[s]; k < psf_ptr[s + 1]; ++k) {
+            const int x = psf_x[k], y = psf_y[k];
+            const bool past_x = x + P->a - 1 >= ga;       // some copy passes the right edge
+            const bool past_y = y + P->alpha - 1 >= xi;   // some copy passes the last row
+            auto add = [&](int xx, int yy) {
+                out.x.push_back(xx);
+                out.y.push_back(yy);
+                out.v.push_back(psf_val[k]);
+            };
+            add(x, y);
+            if (past_x && y + 1 < xi) add(x - ga, y + 1);
+            if (past_y) add(x, y - xi);
+            // copies past the right edge of the last row re-enter at the top
+            if (past_x && y + P->alpha >= xi) add(x - ga, y + 1 - xi);
+        }
+        out.ptr.push_back(static_cast<int32_t>(out.x.size()));
+    }
+    return out;
 }
 
 }  // namespace
@@ -1816,6 +1877,14 @@ int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int
     if (e != cudaSuccess) {
         delete P;
         return cuda_fail(e, "no usable CUDA device");
+    }
+    StoredPsf images;
+    if (P->wrap) {
+        images = wrap_images(P, psf_ptr, psf_x, psf_y, psf_val);
+        psf_ptr = images.ptr.data();
+        psf_x = images.x.data();
+        psf_y = images.y.data();
+        psf_val = images.v.data();
     }
     int rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
     if (!rc) rc = place_by_probe(P);
@@ -1852,6 +1921,14 @@ int ctis_tables_inspect(int a, int alpha, int w, int gamma, int xi, const int32_
     P->host_ctas = n_ctas;
     if (block_sm) {
         (forward ? P->fwd : P->adj).block_sm.assign(block_sm, block_sm + n_ctas);
+    }
+    StoredPsf images;
+    if (P->wrap) {
+        images = wrap_images(P, psf_ptr, psf_x, psf_y, psf_val);
+        psf_ptr = images.ptr.data();
+        psf_x = images.x.data();
+        psf_y = images.y.data();
+        psf_val = images.v.data();
     }
     rc = build(P, psf_ptr, psf_x, psf_y, psf_val);
     if (rc) {
@@ -1939,7 +2016,8 @@ int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
     info->adj_split_q = P->adj.split_q;
     info->fwd_skew_pm = P->fwd.skew_pm;
     info->adj_skew_pm = P->adj.skew_pm;
-    info->boundary = P->clip ? CTIS_BOUNDARY_CLIP : CTIS_BOUNDARY_REJECT;
+    info->boundary = P->wrap ? CTIS_BOUNDARY_WRAP
+                             : (P->clip ? CTIS_BOUNDARY_CLIP : CTIS_BOUNDARY_REJECT);
     return CTIS_OK;
 }
 
@@ -2157,18 +2235,21 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
 namespace {
 
 // Builds the plan's FFT form on first use: the calibration images c_s of the
-// merged nonzeros (as stored), d_s = F c_s, h per wavelength.
+// merged nonzeros on the FPA (under the wrap reading the stored images off
+// it repeat those), d_s = F c_s, h per wavelength.
 int ensure_fft(ctis_plan* P) {
     if (P->fft) return CTIS_OK;
-    if (P->clip)
+    if (P->clip && !P->wrap)
         return fail(CTIS_ERR_UNSUPPORTED,
-                    "the FFT form needs CTIS_BOUNDARY_REJECT (Eq. 7's circulant wraps)");
+                    "the FFT form needs CTIS_BOUNDARY_REJECT or _WRAP (Eq. 7's circulant wraps)");
     if (P->dtype != kDtypeF32) return fail(CTIS_ERR_UNSUPPORTED, "the FFT form needs a float32 plan");
     const int64_t n = P->n;
     std::vector<float> calib(static_cast<size_t>(n) * P->w, 0.f);
-    for (size_t k = 0; k < P->tap_v.size(); ++k)
+    for (size_t k = 0; k < P->tap_v.size(); ++k) {
+        if (P->tap_x[k] < 0 || P->tap_y[k] < 0) continue;
         calib[static_cast<size_t>(P->tap_s[k]) * n + P->tap_x[k] +
               static_cast<int64_t>(P->gamma) * P->tap_y[k]] += P->tap_v[k];
+    }
     int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_fft_u), sizeof(float) * n);
     if (rc) return rc;
     CTIS_CUDA(fft_form_create(&P->fft, P->a, P->alpha, P->w, P->gamma, P->xi, calib.data(),
@@ -2217,6 +2298,9 @@ int ctis_fft_reconstruct(ctis_plan* P, const float* g_dev, float* f_dev, int k, 
 int ctis_plan_set_values(ctis_plan* P, const float* vals) {
     int rc = check_plan(P);
     if (rc) return rc;
+    if (P->wrap)
+        return fail(CTIS_ERR_UNSUPPORTED,
+                    "new values under CTIS_BOUNDARY_WRAP (each image keeps its original's value)");
     const size_t nnz = P->tap_v.size();
     if (!vals && nnz) return fail(CTIS_ERR_INVALID_ARG, "vals is NULL");
     for (size_t k = 0; k < nnz; ++k)
@@ -2240,6 +2324,9 @@ int ctis_psf_grad(const ctis_plan* P, const void* f_dev, const float* r_dev, flo
     int rc = check_plan(P);
     if (rc) return rc;
     if (!f_dev || !r_dev || !dval_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    if (P->wrap)
+        return fail(CTIS_ERR_UNSUPPORTED,
+                    "the PSF-value gradient under CTIS_BOUNDARY_WRAP (images share values)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = scatter_u(P, r_dev, st);
     if (rc) return rc;

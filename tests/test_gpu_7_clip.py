@@ -150,3 +150,32 @@ def test_unrolled_gradient_needs_the_reject_boundary():
         g = torch.ones((wl.xi, wl.gamma), device="cuda")
         with pytest.raises(CtisError):
             plan.unrolled_nll_grad(g, 2)
+
+
+def test_batched_frames_read_zeros_past_their_fpa_edges():
+    """In a batch, an adjoint window past the FPA's first or last row reads
+    zeros, not the neighbouring frame's image: a PSF spilling over all four
+    FPA edges, frames with light in their first and last rows, each frame
+    equal to its single-frame reconstruction and to the oracle."""
+    wl = RAGGED.with_(pitch=20.0)
+    geom = geometry(wl)
+    psf = synth.make_psf(wl)
+    ptr, x, y, v = psf
+    assert y.min() < 0 and y.max() + wl.alpha - 1 >= wl.xi
+    assert x.min() < 0 and x.max() + wl.a - 1 >= wl.gamma
+    H = O.build_H(geom, psf, boundary="clip")
+    with _plan(wl, psf) as plan:
+        gs, refs = [], []
+        for i in range(3):
+            g, _ = synth.make_measurement(H.forward(synth.make_scene(wl, 400 + i).ravel()),
+                                          wl.peak, 400 + i)
+            img = g.reshape(wl.xi, wl.gamma)
+            assert img[0].sum() > 0 and img[-1].sum() > 0
+            gs.append(torch.from_numpy(img).cuda())
+            refs.append(O.mlem(H, g, 4)[0])
+        fs, _ = reconstruct_batched([plan], [0] * 3, gs, 4)
+        for i in range(3):
+            single, _ = plan.reconstruct(gs[i], k=4, init="ones")
+            assert torch.equal(fs[i], single), i
+            assert floored_rel(fs[i].cpu().numpy().ravel(), refs[i]) <= 4e-5, i
+        plan.check()

@@ -224,3 +224,59 @@ def test_inspect_rejects_bad_arguments():
     with pytest.raises(CtisError):
         tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 4, tasks_per_item=16,
                        item_overhead_q=4)
+
+
+def _to_edges(wl):
+    """The workload's PSF moved so that its last nonzeros sit in the FPA's last
+    column and row: every nonzero stays on the FPA, many shifted copies pass
+    the right edge, the last row, or both."""
+    ptr, x, y, v = synth.make_psf(wl)
+    return (ptr, (x + wl.gamma - 1 - x.max()).astype(np.int32),
+            (y + wl.xi - 1 - y.max()).astype(np.int32), v)
+
+
+def _images_meeting_the_fpa(wl, psf):
+    """Each nonzero (x, y) plus its images (x - gamma, y + 1), (x, y - xi),
+    (x - gamma, y + 1 - xi) whose footprint [X, X + a) x [Y, Y + alpha)
+    meets the FPA, wavelength by wavelength."""
+    ptr, x, y, v = psf
+    P, X, Y, V = [0], [], [], []
+    for s in range(wl.w):
+        for k in range(int(ptr[s]), int(ptr[s + 1])):
+            for dx, dy in ((0, 0), (-wl.gamma, 1), (0, -wl.xi), (-wl.gamma, 1 - wl.xi)):
+                xx, yy = int(x[k]) + dx, int(y[k]) + dy
+                if xx + wl.a > 0 and yy + wl.alpha > 0 and xx < wl.gamma and yy < wl.xi:
+                    X.append(xx)
+                    Y.append(yy)
+                    V.append(v[k])
+        P.append(len(X))
+    return (np.array(P, np.int32), np.array(X, np.int32), np.array(Y, np.int32),
+            np.array(V, np.float32))
+
+
+@pytest.mark.parametrize("wl", [synth.TINY, RAGGED, K5, synth.MODEL_A], ids=lambda w: w.name)
+@pytest.mark.parametrize("forward", [True, False], ids=["fwd", "adj"])
+def test_wrap_tables_are_the_clip_tables_of_the_images(wl, forward):
+    """The wrap boundary (Eq. 7 literally) is stored as the clip reading of
+    the PSF and its wrapped images: the work lists and schedules are those of
+    a clip plan given that PSF."""
+    psf = _to_edges(wl)
+    tw = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, forward, 12, boundary="wrap")
+    tc = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, _images_meeting_the_fpa(wl, psf),
+                        forward, 12, boundary="clip")
+    assert tw["clusters"] > _inspect(wl, forward, 12, (0, 0))["clusters"]   # images were added
+    for key, val in tc.items():
+        assert np.array_equal(np.asarray(tw[key]), np.asarray(val)), key
+    _check_schedule(tw)
+
+
+def test_wrap_needs_every_nonzero_on_the_fpa():
+    wl = RAGGED
+    ptr, x, y, v = _to_edges(wl)
+    tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, (ptr, x, y, v), True, 8, boundary="wrap")
+    for bad in ((x + 1, y), (x, y + 1), (x - x.min() - 1, y)):
+        with pytest.raises(CtisError):
+            tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, (ptr, *bad, v), True, 8,
+                           boundary="wrap")
+    with pytest.raises(CtisError):   # and the reject rule refuses the copies past the edges
+        tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, (ptr, x, y, v), True, 8)
