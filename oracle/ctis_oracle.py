@@ -310,6 +310,73 @@ def em_step(H: BlockH, g: np.ndarray, f: np.ndarray) -> np.ndarray:
     return em_update(f, H.adjoint(ratio(g64, q)), H.h())
 
 
+# --- other solvers on the same projector pair (Sec. 2 names ART and MART) -------
+#
+# The paper lists ART and MART among the usual CTIS solvers and calls its
+# projector scheme solver agnostic, without defining them. The oracle takes
+# their simultaneous (whole-image) forms from the literature the paper cites
+# for them: SART (Andersen and Kak's simultaneous algebraic reconstruction
+# technique) and SMART (Byrne's simultaneous multiplicative ART). Both use
+# the row sums ``r = H 1`` and column sums ``h = H^T 1`` and a relaxation
+# ``lam``. Readings: a pixel with ``r_i = 0`` (no footprint) adds nothing;
+# under SMART a pixel with ``g_i = 0`` or ``(H f)_i = 0`` has no logarithm
+# and adds nothing; a voxel with ``h_j = 0`` (seen by no pixel) keeps its
+# value; SART's iterate is clipped at 0 after every update (f stays a
+# radiance).
+
+def row_sums(H: BlockH) -> np.ndarray:
+    """``r_i = sum_j H_ij``."""
+    return H.forward(np.ones(H.geom.m))
+
+
+def sart_step(H: BlockH, g: np.ndarray, f: np.ndarray, lam: float = 1.0) -> np.ndarray:
+    """``f + lam * (H^T ((g - H f) / r)) / h``, then clipped at 0."""
+    g = np.asarray(g, dtype=np.float64).ravel()
+    f = np.asarray(f, dtype=np.float64).ravel()
+    r, h = row_sums(H), H.h()
+    q = H.forward(f)
+    u = np.zeros_like(q)
+    on = r > 0
+    u[on] = (g[on] - q[on]) / r[on]
+    z = H.adjoint(u)
+    step = np.zeros_like(f)
+    seen = h > 0
+    step[seen] = z[seen] / h[seen]
+    return np.maximum(f + lam * step, 0.0)
+
+
+def smart_step(H: BlockH, g: np.ndarray, f: np.ndarray, lam: float = 1.0) -> np.ndarray:
+    """``f * exp(lam * (H^T log(g / H f)) / h)``."""
+    g = np.asarray(g, dtype=np.float64).ravel()
+    f = np.asarray(f, dtype=np.float64).ravel()
+    h = H.h()
+    q = H.forward(f)
+    u = np.zeros_like(q)
+    on = (g > 0) & (q > 0)
+    u[on] = np.log(g[on] / q[on])
+    z = H.adjoint(u)
+    step = np.zeros_like(f)
+    seen = h > 0
+    step[seen] = z[seen] / h[seen]
+    return f * np.exp(lam * step)
+
+
+def solve(H: BlockH, g: np.ndarray, k: int, solver: str = "em", lam: float = 1.0,
+          f0: np.ndarray | None = None):
+    """k updates of ``solver`` ('em', 'sart' or 'smart') from ``f0`` or ones;
+    returns ``(f, history)`` with :func:`stats` of ``H f^(t)``, t = 0..k."""
+    step = {"em": lambda f: em_step(H, g, f), "sart": lambda f: sart_step(H, g, f, lam),
+            "smart": lambda f: smart_step(H, g, f, lam)}[solver]
+    g64 = np.asarray(g, dtype=np.float64).ravel()
+    f = np.ones(H.geom.m) if f0 is None else np.asarray(f0, dtype=np.float64).ravel().copy()
+    history = []
+    for _ in range(k):
+        history.append(stats(H.forward(f), g64))
+        f = step(f)
+    history.append(stats(H.forward(f), g64))
+    return f, history
+
+
 # --- pointwise evaluation for full-size parity on sampled outputs -------------
 
 def forward_at(geom: Geometry, taps: Taps, f: np.ndarray, xs, ys) -> np.ndarray:
