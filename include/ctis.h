@@ -230,6 +230,26 @@ int ctis_adjoint(const ctis_plan* plan, const float* r_dev, float* out_dev, void
 int ctis_reconstruct(const ctis_plan* plan, const float* g_dev, void* f_dev, int k,
                      int flags, double* stats_dev, void* stream);
 
+/* Other solvers on the same projector pair (Sec. 2 lists ART and MART among
+ * the usual CTIS solvers and the scheme is solver agnostic; their
+ * simultaneous forms): k updates of `solver`, with relaxation `relax` in
+ * (0, 2] (ignored by EM), fused into the same two launches per iteration:
+ *   CTIS_SOLVER_EM:    exactly ctis_reconstruct.
+ *   CTIS_SOLVER_SART:  u = (g - H f) / r with r = H 1 (0 where r = 0), then
+ *                      f <- max(f + relax * (H^T u) / h, 0) (simultaneous ART,
+ *                      Andersen and Kak).
+ *   CTIS_SOLVER_SMART: u = log(g / H f) where g > 0 and H f > 0 (0 elsewhere),
+ *                      then f <- f * exp(relax * (H^T u) / h) (simultaneous
+ *                      MART, Byrne).
+ * Voxels with h = 0 keep their value under SART and SMART. Arguments,
+ * statistics and graph caching as ctis_reconstruct. SART builds r on its
+ * first call (a forward projection of ones, synchronous; again after
+ * ctis_plan_set_values), so that call must not be made while the stream is
+ * being captured (CTIS_ERR_INVALID_ARG). */
+enum { CTIS_SOLVER_EM = 0, CTIS_SOLVER_SART = 1, CTIS_SOLVER_SMART = 2 };
+int ctis_reconstruct_solver(const ctis_plan* plan, const float* g_dev, void* f_dev, int k,
+                            int flags, int solver, float relax, double* stats_dev, void* stream);
+
 /* Kernel timing. When enabled, ctis_reconstruct records a CUDA event pair
  * (as event-record nodes of its cached graph) around every projector launch.
  * ctis_plan_kernel_times waits for those events and reports, for the most

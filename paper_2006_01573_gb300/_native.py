@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctis.so"
 
 CTIS_F32, CTIS_BF16 = 0, 1
 CTIS_BOUNDARY_REJECT, CTIS_BOUNDARY_CLIP, CTIS_BOUNDARY_WRAP = 0, 1, 2
+CTIS_SOLVER_EM, CTIS_SOLVER_SART, CTIS_SOLVER_SMART = 0, 1, 2
+_SOLVER = {"em": CTIS_SOLVER_EM, "sart": CTIS_SOLVER_SART, "smart": CTIS_SOLVER_SMART}
 _BOUNDARY = {"reject": CTIS_BOUNDARY_REJECT, "clip": CTIS_BOUNDARY_CLIP,
              "wrap": CTIS_BOUNDARY_WRAP}
 CTIS_INIT_ONES, CTIS_INIT_HTG = 1, 2
@@ -31,7 +33,7 @@ EXPORTED = (
     "ctis_plan_set_profiling", "ctis_plan_kernel_times", "ctis_forward_static_scratch",
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
-    "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct",
+    "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct", "ctis_reconstruct_solver",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -86,6 +88,7 @@ def load(path: str = LIB_PATH):
         "ctis_forward": (I, [P, VP, VP, VP]),
         "ctis_adjoint": (I, [P, VP, VP, VP]),
         "ctis_reconstruct": (I, [P, VP, VP, I, I, VP, VP]),
+        "ctis_reconstruct_solver": (I, [P, VP, VP, I, I, I, ctypes.c_float, VP, VP]),
         "ctis_plan_check": (I, [P, VP]),
         "ctis_forward_static_scratch": (I, [P, VP, VP, VP]),
         "ctis_plan_set_profiling": (I, [P, I]),
@@ -288,11 +291,13 @@ class Plan:
         return out
 
     def reconstruct(self, g, k: int, f=None, init: str | None = "ones", stats=False,
-                    stream=None):
-        """k EM updates (Eq. 2). Returns ``(f, stats)``. ``stats`` may be False,
-        True (allocate) or a float64 CUDA tensor of ``(k+1, 4)`` to fill: rows
-        0..k-1 describe ``H f^(t+1)`` of each iteration, row k the returned f.
-        Reusing the same f, g and stats tensors replays the plan's cached graph."""
+                    stream=None, solver: str = "em", relax: float = 1.0):
+        """k EM updates (Eq. 2), or of ``solver`` 'sart' / 'smart' with
+        relaxation ``relax`` (ctis_reconstruct_solver). Returns ``(f, stats)``.
+        ``stats`` may be False, True (allocate) or a float64 CUDA tensor of
+        ``(k+1, 4)`` to fill: rows 0..k-1 describe ``H f^(t+1)`` of each
+        iteration, row k the returned f. Reusing the same f, g and stats
+        tensors replays the plan's cached graph."""
         import torch
         self._check_fpa(g)
         if f is None:
@@ -309,10 +314,10 @@ class Plan:
                 raise ValueError("stats must be a contiguous CUDA float64 tensor of (k+1)*4")
         elif stats:
             st = torch.empty((k + 1, NSTATS), device=g.device, dtype=torch.float64)
-        _check(load().ctis_reconstruct(self._h, ctypes.c_void_p(g.data_ptr()),
-                                       ctypes.c_void_p(f.data_ptr()), k, flags,
-                                       ctypes.c_void_p(st.data_ptr() if st is not None else 0),
-                                       _stream(stream)))
+        _check(load().ctis_reconstruct_solver(
+            self._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(f.data_ptr()), k, flags,
+            _SOLVER[solver], float(relax),
+            ctypes.c_void_p(st.data_ptr() if st is not None else 0), _stream(stream)))
         return f, st
 
     def index_map(self, stream=None):

@@ -609,6 +609,19 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
                 // d/dq (q - g log q) = 1 - g / q on the support of q
                 if (p.ratio_one_minus) u[c] = val > 0.f ? 1.f - u[c] : 0.f;
             }
+            if (p.solver == kSolverSmart) {   // uniform; log(g / q) where both are > 0
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    u[c] = (gv[c] > 0.f && v[o][c] > 0.f) ? __logf(u[c]) : 0.f;
+            } else if (p.solver == kSolverSart) {   // (g - q) / r where r = (H 1) > 0
+                const float* rp = p.row_sum + (long long)(row_ok ? y : 0) * p.out_w + it.x0 + col0;
+                float rs[C];
+                load_row<float, C>(rp, row_ok ? n_valid : 0,
+                                   (p.out_w % 4) == 0 && (reinterpret_cast<uintptr_t>(rp) & 15) == 0, rs);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    u[c] = rs[c] > 0.f ? __fdividef(gv[c] - v[o][c], rs[c]) : 0.f;
+            }
             if (p.with_stats) {   // uniform; selects instead of branches per element
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -632,7 +645,29 @@ __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& 
             const long long rowoff = it.plane * p.f_plane_stride +
                                      (long long)(row_ok ? y : 0) * p.f_pitch + it.x0;
             float fv[C];
-            if (p.mode == kEpiUpdate) {   // ein: f_in of this row (loaded by the caller)
+            if (p.mode == kEpiUpdate && p.solver != kSolverEm) {
+                // SART / SMART step relax * z / h (0 where h == 0: f stays)
+                float rhc[C];
+                if (p.h_vox) {
+                    const float* hp = p.h_vox +
+                                      ((long long)(it.plane % p.h_vox_planes) * p.out_h +
+                                       (row_ok ? y : 0)) * p.out_w + it.x0 + col0;
+                    load_row<float, C>(hp, row_ok ? n_valid : 0,
+                                       (p.out_w % 4) == 0 && (reinterpret_cast<uintptr_t>(hp) & 15) == 0,
+                                       rhc);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) rhc[c] = rhc[c] != 0.f ? 1.0f / rhc[c] : 0.f;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) rhc[c] = rh;
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float step = p.relax * v[o][c] * rhc[c];
+                    fv[c] = p.solver == kSolverSart ? fmaxf(ein[o][c] + step, 0.f)
+                                                    : ein[o][c] * __expf(step);
+                }
+            } else if (p.mode == kEpiUpdate) {   // ein: f_in of this row (loaded by the caller)
                 if (p.h_vox) {            // clipped boundary: h per voxel
                     const float* hp = p.h_vox +
                                       ((long long)(it.plane % p.h_vox_planes) * p.out_h +

@@ -71,6 +71,14 @@ enum Epilogue : int {
                      // task's input window (PSF-value gradient), into grad_part
 };
 
+// Update rule of the EM-style launches (kEpiRatio forward, kEpiUpdate
+// adjoint); values as CTIS_SOLVER_* in ctis.h.
+enum Solver : int {
+    kSolverEm = 0,      // u = g / q;              f <- f * z / h            (Eq. 2)
+    kSolverSart = 1,    // u = (g - q) / (H 1);    f <- max(f + relax z / h, 0)
+    kSolverSmart = 2    // u = log(g / q);         f <- f * exp(relax z / h)
+};
+
 struct GatherParams {
     const WorkItem* items;     // grouped by warp, in processing order
     const int* warp_begin;     // [n_warps + 1] range of each warp in items
@@ -114,6 +122,12 @@ struct GatherParams {
     int h_vox_planes;
     // kEpiRatio: write 1 - g / value instead of g / value (0 where value == 0)
     int ratio_one_minus;
+    // kEpiRatio / kEpiUpdate: the solver's rule (Solver) and relaxation;
+    // kSolverSart's forward divides by the row sums r = H 1, [out_h][out_w]
+    // dense (single frames only)
+    int solver;
+    float relax;
+    const float* row_sum;
     // kEpiGrad: f_in is the dense datacube [w][alpha][a] (out_w = a,
     // out_h = alpha); sums go to grad_part[(cluster * tiles_per_plane + tile
     // of the plane) * K * K + dy * K + dx]

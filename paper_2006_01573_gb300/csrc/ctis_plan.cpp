@@ -127,15 +127,20 @@ EncodeFn encode_fn() {
     return fn;
 }
 
+static_assert(CTIS_SOLVER_EM == kSolverEm && CTIS_SOLVER_SART == kSolverSart &&
+                  CTIS_SOLVER_SMART == kSolverSmart,
+              "the C ABI's solver codes are the kernels'");
+
 struct GraphKey {
     const void* g = nullptr;
     const void* f = nullptr;
     const void* stats = nullptr;
-    int k = -1, flags = 0;
+    int k = -1, flags = 0, solver = 0;
+    float relax = 1.f;
     bool profiling = false;
     bool operator==(const GraphKey& o) const {
         return g == o.g && f == o.f && stats == o.stats && k == o.k && flags == o.flags &&
-               profiling == o.profiling;
+               solver == o.solver && relax == o.relax && profiling == o.profiling;
     }
 };
 
@@ -194,6 +199,8 @@ struct ctis_plan {
     bool wrap = false;                // CTIS_BOUNDARY_WRAP: stored as the clip reading of the
                                       // PSF and its wrapped images (clip is set too)
     float* d_hvox = nullptr;          // clip: h = H^T 1 per voxel [w][alpha][a]
+    float* d_rowsum = nullptr;        // SART: r = H 1 per pixel [xi][gamma], built on first use
+    bool rowsum_valid = false;
     FftForm* fft = nullptr;           // the paper's FFT form, built on first use
     float* d_fft_u = nullptr;         // its EM ratio [n]
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
@@ -255,6 +262,7 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_tile_stats);
     cudaFree(P->d_red_part);
     cudaFree(P->d_hvox);
+    cudaFree(P->d_rowsum);
     fft_form_destroy(P->fft);
     cudaFree(P->d_fft_u);
     cudaFree(P->d_tap_slot);
@@ -1246,9 +1254,37 @@ int compute_hvox(ctis_plan* P, cudaStream_t st) {
     return CTIS_OK;
 }
 
-// Enqueues the whole reconstruction on `st`.
+// SART's row sums r = H 1 (per FPA pixel, from the stored values), as the
+// forward projection of an all-ones datacube; built once per set of values.
+// Synchronous (it uses the plan's datacube copies).
+int ensure_rowsum(ctis_plan* P) {
+    if (P->rowsum_valid) return CTIS_OK;
+    CTIS_CUDA(cudaDeviceSynchronize());   // queued work may still use the copies
+    if (!P->d_rowsum) {
+        const int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_rowsum), sizeof(float) * P->n);
+        if (rc) return rc;
+    }
+    int rc = scatter_f(P, nullptr, P->dtype, 1.0f, nullptr);
+    if (rc) return rc;
+    GatherParams p = base_params(P, P->fwd);
+    p.mode = kEpiRaw;
+    p.out_w = P->gamma;
+    p.out_h = P->xi;
+    p.out_f32 = P->d_rowsum;
+    p.out_pitch = P->gamma;
+    p.out_plane_stride = 0;
+    rc = enqueue_forward(P, p, nullptr);
+    if (rc) return rc;
+    CTIS_CUDA(cudaDeviceSynchronize());
+    P->rowsum_valid = true;
+    return CTIS_OK;
+}
+
+// Enqueues the whole reconstruction on `st`: k updates of `solver` (Solver)
+// with relaxation `relax` (EM ignores it).
 int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
-                        double* stats, cudaStream_t st) {
+                        double* stats, cudaStream_t st, int solver = kSolverEm,
+                        float relax = 1.f) {
     int rc = zero_u(P, st);   // the ratio writes u only where H f can be nonzero
     if (rc) return rc;
     if (flags & CTIS_INIT_ONES) {
@@ -1276,10 +1312,15 @@ int enqueue_reconstruct(ctis_plan* P, const float* g, void* f, int k, int flags,
     pf.out_copies = P->u_copies;
     pf.g = g;
     pf.g_pitch = P->gamma;
+    pf.solver = solver;
+    pf.relax = relax;
+    pf.row_sum = P->d_rowsum;
     GatherParams pa = base_params(P, P->adj);
     pa.mode = kEpiUpdate;
     pa.out_w = P->a;
     pa.out_h = P->alpha;
+    pa.solver = solver;
+    pa.relax = relax;
     set_f_copies(P, pa);
     P->prof_fwd.clear();
     P->prof_adj.clear();
@@ -2095,6 +2136,12 @@ int ctis_debug_arm(const ctis_plan* P, const void* user0, size_t bytes0, const v
 
 int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k, int flags,
                      double* stats_dev, void* stream) {
+    return ctis_reconstruct_solver(Pc, g_dev, f_dev, k, flags, CTIS_SOLVER_EM, 1.0f, stats_dev,
+                                   stream);
+}
+
+int ctis_reconstruct_solver(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k, int flags,
+                            int solver, float relax, double* stats_dev, void* stream) {
     int rc = check_plan(Pc);
     if (rc) return rc;
     ctis_plan* P = const_cast<ctis_plan*>(Pc);
@@ -2103,11 +2150,23 @@ int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k
     if (flags & ~(CTIS_INIT_ONES | CTIS_INIT_HTG) ||
         (flags & CTIS_INIT_ONES && flags & CTIS_INIT_HTG))
         return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    if (solver != CTIS_SOLVER_EM && solver != CTIS_SOLVER_SART && solver != CTIS_SOLVER_SMART)
+        return fail(CTIS_ERR_INVALID_ARG, "solver must be CTIS_SOLVER_EM, _SART or _SMART");
+    if (!(relax > 0.f && relax <= 2.f))
+        return fail(CTIS_ERR_INVALID_ARG, "relax = %g is not in (0, 2]", (double)relax);
+    if (solver == CTIS_SOLVER_EM) relax = 1.f;   // unused: one graph for every value
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CTIS_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (solver == CTIS_SOLVER_SART && !P->rowsum_valid) {
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(CTIS_ERR_INVALID_ARG,
+                        "SART's row sums are built by the first uncaptured call");
+        rc = ensure_rowsum(P);
+        if (rc) return rc;
+    }
     if (cap != cudaStreamCaptureStatusNone)   // caller is building its own graph
-        return enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, st);
+        return enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, st, solver, relax);
 
     GraphKey key;
     key.g = g_dev;
@@ -2115,6 +2174,8 @@ int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k
     key.stats = stats_dev;
     key.k = k;
     key.flags = flags;
+    key.solver = solver;
+    key.relax = relax;
     key.profiling = P->profiling;
     if (!(P->gexec && P->gkey == key)) {
         if (P->gexec) {
@@ -2122,7 +2183,8 @@ int ctis_reconstruct(const ctis_plan* Pc, const float* g_dev, void* f_dev, int k
             P->gexec = nullptr;
         }
         CTIS_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, P->cap_stream);
+        rc = enqueue_reconstruct(P, g_dev, f_dev, k, flags, stats_dev, P->cap_stream, solver,
+                                 relax);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
         if (rc) {
@@ -2312,6 +2374,7 @@ int ctis_plan_set_values(ctis_plan* P, const float* vals) {
     for (size_t k = 0; k < nnz; ++k)
         P->tap_v[k] = P->dtype == kDtypeBF16 ? bf16_bits_to_float(to_bf16_bits(vals[k])) : vals[k];
     compute_h(P);
+    P->rowsum_valid = false;   // rebuilt from the new values on SART's next use
     rc = write_values(P, false);
     if (!rc) rc = compute_hvox(P, nullptr);
     fft_form_destroy(P->fft);   // rebuilt from the new values on its next use
