@@ -423,7 +423,8 @@ def run_ours(args, wl, k):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
-    line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value)}
+    line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value),
+                     "solvers": solver_forms(args, wl, k, plan, g, flush, stream, value)}
     if world == 1 and not args.no_forms:
         line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
         line["forms"]["batched"] = batched_form(args, flush, stream)
@@ -470,6 +471,29 @@ def bf16_form(args, wl, k, psf, g, f32_result, flush, stream, f32_value):
     plan.close()
     return {"value": value, "unit": "it/s", "steps": steps, "vs_f32": value / f32_value,
             "rel_l2_vs_f32_after_k": err, "dtype": "bf16 storage, f32 accumulate"}
+
+
+def solver_forms(args, wl, k, plan, g, flush, stream, em_value):
+    """SART and SMART (ctis_reconstruct_solver, relaxation 1) on the same plan,
+    workload and g, with the per-iteration statistics: their iterations/s and
+    the ratio to EM's (the same two launches per iteration, other epilogue
+    rules)."""
+    import torch
+    f = torch.empty((wl.w, wl.alpha, wl.a), device=g.device)
+    stats = torch.empty((k + 1, 4), device=g.device, dtype=torch.float64)
+    out = {}
+    for solver in ("sart", "smart"):
+        run = lambda: plan.reconstruct(g, k, f=f, init="ones", stats=stats, solver=solver)
+        for _ in range(max(1, args.warmup)):
+            run()
+        torch.cuda.synchronize()
+        steps = max(1, min(args.steps, 5))
+        total = _timed_steps(run, steps, flush, stream)
+        plan.check()
+        value = steps * k / (total / 1e3)
+        out[solver] = {"value": value, "unit": "it/s", "steps": steps, "vs_em": value / em_value,
+                       "relax": 1.0}
+    return out
 
 
 def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=10):
