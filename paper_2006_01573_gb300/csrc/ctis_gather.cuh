@@ -235,11 +235,9 @@ struct Geo {
     static constexpr int SMEM_BYTES = BAR_OFF + NW * NS * 8;
     static constexpr int ER = R / NW;   // epilogue rows of each lane's block per warp
     static_assert(R % NW == 0, "the epilogue splits a lane's rows evenly over the warps");
-    // resident CTAs per SM the register budget must allow: 16 warps per SM
-    // (128 registers a thread) when the stages fit, else one CTA; the
-    // occupancy query has the last word
-    static constexpr int SMEM_FIT = (227 * 1024) / (SMEM_BYTES + 1024);
-    static constexpr int MIN_BLOCKS = SMEM_FIT >= 16 / NW ? 16 / NW : 1;
+    // resident CTAs per SM the register budget must allow (4 x 4 warps = 16
+    // warps per SM when the stages fit; the occupancy query has the last word)
+    static constexpr int MIN_BLOCKS = (227 * 1024) / (SMEM_BYTES + 1024) >= 4 ? 4 : 1;
 };
 
 // ---------------------------------------------------------------------------
