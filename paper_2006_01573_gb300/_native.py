@@ -34,6 +34,7 @@ EXPORTED = (
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
     "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct", "ctis_reconstruct_solver",
+    "ctis_plan_set_debug",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
         "ctis_plan_check": (I, [P, VP]),
         "ctis_forward_static_scratch": (I, [P, VP, VP, VP]),
         "ctis_plan_set_profiling": (I, [P, I]),
+        "ctis_plan_set_debug": (I, [P, I]),
         "ctis_plan_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "ctis_plan_set_values": (I, [P, f32p]),
@@ -325,6 +327,12 @@ class Plan:
         out = torch.empty(self.w * self.alpha * self.a, device="cuda", dtype=torch.int64)
         _check(load().ctis_index_map(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
+
+    def set_debug(self, drop_copies: bool):
+        """Test hook (ctis_plan_set_debug): with ``drop_copies`` every bounded
+        wait in the gather kernels runs out and ``check()`` raises
+        CTIS_ERR_TIMEOUT."""
+        _check(load().ctis_plan_set_debug(self._h, 1 if drop_copies else 0))
 
     def set_profiling(self, enable: bool):
         _check(load().ctis_plan_set_profiling(self._h, int(bool(enable))))

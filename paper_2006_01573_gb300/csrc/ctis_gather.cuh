@@ -872,10 +872,13 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
             uint64_t* bar = &my_bars[issue_stage];
             mbar_arrive_expect_tx(bar, G::TX_BYTES);
-            tma_load_3d(stage, &tm_win, nxt.wx, nxt.wy, nxt.plane, bar);
-            bulk_load(stage + G::WOFF,
-                      static_cast<const unsigned char*>(p.weights) + (long long)nxt.cluster * G::WBYTES,
-                      G::WBYTES, bar);
+            if (!p.drop_copies) {
+                tma_load_3d(stage, &tm_win, nxt.wx, nxt.wy, nxt.plane, bar);
+                bulk_load(stage + G::WOFF,
+                          static_cast<const unsigned char*>(p.weights) +
+                              (long long)nxt.cluster * G::WBYTES,
+                          G::WBYTES, bar);
+            }
             if (issue_task + 1 < task_end) nxt = p.tasks[issue_task + 1];
         }
         ++issue_task;

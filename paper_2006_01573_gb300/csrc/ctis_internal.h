@@ -141,6 +141,9 @@ struct GatherParams {
     // stays resident ~30 us (so the grid is placed as a real launch is) and
     // returns without touching anything else
     int* smid_out;
+    // test hook (ctis_plan_set_debug): arm each copy's barrier without
+    // issuing the copy, so every wait runs out through its bounded path
+    int drop_copies;
     double* tile_stats;        // [n_tiles][kNumStats] written by kEpiRatio with_stats
 };
 

@@ -201,6 +201,7 @@ struct ctis_plan {
     float* d_hvox = nullptr;          // clip: h = H^T 1 per voxel [w][alpha][a]
     float* d_rowsum = nullptr;        // SART: r = H 1 per pixel [xi][gamma], built on first use
     bool rowsum_valid = false;
+    bool drop_copies = false;         // CTIS_DEBUG_DROP_COPIES (test hook)
     FftForm* fft = nullptr;           // the paper's FFT form, built on first use
     float* d_fft_u = nullptr;         // its EM ratio [n]
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
@@ -1081,6 +1082,7 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.h = P->d_h;
     p.h_vox = P->d_hvox;
     p.h_vox_planes = P->w;
+    p.drop_copies = P->drop_copies;
     return p;
 }
 
@@ -1580,6 +1582,7 @@ GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward)
     p.h = B->d_h;
     p.h_vox = P->d_hvox;
     p.h_vox_planes = P->w;
+    p.drop_copies = P->drop_copies;
     return p;
 }
 
@@ -2201,6 +2204,15 @@ int ctis_reconstruct_solver(const ctis_plan* Pc, const float* g_dev, void* f_dev
         P->gkey = key;
     }
     CTIS_CUDA(cudaGraphLaunch(P->gexec, st));
+    return CTIS_OK;
+}
+
+int ctis_plan_set_debug(ctis_plan* P, int flags) {
+    if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
+    if (flags & ~CTIS_DEBUG_DROP_COPIES) return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    CTIS_CUDA(cudaDeviceSynchronize());   // cached graphs hold the old parameters
+    drop_table_users(P);
+    P->drop_copies = (flags & CTIS_DEBUG_DROP_COPIES) != 0;
     return CTIS_OK;
 }
 
