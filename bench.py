@@ -208,21 +208,24 @@ def oracle_sample(wl, g, budget_s: float, n_waves: int = 4):
     return iters * frac / el, iters, el, desc
 
 
+def oracle_measurement(wl):
+    """The oracle's timing input: Poisson counts of the scene as imaged by
+    the oracle's own first wavelength blocks (nothing from the GPU path)."""
+    import oracle as O
+    import synth
+    geom = O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    taps = O.merge_psf(geom, synth.make_psf(wl))
+    f_true = synth.make_scene(wl).ravel()
+    Hs = O.BlockH(geom, taps, range(min(4, wl.w)))
+    g, _ = synth.make_measurement(Hs.forward(f_true), wl.peak, wl.seed)
+    return g
+
+
 def run_reference(args, wl, k):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
-    import oracle as O
-    import synth
-    geom = O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
-    psf = synth.make_psf(wl)
-    taps = O.merge_psf(geom, psf)
-    f_true = synth.make_scene(wl).ravel()
-    # noiseless image of the first wavelength blocks only: timing input
-    Hs = O.BlockH(geom, taps, range(min(4, wl.w)))
-    g, _ = synth.make_measurement(Hs.forward(f_true), wl.peak, wl.seed)
+    g = oracle_measurement(wl)
     budget = max(2.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(wl, g, budget / 4)
@@ -431,7 +434,7 @@ def run_ours(args, wl, k):
         line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
-        v, iters_cpu, el, desc = oracle_sample(wl, g_host, args.cpu_budget)
+        v, iters_cpu, el, desc = oracle_sample(wl, oracle_measurement(wl), args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "it/s", "cores": 1, "kind": "oracle",
                                 "sample": desc, "host_cpus": os.cpu_count()}
     print(json.dumps(line), flush=True)
