@@ -431,6 +431,7 @@ def run_ours(args, wl, k):
     if world == 1 and not args.no_forms:
         line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
         line["forms"]["batched"] = batched_form(args, flush, stream)
+        line["forms"]["large"] = large_form(args, flush, stream)
         line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
@@ -587,6 +588,40 @@ def batched_form(args, flush, stream, nframes=256, k=100):
     for p in plans:
         p.close()
     return out
+
+
+def large_form(args, flush, stream):
+    """The large workload (256x256x128 cube, 2048x2048 FPA, 5x5 orders of
+    5x5 spots: 625 nonzeros per image, K = 5 clusters), k = 50 EM iterations
+    with statistics per step: iterations/s, voxel-updates/s and the FP32
+    FLOP rate of the two projections."""
+    import torch
+    import synth
+    from paper_2006_01573_gb300 import Plan
+    wl = synth.LARGE
+    k = wl.k
+    psf = synth.make_psf(wl)
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+    hf = plan.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
+    g = torch.poisson(hf * (wl.peak / hf.max()), generator=torch.Generator(device="cuda").manual_seed(wl.seed))
+    plan.autotune(g)
+    f = torch.empty((wl.w, wl.alpha, wl.a), device="cuda")
+    stats = torch.empty((k + 1, 4), device="cuda", dtype=torch.float64)
+    run = lambda: plan.reconstruct(g, k, f=f, init="ones", stats=stats)
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    total = _timed_steps(run, steps, flush, stream)
+    plan.check()
+    info = plan.info()
+    plan.close()
+    value = steps * k / (total / 1e3)
+    flops = 2 * 2 * int(info["nnz"]) * wl.a * wl.alpha   # two projections, 2 FLOP per FMA
+    return {"workload": wl.name, "k": k, "steps": steps, "value": value, "unit": "it/s",
+            "voxel_updates_per_s": value * wl.m, "tflops_two_projections": value * flops / 1e12,
+            "cluster_k": int(info["cluster_k"]),
+            "data": "seeded scene, Poisson counts of the GPU image drawn on the GPU"}
 
 
 def autograd_form(args, flush, stream, k=10):

@@ -341,8 +341,9 @@ int ctis_psf_grad(const ctis_plan* plan, const void* f_dev, const float* r_dev,
  *   dependence of h = H^T 1 on v), df0_dev = dL/df0 when not NULL (float32).
  * The iterates are checkpointed (the plan keeps (k+1)*m float32 of workspace,
  * grown on demand); the backward pass recomputes each step's projections.
- * float32 plans with CTIS_BOUNDARY_REJECT only (CTIS_ERR_UNSUPPORTED
- * otherwise); 0 <= k <= 4096. */
+ * float32 plans with CTIS_BOUNDARY_REJECT or _CLIP (under CLIP h = H^T 1 is
+ * per voxel, and its dependence on v goes through the taps whose shifted
+ * copy lands on the FPA); CTIS_ERR_UNSUPPORTED otherwise; 0 <= k <= 4096. */
 int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_dev, int k,
                            double* nll_dev, float* dval_dev, float* df0_dev, void* stream);
 

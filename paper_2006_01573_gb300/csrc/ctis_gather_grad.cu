@@ -85,22 +85,31 @@ __global__ void fpa_to_copies_kernel(float* copies, long long copy_stride, int n
 //   gfd = gb * z / h_s     (direct part of dL/df);
 //   part[s][block] = sum over the block of gb * f * z  (float64), from which
 //   dL/dh_s = -sum / h_s^2.
+// With h per voxel (h_vox, the clipped boundary) the same with h_j in place
+// of h_s, and dL/dh_j = -gb f z / h_j^2 per voxel into dh_vox (0 where
+// h_j == 0).
 // Grid: (blocks per plane, w); each block sums its slice in a fixed order.
 constexpr int kVjpThreads = 256;
 __global__ void __launch_bounds__(kVjpThreads)
     voxel_vjp_kernel(float* a_dense, float* a_copies, long long copy_stride, int ncopies,
                      int pitch, long long plane_stride, float* gfd, double* part,
                      const float* gb, const float* f, const float* z, const float* h, int a,
-                     int alpha) {
+                     int alpha, const float* h_vox, float* dh_vox) {
     const int s = blockIdx.y;
     const long long plane = (long long)a * alpha;
     const float hs = h[s];
-    const float rh = hs != 0.f ? 1.0f / hs : 0.f;
+    const float rh_s = hs != 0.f ? 1.0f / hs : 0.f;
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
          i += (long long)gridDim.x * blockDim.x) {
         const long long j = s * plane + i;
         const float gv = gb[j], fv = f[j], zv = z[j];
+        float rh = rh_s;
+        if (h_vox) {
+            const float hj = h_vox[j];
+            rh = hj != 0.f ? 1.0f / hj : 0.f;
+            dh_vox[j] = -gv * fv * zv * rh * rh;
+        }
         const float av = gv * fv * rh;
         a_dense[j] = av;
         gfd[j] = gv * zv * rh;
@@ -178,11 +187,12 @@ int voxel_vjp_blocks() { return 32; }
 cudaError_t launch_voxel_vjp(float* a_dense, float* a_copies, long long copy_stride, int ncopies,
                              int pitch, long long plane_stride, float* gfd, double* part,
                              const float* gb, const float* f, const float* z, const float* h,
-                             int a, int alpha, int w, cudaStream_t stream) {
+                             int a, int alpha, int w, const float* h_vox, float* dh_vox,
+                             cudaStream_t stream) {
     dim3 grid(voxel_vjp_blocks(), w);
     voxel_vjp_kernel<<<grid, kVjpThreads, 0, stream>>>(a_dense, a_copies, copy_stride, ncopies,
                                                        pitch, plane_stride, gfd, part, gb, f, z,
-                                                       h, a, alpha);
+                                                       h, a, alpha, h_vox, dh_vox);
     return cudaGetLastError();
 }
 

@@ -95,12 +95,14 @@ cudaError_t launch_fpa_to_copies(float* copies, long long copy_stride, int ncopi
                                  int height, int mode, cudaStream_t stream);
 // Vector-Jacobian product of f' = f * z / h_s: a = gb f / h_s (dense and into
 // the datacube copies), gfd = gb z / h_s, per-plane float64 partials of
-// gb f z; launch_dh_finish turns them into dL/dh_s.
+// gb f z; launch_dh_finish turns them into dL/dh_s. With h_vox (h per voxel)
+// h_j replaces h_s and dL/dh_j goes to dh_vox per voxel.
 int voxel_vjp_blocks();
 cudaError_t launch_voxel_vjp(float* a_dense, float* a_copies, long long copy_stride, int ncopies,
                              int pitch, long long plane_stride, float* gfd, double* part,
                              const float* gb, const float* f, const float* z, const float* h,
-                             int a, int alpha, int w, cudaStream_t stream);
+                             int a, int alpha, int w, const float* h_vox, float* dh_vox,
+                             cudaStream_t stream);
 cudaError_t launch_dh_finish(double* dh, const double* part, const float* h, int w,
                              cudaStream_t stream);
 cudaError_t launch_add(float* out, const float* x, const float* y, long long n,

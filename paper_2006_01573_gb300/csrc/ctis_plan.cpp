@@ -2414,9 +2414,9 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     if (rc) return rc;
     if (P->dtype != kDtypeF32)
         return fail(CTIS_ERR_UNSUPPORTED, "the unrolled EM gradient needs a float32 plan");
-    if (P->clip)
+    if (P->wrap)
         return fail(CTIS_ERR_UNSUPPORTED,
-                    "the unrolled EM gradient needs CTIS_BOUNDARY_REJECT (h per wavelength)");
+                    "the unrolled EM gradient under CTIS_BOUNDARY_WRAP (images share values)");
     if (!g_dev || !nll_dev || !dval_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
     if (k < 0 || k > 4096) return fail(CTIS_ERR_INVALID_ARG, "k must be in [0, 4096]");
     const int64_t m = P->m, n = P->n;
@@ -2435,7 +2435,7 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     }
     const int vb = voxel_vjp_blocks();
     if (!P->d_work) {
-        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_work), sizeof(float) * (2 * n + 5 * m));
+        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_work), sizeof(float) * (2 * n + 6 * m));
         if (!rc)
             rc = dmalloc(P, reinterpret_cast<void**>(&P->d_gwork),
                          sizeof(double) * (static_cast<size_t>(w) * vb + w + kNumStats));
@@ -2448,6 +2448,7 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
     float* gb = gfd + m;
     float* hq = gb + m;
     float* adense = hq + m;
+    float* dh_vox = adense + m;   // clipped boundary: dL/dh per voxel
     double* vjp_part = P->d_gwork;
     double* dh = vjp_part + static_cast<size_t>(w) * vb;
     double* stats = dh + w;
@@ -2531,16 +2532,23 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
         if (rc) return rc;
         CTIS_CUDA(launch_voxel_vjp(adense, static_cast<float*>(P->d_fwork), P->f_copy_stride,
                                    P->f_copies, P->a_pitch, fplane, gfd, vjp_part, gb, ck(t), z,
-                                   P->d_h, a, al, w, st));             // a, gfd, dL/dh parts
-        CTIS_CUDA(launch_dh_finish(dh, vjp_part, P->d_h, w, st));
+                                   P->d_h, a, al, w, P->clip ? P->d_hvox : nullptr, dh_vox,
+                                   st));                                // a, gfd, dL/dh parts
+        if (!P->clip) CTIS_CUDA(launch_dh_finish(dh, vjp_part, P->d_h, w, st));
         rc = forward_raw(gu);                                           // dL/du = H a
         if (!rc) rc = enqueue_psf_grad(P, adense, dval_dev, true, nullptr, st);   // via H^T u
         if (rc) return rc;
         CTIS_CUDA(launch_fpa_to_copies(P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch, q, g_dev,
                                        gu, ga, xi, 1, st));            // dL/dq = -gu g / q^2
         rc = adjoint_raw(hq);                                           // H^T dL/dq
-        if (!rc) rc = enqueue_psf_grad(P, ck(t), dval_dev, true, dh, st);   // via H f, and h
-        if (rc) return rc;
+        if (!rc) rc = enqueue_psf_grad(P, ck(t), dval_dev, true, P->clip ? nullptr : dh, st);
+        if (rc) return rc;                                              // via H f (and h_s)
+        if (P->clip) {   // via h_j = sum of the taps whose copy for voxel j lands on the FPA:
+                         // dh_j/dv_t = 1 there, the adjoint of an all-ones FPA image
+            rc = scatter_u(P, nullptr, st, 1.0f);
+            if (!rc) rc = enqueue_psf_grad(P, dh_vox, dval_dev, true, nullptr, st);
+            if (rc) return rc;
+        }
         CTIS_CUDA(launch_add(gb, gfd, hq, m, st));                      // dL/df
     }
     if (df0_dev)

@@ -144,12 +144,35 @@ def test_batched_clipped_frames_equal_single_frame_reconstructions():
         plan.check()
 
 
-def test_unrolled_gradient_needs_the_reject_boundary():
+@pytest.mark.parametrize("k", [0, 1, 3])
+def test_unrolled_gradient_with_h_per_voxel(k):
+    """The NLL after k EM updates under clipping and its gradient in the tap
+    values (h per voxel depends on the taps that land for each voxel),
+    against the oracle's NLL and central differences of it."""
     wl, shift = CASES[0]
-    with _plan(wl, _psf(wl, shift)) as plan:
-        g = torch.ones((wl.xi, wl.gamma), device="cuda")
-        with pytest.raises(CtisError):
-            plan.unrolled_nll_grad(g, 2)
+    geom = geometry(wl)
+    psf = _psf(wl, shift)
+    taps = O.merge_psf(geom, psf, "clip")
+    taps = O.with_values(taps, taps.v.astype(np.float32).astype(np.float64))
+    H = O.BlockH(geom, taps)
+    g, _ = synth.make_measurement(H.forward(synth.make_scene(wl).ravel()), wl.peak, wl.seed)
+    f0 = np.ones(geom.m)
+    with _plan(wl, psf) as plan:
+        nll, dval, _ = plan.unrolled_nll_grad(torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda(), k)
+        plan.check()
+        nll, dval = float(nll), dval.cpu().numpy()
+    ref = O.unrolled_nll(geom, taps, g, f0, k)
+    assert abs(nll - ref) <= 1e-5 * abs(ref)
+    idx = np.random.default_rng(20 + k).choice(taps.v.size, 24, replace=False)
+    fd = np.zeros(len(idx))
+    for n, t in enumerate(idx):
+        eps = 1e-4 * max(taps.v[t], 1e-3)
+        vp, vm = taps.v.copy(), taps.v.copy()
+        vp[t] += eps
+        vm[t] -= eps
+        fd[n] = (O.unrolled_nll(geom, O.with_values(taps, vp), g, f0, k) -
+                 O.unrolled_nll(geom, O.with_values(taps, vm), g, f0, k)) / (2 * eps)
+    assert np.all(np.abs(dval[idx] - fd) <= 2e-3 * np.abs(fd).max()), (dval[idx], fd)
 
 
 def test_batched_frames_read_zeros_past_their_fpa_edges():

@@ -125,6 +125,8 @@ def test_h_is_the_total_psf_value_and_values_are_fixed():
         f = torch.ones((wl.w, wl.alpha, wl.a), device="cuda")
         with pytest.raises(CtisError):
             plan.psf_grad(f, torch.ones((wl.xi, wl.gamma), device="cuda"))
+        with pytest.raises(CtisError):
+            plan.unrolled_nll_grad(torch.ones((wl.xi, wl.gamma), device="cuda"), 1)
 
 
 def test_batched_wrapped_frames_equal_single_frame_reconstructions():
