@@ -77,3 +77,22 @@ def test_host_side_argument_errors(lib, case, expect):
 
 def test_destroy_null_is_ok(lib):
     assert lib.ctis_plan_destroy(None) == 0
+
+
+def test_header_compiles_as_c_and_a_c_caller_links(lib, tmp_path):
+    """include/ctis.h is plain C: a C99 program built with gcc against it and
+    libctis.so runs the host-only entry points (no GPU needed)."""
+    root = os.path.dirname(os.path.dirname(__file__))
+    exe = str(tmp_path / "abi_host_only")
+    libdir = os.path.dirname(ctis.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c", "abi_host_only.c"), "-o", exe,
+                    "-L", libdir, "-lctis", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert "reject CTIS_ERR_OUT_OF_BOUNDS" in out.stdout
+    first = out.stdout.splitlines()[0].split()
+    # each wavelength's two nonzeros are 8-connected: one 3 x 3 cluster each;
+    # a 6 x 5 footprint on a 10 x 9 FPA meets at least one 32 x 32 tile
+    assert first[:4] == ["clusters", "2", "k", "3"] and int(first[5]) >= 1 and int(first[7]) >= 2
