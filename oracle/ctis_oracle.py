@@ -23,6 +23,9 @@ shift-invariance":
 * The bfloat16 storage form (datacube and PSF values kept in bfloat16, sums in
   wider precision) is not in the paper; :func:`round_bf16` states the storage
   rounding and :func:`em_step_stored` applies it to an EM step.
+* Sec. 2 names ART and MART among the usual solvers without defining them;
+  :func:`sart_step` and :func:`smart_step` are their simultaneous forms from
+  the literature the paper cites (SART, SMART), on the same projector pair.
 
 Everything is float64. Inputs given as float32 (datacube, PSF values, counts)
 are promoted exactly. Readings of points the paper leaves open:
@@ -49,7 +52,10 @@ Eqs. 13/17 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
 for w = 1, brute-force Python loops on tiny inputs, hand-worked values in
 tests/golden/, the EM invariants (nonnegativity, flux, monotone likelihood),
 finite differences of a dense H, and PyTorch's float32 -> bfloat16 conversion
-for :func:`round_bf16`.
+for :func:`round_bf16`. The wrap reading is pinned to the literal circulant of
+Eq. 7 (:func:`dense_H`) and to the FFT form; the solvers
+(tests/test_oracle_solvers.py) to hand-worked steps, brute-force loops over a
+dense H, fixed points at consistent data and their monotone objectives.
 """
 from __future__ import annotations
 
