@@ -312,6 +312,16 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
                              void* const* f_dev, int k, int flags, double* stats_dev,
                              void* stream);
 
+/* ctis_reconstruct_batched with the update rule of `solver` and relaxation
+ * `relax` (as ctis_reconstruct_solver; CTIS_SOLVER_EM is exactly
+ * ctis_reconstruct_batched). Each frame equals its single-frame
+ * ctis_reconstruct_solver run bit for bit. SART builds a plan's row sums
+ * on its first use (synchronous). */
+int ctis_reconstruct_batched_solver(ctis_plan* const* plans, int nplans, int nframes,
+                                    const int* plan_idx, const float* const* g_dev,
+                                    void* const* f_dev, int k, int flags, int solver, float relax,
+                                    double* stats_dev, void* stream);
+
 /* ---- gradients (the differentiable form of the projector pair) ----------
  * The PSF values are the parameters: tap t of wavelength s, at FPA offset
  * (x_t, y_t) for field-stop pixel (0, 0), adds v_t f_s(p, r) to pixel

@@ -34,7 +34,7 @@ EXPORTED = (
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
     "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct", "ctis_reconstruct_solver",
-    "ctis_plan_set_debug",
+    "ctis_plan_set_debug", "ctis_reconstruct_batched_solver",
     "ctis_status_string", "ctis_last_error",
 )
 
@@ -104,6 +104,9 @@ def load(path: str = LIB_PATH):
         "ctis_fft_reconstruct": (I, [P, VP, VP, I, I, VP]),
         "ctis_reconstruct_batched": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
                                          ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, VP, VP]),
+        "ctis_reconstruct_batched_solver": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I),
+                                                ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, I,
+                                                ctypes.c_float, VP, VP]),
         "ctis_psf_grad": (I, [P, VP, VP, VP, VP]),
         "ctis_unrolled_nll_grad": (I, [P, VP, VP, I, VP, VP, VP, VP]),
         "ctis_tables_inspect": (I, [I, I, I, I, I, i32p, i32p, i32p, f32p, I,
@@ -467,10 +470,11 @@ class Plan:
 
 
 def reconstruct_batched(plans, plan_idx, gs, k: int, fs=None, init: str | None = "ones",
-                        stats=False, stream=None):
+                        stats=False, stream=None, solver: str = "em", relax: float = 1.0):
     """k EM updates on every frame i: plan ``plans[plan_idx[i]]``, counts
     ``gs[i]``, result in ``fs[i]`` (allocated when ``fs`` is None; read as the
     initial guess when ``init`` is None). One CUDA graph for the whole batch.
+    ``solver`` / ``relax`` as in ``Plan.reconstruct`` ('em', 'sart', 'smart').
     Returns ``(fs, stats)`` with stats a ``(nframes, k+1, 4)`` float64 tensor
     when requested."""
     import torch
@@ -497,7 +501,7 @@ def reconstruct_batched(plans, plan_idx, gs, k: int, fs=None, init: str | None =
     idx = (ctypes.c_int * nframes)(*plan_idx)
     gp = (ctypes.c_void_p * nframes)(*[g.data_ptr() for g in gs])
     fp = (ctypes.c_void_p * nframes)(*[f.data_ptr() for f in fs])
-    _check(load().ctis_reconstruct_batched(hp, len(plans), nframes, idx, gp, fp, int(k), flags,
-                                           ctypes.c_void_p(st.data_ptr() if st is not None else 0),
-                                           _stream(stream)))
+    _check(load().ctis_reconstruct_batched_solver(
+        hp, len(plans), nframes, idx, gp, fp, int(k), flags, _SOLVER[solver], float(relax),
+        ctypes.c_void_p(st.data_ptr() if st is not None else 0), _stream(stream)))
     return fs, st

@@ -1615,6 +1615,8 @@ struct BatchRun {
     BatchState* B;
     GatherParams pf, pa;
     bool stats;
+    int solver = kSolverEm;
+    float relax = 1.f;
 };
 
 int batch_setup(BatchRun& r, int flags, cudaStream_t st) {
@@ -1673,6 +1675,9 @@ int batch_setup(BatchRun& r, int flags, cudaStream_t st) {
     pa.f_plane_stride = fplane;
     pa.f_copy_stride = B->f_copy_stride;
     pa.f_copies = P->f_copies;
+    pf.solver = pa.solver = r.solver;   // the rules of ctis_reconstruct_solver
+    pf.relax = pa.relax = r.relax;
+    pf.row_sum = P->d_rowsum;           // per pixel, the same for every frame
     return CTIS_OK;
 }
 
@@ -1726,11 +1731,12 @@ struct BatchedKey {
     std::vector<const ctis_plan*> plans;
     std::vector<int> plan_idx;
     std::vector<const void*> g, f;
-    int k = -1, flags = 0;
+    int k = -1, flags = 0, solver = 0;
+    float relax = 1.f;
     const void* stats = nullptr;
     bool operator==(const BatchedKey& o) const {
         return plans == o.plans && plan_idx == o.plan_idx && g == o.g && f == o.f && k == o.k &&
-               flags == o.flags && stats == o.stats;
+               flags == o.flags && solver == o.solver && relax == o.relax && stats == o.stats;
     }
 };
 std::mutex g_batched_mu;
@@ -2559,12 +2565,25 @@ int ctis_unrolled_nll_grad(ctis_plan* P, const float* g_dev, const float* f0_dev
 int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
                              const int* plan_idx, const float* const* g_dev, void* const* f_dev,
                              int k, int flags, double* stats_dev, void* stream) {
+    return ctis_reconstruct_batched_solver(plans, nplans, nframes, plan_idx, g_dev, f_dev, k,
+                                           flags, CTIS_SOLVER_EM, 1.0f, stats_dev, stream);
+}
+
+int ctis_reconstruct_batched_solver(ctis_plan* const* plans, int nplans, int nframes,
+                                    const int* plan_idx, const float* const* g_dev,
+                                    void* const* f_dev, int k, int flags, int solver, float relax,
+                                    double* stats_dev, void* stream) {
     if (!plans || nplans < 1 || nframes < 1 || !plan_idx || !g_dev || !f_dev)
         return fail(CTIS_ERR_INVALID_ARG, "NULL array or empty batch");
     if (k < 0) return fail(CTIS_ERR_INVALID_ARG, "k must be >= 0");
     if (flags & ~(CTIS_INIT_ONES | CTIS_INIT_HTG) ||
         (flags & CTIS_INIT_ONES && flags & CTIS_INIT_HTG))
         return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    if (solver != CTIS_SOLVER_EM && solver != CTIS_SOLVER_SART && solver != CTIS_SOLVER_SMART)
+        return fail(CTIS_ERR_INVALID_ARG, "solver must be CTIS_SOLVER_EM, _SART or _SMART");
+    if (!(relax > 0.f && relax <= 2.f))
+        return fail(CTIS_ERR_INVALID_ARG, "relax = %g is not in (0, 2]", (double)relax);
+    if (solver == CTIS_SOLVER_EM) relax = 1.f;
     for (int p = 0; p < nplans; ++p) {
         int rc = check_plan(plans[p]);
         if (rc) return rc;
@@ -2585,6 +2604,7 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
     for (int p = 0; p < nplans; ++p) {
         if (frames[p].empty()) continue;
         int rc = ensure_batch(plans[p], static_cast<int>(frames[p].size()), k);
+        if (!rc && solver == CTIS_SOLVER_SART) rc = ensure_rowsum(plans[p]);
         if (rc) return rc;
         used.push_back(p);
     }
@@ -2611,6 +2631,8 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
     key.f.assign(f_dev, f_dev + nframes);
     key.k = k;
     key.flags = flags;
+    key.solver = solver;
+    key.relax = relax;
     key.stats = stats_dev;
     std::lock_guard<std::mutex> lock(g_batched_mu);
     int dev = 0;
@@ -2631,7 +2653,9 @@ int ctis_reconstruct_batched(ctis_plan* const* plans, int nplans, int nframes,
         }
         cudaStream_t cs = g_batched_stream;
         std::vector<BatchRun> runs;
-        for (int p : used) runs.push_back(BatchRun{plans[p], plans[p]->batch, {}, {}, stats_dev != nullptr});
+        for (int p : used)
+            runs.push_back(BatchRun{plans[p], plans[p]->batch, {}, {}, stats_dev != nullptr, solver,
+                                    relax});
         CTIS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int rc = CTIS_OK;
         for (BatchRun& r : runs)

@@ -153,3 +153,31 @@ def test_bad_solver_arguments_are_refused():
                 plan.reconstruct(gt, 2, solver="sart", relax=lam)
         with pytest.raises(KeyError):
             plan.reconstruct(gt, 2, solver="mart")
+
+
+@pytest.mark.parametrize("solver", ["sart", "smart"])
+def test_batched_frames_equal_single_frame_solver_runs(solver):
+    """ctis_reconstruct_batched_solver: frames of two geometries, each equal
+    bit for bit to its single-frame ctis_reconstruct_solver run."""
+    from paper_2006_01573_gb300 import reconstruct_batched
+    wls = [synth.TINY, RAGGED]
+    plans = [Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl)) for wl in wls]
+    try:
+        plan_idx = [0, 1, 1, 0, 1]
+        gs = []
+        for n, i in enumerate(plan_idx):
+            wl = wls[i]
+            H = O.build_H(geometry(wl), synth.make_psf(wl))
+            g, _ = synth.make_measurement(H.forward(synth.make_scene(wl, 500 + n).ravel()),
+                                          wl.peak, 500 + n)
+            gs.append(torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda())
+        fs, st = reconstruct_batched(plans, plan_idx, gs, 5, stats=True, solver=solver, relax=0.9)
+        for p in plans:
+            p.check()
+        for n, i in enumerate(plan_idx):
+            ref, ref_st = plans[i].reconstruct(gs[n], 5, init="ones", stats=True, solver=solver,
+                                               relax=0.9)
+            assert torch.equal(fs[n], ref) and torch.equal(st[n], ref_st), n
+    finally:
+        for p in plans:
+            p.close()
