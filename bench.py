@@ -154,16 +154,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, units_scale: float = 1.0):
+def ncu_traffic(kernel: str, workload: str, units_scale: float = 1.0):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel sources changed since those counters were taken."""
+    when the kernel sources changed since those counters were taken or they
+    were taken on another workload."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             data = json.load(fh)
     except (OSError, ValueError):
         return None
-    if data.get("source_hash") != kernel_source_hash():
+    if data.get("source_hash") != kernel_source_hash() or data.get("workload") != workload:
         return None
     entry = data.get("kernels", {}).get(kernel)
     return None if entry is None else entry["dram_bytes_per_launch"] * units_scale
@@ -411,7 +412,7 @@ def run_ours(args, wl, k):
         "voxel_updates_per_s": value * wl.m,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": ncu_traffic(dom),
+                     "traffic": ncu_traffic(dom, wl.name),
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2070 MHz (max SM clock)",
                      "timing": "CUDA event pair around every launch on its stream, over K steps "
                                "run right after the timed region (same workload and L2 flush)",
