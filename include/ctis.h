@@ -72,8 +72,8 @@ enum { CTIS_F32 = 0, CTIS_BF16 = 1 };
  * images at (x - gamma, y + 1), (x, y - xi) and (x - gamma, y + 1 - xi)
  * (those whose shifted copies can meet the FPA): each shifted copy re-enters
  * at exactly one of them. ctis_plan_export_taps then lists the images too,
- * and ctis_plan_set_values and ctis_psf_grad return CTIS_ERR_UNSUPPORTED
- * (an image must keep its original's value). */
+ * and ctis_plan_set_values, ctis_psf_grad and ctis_unrolled_nll_grad return
+ * CTIS_ERR_UNSUPPORTED (an image must keep its original's value). */
 enum { CTIS_BOUNDARY_REJECT = 0, CTIS_BOUNDARY_CLIP = 1, CTIS_BOUNDARY_WRAP = 2 };
 
 /* ctis_reconstruct flags. Without an INIT flag, f_dev holds the initial guess. */
