@@ -172,3 +172,36 @@ def test_bf16_full_size_sampled_outputs():
     ps = rng.integers(0, wl.a, 200)
     rs = rng.integers(0, wl.alpha, 200)
     assert floored_rel(z[ss, rs, ps], O.adjoint_at(geom, taps, r.ravel(), ss, ps, rs)) <= TOL
+
+
+@pytest.mark.parametrize("boundary", ["clip", "wrap"])
+def test_bf16_under_the_other_boundaries(boundary):
+    """bfloat16 storage under the clip (h per voxel) and wrap (stored images)
+    boundaries: projectors on the rounded inputs within the float32 bound,
+    one EM step within one bfloat16 unit of the float64 step from the same
+    stored iterate."""
+    wl = CASES["ragged"]
+    ptr, x, y, v = synth.make_psf(wl)
+    if boundary == "clip":
+        x, y = x - 9, y + 4
+    else:
+        x, y = x + wl.gamma - 1 - x.max(), y + wl.xi - 1 - y.max()
+    psf = (ptr, x.astype(np.int32), y.astype(np.int32), v)
+    geom = geometry(wl)
+    taps = O.merge_psf(geom, psf, boundary)
+    taps = O.with_values(taps, O.round_bf16(taps.v.astype(np.float32)).astype(np.float64))
+    H = O.BlockH(geom, taps)
+    f, ft = _bf16_cube(wl, 71)
+    r = synth.random_positive((wl.xi, wl.gamma), 72)
+    g = (synth.random_positive(geom.n, 73) * 100).astype(np.float32)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16", boundary=boundary) as plan:
+        hf = plan.forward(ft).cpu().numpy().ravel()
+        ht = plan.adjoint(torch.from_numpy(r).cuda()).cpu().numpy().ravel()
+        f1, _ = plan.reconstruct(torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda(), 1,
+                                 f=ft.clone(), init=None)
+        plan.check()
+        f1 = f1.float().cpu().numpy().ravel()
+    assert floored_rel(hf, H.forward(f.ravel())) <= TOL
+    assert floored_rel(ht, H.adjoint(r.ravel())) <= TOL
+    step = O.em_step(H, g, f.ravel().astype(np.float64))
+    assert floored_rel(f1, step) <= BF16_ULP
