@@ -501,12 +501,14 @@ def solver_forms(args, wl, k, plan, g, flush, stream, em_value):
     return out
 
 
-def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=10):
+def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=33):
     """The paper's own (WBH) form of the projectors, on the same workload and
-    g: k EM updates with cuFFT transforms of length n and this project's
-    spectral multiply-accumulate and index maps (Eqs. 11, 13, 14, 17). Its
-    iterations/s, the ratio to the gather path, and its distance from the
-    gather reconstruction after k iterations (both from ones)."""
+    g: k EM updates (33, as the paper's validation) with cuFFT transforms of
+    length n and this project's spectral multiply-accumulate and index maps
+    (Eqs. 11, 13, 14, 17). Its iterations/s, the ratio to the gather path, and
+    its distance from the gather reconstruction after k iterations (both from
+    ones): relative L2 and the paper's average relative pixel error (Sec. 4,
+    over the voxels above 1e-6 of the maximum)."""
     import torch
     from paper_2006_01573_gb300 import Plan
     plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
@@ -518,11 +520,14 @@ def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=10):
     total = _timed_steps(lambda: plan.fft_reconstruct(g, k, f=f.fill_(1.0)), steps, flush, stream)
     ref, _ = plan.reconstruct(g, k, init="ones")
     plan.check()
-    err = float(torch.linalg.vector_norm(f.double() - ref.double()) / torch.linalg.vector_norm(ref.double()))
+    a, b = f.double(), ref.double()
+    err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    on = b > 1e-6 * b.max()
+    avg_rel = float(((a[on] - b[on]).abs() / b[on]).mean())
     plan.close()
     value = steps * k / (total / 1e3)
     return {"value": value, "unit": "it/s", "k": k, "steps": steps, "vs_gather": value / f32_value,
-            "rel_l2_vs_gather_after_k": err,
+            "rel_l2_vs_gather_after_k": err, "avg_rel_pixel_err_vs_gather_after_k": avg_rel,
             "form": "cuFFT R2C/C2R of length n per wavelength + spectral MAC (float32)"}
 
 

@@ -19,6 +19,16 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def avg_rel_pixel_err(a, b, floor_frac=1e-6):
+    """The paper's reconstruction-quality figure (Sec. 4): the mean over
+    voxels of |a_j - b_j| / b_j, here over the voxels with
+    b_j > floor_frac * max b (the paper's sum divides by values that may be 0)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    on = b > floor_frac * max(b.max(), 1e-300)
+    return float(np.mean(np.abs(a[on] - b[on]) / b[on]))
+
+
 def geometry(wl):
     return O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
 
