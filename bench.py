@@ -54,6 +54,11 @@ def parse_args():
                     help="skip the autotuner and use these schedules, 'FWD,ADJ' with each "
                          "'chunk:TASKS:SKEW' or 'split:OVERHEAD_Q:SKEW' (SKEW in permille), "
                          "e.g. a bench line's config.schedule.spec")
+    ap.add_argument("--paper-table", default=None, metavar="OUT_JSON",
+                    help="instead of the bench line: the paper's Table 1 grid (field stop "
+                         "89x80, 2048x2048 FPA, w = 3, 24, 75, K = 10..3100) on a synthetic PSF, "
+                         "gather and FFT-form reconstruction times beside the paper's P4000 "
+                         "times; writes OUT_JSON and prints a one-line summary")
     ap.add_argument("--crossover", default=None, metavar="OUT_JSON",
                     help="instead of the bench line: sweep the spot size on the realistic "
                          "geometry, time the gather and the FFT form per EM iteration, write "
@@ -661,6 +666,70 @@ def autograd_form(args, flush, stream, k=10):
             "grad_entries": int(info["nnz"])}
 
 
+# Table 1 of the paper: WBH + EM + P4000 reconstruction times in seconds, by
+# (w, K) (Quadro P4000, FP32 FFT form; context only: other hardware, and the
+# paper's calibration matrix is not available, so the PSF here is synthetic)
+PAPER_TABLE1_P4000_S = {
+    (75, 3100): 467.2, (75, 50): 7.5, (75, 33): 5.0, (75, 25): 3.8, (75, 10): 1.5,
+    (24, 3100): 153.2, (24, 50): 2.5, (24, 33): 1.6, (24, 25): 1.2, (24, 10): 0.5,
+    (3, 3100): 24.0, (3, 50): 0.4, (3, 33): 0.3, (3, 25): 0.2, (3, 10): 0.08,
+}
+
+
+def run_paper_table(args, fft_max_k=33):
+    """The paper's Table 1 grid on GB300: its field stop (89x80), FPA
+    (2048x2048) and wavelength counts (3, 24, 75), with a synthetic CTIS PSF
+    (5x5 orders, pitch 360, dispersion 2 px per wavelength, 3x3 spots: 225
+    nonzeros per image) standing in for the unavailable calibration matrix.
+    Per (w, K): seconds for K EM updates with statistics through the gather
+    path (autotuned; one timed run after a warm-up, L2 flushed), and through
+    the FFT form for K <= fft_max_k, beside the paper's P4000 time."""
+    import torch
+    import synth
+    from paper_2006_01573_gb300 import Plan
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    rows = []
+    for w in (3, 24, 75):
+        wl = synth.Workload(f"paper_89x80x{w}_fpa2048", 89, 80, w, 2048, 2048, 5, 360.0, 2.0, 3,
+                            0.8, "segmentation", 4000.0, 10)
+        psf = synth.make_psf(wl)
+        plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+        hf = plan.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
+        gen = torch.Generator(device="cuda").manual_seed(wl.seed)
+        g = torch.poisson(hf * (wl.peak / hf.max()), generator=gen)
+        plan.autotune(g)
+        f = torch.empty((wl.w, wl.alpha, wl.a), device="cuda")
+        ff = torch.empty_like(f)
+        for K in (10, 25, 33, 50, 3100):
+            st = torch.empty((K + 1, 4), device="cuda", dtype=torch.float64)
+            run = lambda: plan.reconstruct(g, K, f=f, init="ones", stats=st)
+            run()
+            torch.cuda.synchronize()
+            t_g = _timed_steps(run, 1, flush, stream) / 1e3
+            row = {"w": w, "K": K, "gather_s": t_g, "gather_it_per_s": K / t_g,
+                   "paper_p4000_s": PAPER_TABLE1_P4000_S[(w, K)]}
+            if K <= fft_max_k:
+                fft = lambda: plan.fft_reconstruct(g, K, f=ff.fill_(1.0))
+                fft()
+                torch.cuda.synchronize()
+                row["fft_s"] = _timed_steps(fft, 1, flush, stream) / 1e3
+            rows.append(row)
+        plan.check()
+        plan.close()
+        torch.cuda.empty_cache()
+    out = {"geometry": "field stop 89x80, FPA 2048x2048 (the paper's); synthetic PSF: 5x5 orders, "
+                       "pitch 360, dispersion 2, 3x3 spots (225 nonzeros per image)",
+           "paper": "Table 1, WBH + EM on a Quadro P4000 (FP32 FFT form), context only",
+           "rows": rows}
+    with open(args.paper_table, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps({"points": [(r["w"], r["K"], round(r["gather_s"], 4), r.get("fft_s") and
+                                  round(r["fft_s"], 3), r["paper_p4000_s"]) for r in rows]}),
+          flush=True)
+
+
 CROSSOVER_SPOTS = (3, 5, 7, 9, 11, 13, 15, 17, 21)
 
 
@@ -737,6 +806,9 @@ def main():
     import synth
     if args.crossover:
         run_crossover(args)
+        return
+    if args.paper_table:
+        run_paper_table(args)
         return
     wl = synth.WORKLOADS[args.workload]
     k = args.k if args.k is not None else wl.k
