@@ -1046,6 +1046,12 @@ int check_plan(const ctis_plan* P) {
     return CTIS_OK;
 }
 
+// L2 sector promotion of the window maps' loads (a build-time option; the
+// default was kept after measuring the others on the realistic workload)
+#ifndef CTIS_TMA_L2_PROMOTION
+#define CTIS_TMA_L2_PROMOTION CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+#endif
+
 int make_map(CUtensorMap* map, const void* base, int dtype, int width, int height, int depth,
              int64_t pitch, int64_t plane, int box_w, int box_h) {
     EncodeFn fn = encode_fn();
@@ -1060,7 +1066,7 @@ int make_map(CUtensorMap* map, const void* base, int dtype, int width, int heigh
                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                           3, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          CTIS_TMA_L2_PROMOTION, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(CTIS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for %dx%dx%d box %dx%d",
                     (int)r, width, height, depth, box_w, box_h);
