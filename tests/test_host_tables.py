@@ -280,3 +280,36 @@ def test_wrap_needs_every_nonzero_on_the_fpa():
                            boundary="wrap")
     with pytest.raises(CtisError):   # and the reject rule refuses the copies past the edges
         tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, (ptr, x, y, v), True, 8)
+
+
+@pytest.mark.parametrize("seed", range(30))
+@pytest.mark.parametrize("forward", [True, False], ids=["fwd", "adj"])
+def test_random_wrap_tables_are_the_clip_tables_of_the_images(seed, forward):
+    """Random small geometries, including a field stop as wide or as tall as
+    the FPA and nonzeros in the last column and row: the wrap plan's lists are
+    the clip plan's lists of the images that meet the FPA."""
+    rng = np.random.default_rng(7000 + seed)
+    a, al = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    ga = a + int(rng.integers(0, 3)) * int(rng.integers(0, 40))
+    xi = al + int(rng.integers(0, 3)) * int(rng.integers(0, 40))
+    w = int(rng.integers(1, 4))
+    wl = synth.Workload("r", a, al, w, ga, xi, 1, 0.0, 0.0, 1, 1.0, "mask_spectra", 1.0, 1)
+    ptr, xs, ys, vs = [0], [], [], []
+    for _ in range(w):
+        n = int(rng.integers(0, 12))
+        xs += rng.integers(0, ga, n).tolist()
+        ys += rng.integers(0, xi, n).tolist()
+        vs += rng.uniform(0.1, 1.0, n).tolist()
+        ptr.append(len(xs))
+    xs.append(ga - 1)                                   # the last pixel, in the last wavelength
+    ys.append(xi - 1)
+    vs.append(0.5)
+    ptr[-1] += 1
+    psf = (np.array(ptr, np.int32), np.array(xs, np.int32), np.array(ys, np.int32),
+           np.array(vs, np.float32))
+    tw = tables_inspect(a, al, w, ga, xi, psf, forward, 6, boundary="wrap")
+    tc = tables_inspect(a, al, w, ga, xi, _images_meeting_the_fpa(wl, psf), forward, 6,
+                        boundary="clip")
+    for key, val in tc.items():
+        assert np.array_equal(np.asarray(tw[key]), np.asarray(val)), key
+    _check_schedule(tw)
