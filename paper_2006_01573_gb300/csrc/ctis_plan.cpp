@@ -865,12 +865,16 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
         for (int64_t c = 0; c < ncl; ++c) {
             const Cluster& cl = P->clusters[c];
-            // the footprint's tiles on the FPA (under clipping it may reach
-            // past any edge, or miss the FPA altogether)
-            const int64_t tx0 = std::max<int64_t>(0, floor_div(cl.X, TX));
-            const int64_t tx1 = std::min<int64_t>(ntx - 1, floor_div(int64_t{cl.X} + fw - 1, TX));
-            const int64_t ty0 = std::max<int64_t>(0, floor_div(cl.Y, TY));
-            const int64_t ty1 = std::min<int64_t>(nty - 1, floor_div(int64_t{cl.Y} + fh - 1, TY));
+            // the tiles that the footprint's part on the FPA meets (under
+            // clipping the footprint may reach past any edge, or miss the FPA
+            // altogether; a cluster box may also reach past its last tap)
+            const int64_t fx0 = std::max<int64_t>(0, cl.X);
+            const int64_t fx1 = std::min<int64_t>(ga, int64_t{cl.X} + fw);
+            const int64_t fy0 = std::max<int64_t>(0, cl.Y);
+            const int64_t fy1 = std::min<int64_t>(xi, int64_t{cl.Y} + fh);
+            if (fx0 >= fx1 || fy0 >= fy1) continue;
+            const int64_t tx0 = fx0 / TX, tx1 = (fx1 - 1) / TX;
+            const int64_t ty0 = fy0 / TY, ty1 = (fy1 - 1) / TY;
             for (int64_t ty = ty0; ty <= ty1; ++ty)
                 for (int64_t tx = tx0; tx <= tx1; ++tx)
                     per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));

@@ -76,8 +76,11 @@ def test_forward_tasks_are_the_footprint_overlaps(case):
     K, TW, TH = t["cluster_k"], t["tile_w"], t["tile_h"]
     expect = {}
     for c, (s, X, Y) in enumerate(t["cluster_sxy"]):
-        x0, x1 = X, X + wl.a + K - 1          # footprint [x0, x1) x [y0, y1)
-        y0, y1 = Y, Y + wl.alpha + K - 1
+        # the footprint's part on the FPA: [x0, x1) x [y0, y1)
+        x0, x1 = max(X, 0), min(X + wl.a + K - 1, wl.gamma)
+        y0, y1 = max(Y, 0), min(Y + wl.alpha + K - 1, wl.xi)
+        if x0 >= x1 or y0 >= y1:
+            continue
         for ty in range(0, wl.xi, TH):
             for tx in range(0, wl.gamma, TW):
                 if tx < x1 and x0 < tx + TW and ty < y1 and y0 < ty + TH:
@@ -313,3 +316,67 @@ def test_random_wrap_tables_are_the_clip_tables_of_the_images(seed, forward):
     for key, val in tc.items():
         assert np.array_equal(np.asarray(tw[key]), np.asarray(val)), key
     _check_schedule(tw)
+
+
+def _random_case(seed, boundary):
+    rng = np.random.default_rng(8000 + seed)
+    a, al = int(rng.integers(1, 50)), int(rng.integers(1, 50))
+    ga, xi = a + int(rng.integers(0, 90)), al + int(rng.integers(0, 90))
+    w = int(rng.integers(1, 4))
+    wl = synth.Workload("r", a, al, w, ga, xi, 1, 0.0, 0.0, 1, 1.0, "mask_spectra", 1.0, 1)
+    ptr, xs, ys, vs = [0], [], [], []
+    for _ in range(w):
+        for _ in range(int(rng.integers(0, 4))):   # blobs of side 1..5
+            side = int(rng.integers(1, 6))
+            if boundary == "clip":
+                x0, y0 = int(rng.integers(-a - 6, ga + 2)), int(rng.integers(-al - 6, xi + 2))
+            else:
+                x0, y0 = int(rng.integers(0, ga - a + 1)), int(rng.integers(0, xi - al + 1))
+            for dy in range(side):
+                for dx in range(side):
+                    x, y = x0 + dx, y0 + dy
+                    if boundary == "reject" and (x + a > ga or y + al > xi):
+                        continue
+                    xs.append(x)
+                    ys.append(y)
+                    vs.append(float(rng.uniform(0.1, 1.0)))
+        ptr.append(len(xs))
+    psf = (np.array(ptr, np.int32), np.array(xs, np.int32), np.array(ys, np.int32),
+           np.array(vs, np.float32))
+    return wl, psf
+
+
+@pytest.mark.parametrize("seed", range(20))
+@pytest.mark.parametrize("boundary", ["reject", "clip"])
+def test_random_work_lists_follow_their_definitions(seed, boundary):
+    """Random geometries and blob PSFs: forward tasks are exactly the
+    (tile, cluster) pairs whose footprint (its part on the FPA) meets the
+    tile; adjoint tiles list the clusters of their plane whose window meets
+    the FPA; every schedule runs every task once."""
+    wl, psf = _random_case(seed, boundary)
+    tf = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 6, boundary=boundary)
+    K, TW, TH = tf["cluster_k"], tf["tile_w"], tf["tile_h"]
+    expect = {}
+    for c, (s, X, Y) in enumerate(tf["cluster_sxy"]):
+        x0, x1 = max(X, 0), min(X + wl.a + K - 1, wl.gamma)
+        y0, y1 = max(Y, 0), min(Y + wl.alpha + K - 1, wl.xi)
+        for ty in range(0, wl.xi, TH):
+            for tx in range(0, wl.gamma, TW):
+                if x0 < x1 and y0 < y1 and tx < x1 and x0 < tx + TW and ty < y1 and y0 < ty + TH:
+                    expect.setdefault((tx, ty, 0), []).append(c)
+    assert _tile_tasks(tf) == {k: sorted(v) for k, v in expect.items()}
+    _check_schedule(tf)
+    ta = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, False, 6, boundary=boundary)
+    TW, TH = ta["tile_w"], ta["tile_h"]
+    cl = ta["cluster_sxy"]
+    expect = {}
+    for s in range(wl.w):
+        for ty in range(0, wl.alpha, TH):
+            for tx in range(0, wl.a, TW):
+                expect[(tx, ty, s)] = sorted(
+                    c for c in np.nonzero(cl[:, 0] == s)[0].tolist()
+                    if boundary == "reject" or (cl[c, 1] + tx < wl.gamma and cl[c, 2] + ty < wl.xi and
+                                                cl[c, 1] + tx + TW + K - 1 > 0 and
+                                                cl[c, 2] + ty + TH + K - 1 > 0))
+    assert _tile_tasks(ta) == expect
+    _check_schedule(ta)
