@@ -96,3 +96,16 @@ def test_header_compiles_as_c_and_a_c_caller_links(lib, tmp_path):
     # each wavelength's two nonzeros are 8-connected: one 3 x 3 cluster each;
     # a 6 x 5 footprint on a 10 x 9 FPA meets at least one 32 x 32 tile
     assert first[:4] == ["clusters", "2", "k", "3"] and int(first[5]) >= 1 and int(first[7]) >= 2
+
+
+def test_header_constants_match_the_binding():
+    """The enum values the header declares are the ones the binding passes."""
+    text = open(HEADER).read()
+    consts = {name: int(val) for name, val in re.findall(r"\b(CTIS_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    for name in ("CTIS_F32", "CTIS_BF16", "CTIS_BOUNDARY_REJECT", "CTIS_BOUNDARY_CLIP",
+                 "CTIS_BOUNDARY_WRAP", "CTIS_SOLVER_EM", "CTIS_SOLVER_SART", "CTIS_SOLVER_SMART",
+                 "CTIS_INIT_ONES", "CTIS_INIT_HTG"):
+        assert consts[name] == getattr(_native, name), name
+    assert consts["CTIS_NSTATS"] == _native.NSTATS
+    assert consts["CTIS_DEBUG_DROP_COPIES"] == 1
+    assert consts["CTIS_ERR_TIMEOUT"] == -5 and consts["CTIS_ERR_UNSUPPORTED"] == -6
