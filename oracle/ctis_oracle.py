@@ -269,6 +269,12 @@ def stats(q: np.ndarray, g: np.ndarray) -> dict:
     ``q_i = 0`` are left out of every sum here (they add ``-q_i = 0`` when
     ``g_i = 0``; a pixel with ``g_i > 0 = q_i`` would make the full likelihood
     ``-inf``, which no measurement generated by H can produce).
+
+    ``resid2 = sum (g_i - q_i)^2`` over the same support is a diagnostic, not
+    a term of Eq. 2: off the support ``q_i = 0`` for every iterate, so the
+    residual there is the data's own ``sum g_i^2``, a constant that says
+    nothing about f; the statistic keeps the part that depends on f. Pinned
+    by a hand-worked example that has a ``g > 0`` pixel off the support.
     """
     q = np.asarray(q, dtype=np.float64).ravel()
     g = np.asarray(g, dtype=np.float64).ravel()

@@ -210,6 +210,9 @@ class Plan:
                                        self.dtype, ctypes.byref(opt)))
         self._h = handle
         self.a, self.alpha, self.w, self.gamma, self.xi = a, alpha, w, gamma, xi
+        # bumped by every set_values: tells a pending autograd backward whether
+        # the plan still holds the tap values its forward projected with
+        self.values_version = 0
 
     # -- lifetime ---------------------------------------------------------------
     def close(self):
@@ -434,6 +437,7 @@ class Plan:
             raise ValueError(f"expected {self.nnz} tap values, got {v.size}")
         keep, ptr = _arr(v, np.float32)
         _check(load().ctis_plan_set_values(self._h, ptr))
+        self.values_version += 1
 
     def psf_grad(self, f, r, out=None, stream=None):
         """``d <r, H f> / d v_t`` for every stored tap t (float32, nnz)."""

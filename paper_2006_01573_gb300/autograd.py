@@ -10,7 +10,9 @@ marshalling only: every projection and gradient runs in libctis).
   checkpointed iterates.
 
 Both load the given values into the plan (``Plan.set_values``) before they
-project, so one plan serves a whole optimisation of the PSF values.
+project, so one plan serves a whole optimisation of the PSF values. Several
+live graphs may share one plan: a backward pass whose forward projected with
+other values than the plan now holds loads its own values again first.
 """
 from __future__ import annotations
 
@@ -26,13 +28,19 @@ class _Project(torch.autograd.Function):
     def forward(ctx, f, vals, plan):
         _load_values(plan, vals)
         ctx.plan = plan
-        ctx.save_for_backward(f)
+        ctx.version = plan.values_version
+        ctx.save_for_backward(f, vals.detach().clone())
         return plan.forward(f.contiguous())
 
     @staticmethod
     def backward(ctx, gy):
-        (f,) = ctx.saved_tensors
+        f, vals = ctx.saved_tensors
         plan = ctx.plan
+        if plan.values_version != ctx.version:
+            # another forward loaded other values since: the adjoint below
+            # must apply the H this forward used
+            _load_values(plan, vals)
+            ctx.version = plan.values_version
         gy = gy.contiguous().float()
         df = plan.adjoint(gy) if ctx.needs_input_grad[0] else None
         dv = plan.psf_grad(f.contiguous(), gy) if ctx.needs_input_grad[1] else None

@@ -134,6 +134,41 @@ def test_project_autograd_matches_adjoint_and_psf_grad():
     assert floored_rel(dv, O.psf_value_grad(geom, taps, f, gy)) <= TOL
 
 
+def test_two_live_projections_with_different_values_on_one_plan():
+    """Two project() calls on one plan with different tap values, both
+    pending when backward runs: each df must be H^T gy of its own values."""
+    wl = CASES["ragged"]
+    psf = synth.make_psf(wl)
+    geom = geometry(wl)
+    taps = O.merge_psf(geom, psf)
+    v2 = (taps.v * (1.0 + synth.random_positive(taps.v.size, 80))).astype(np.float32)
+    f = synth.random_positive((wl.w, wl.alpha, wl.a), 81)
+    gy1 = synth.random_positive((wl.xi, wl.gamma), 82)
+    gy2 = synth.random_positive((wl.xi, wl.gamma), 83)
+    with _plan(wl, psf) as plan:
+        f1 = torch.from_numpy(f).cuda().requires_grad_(True)
+        f2 = torch.from_numpy(f).cuda().requires_grad_(True)
+        out1 = project(plan, f1, torch.from_numpy(taps.v.astype(np.float32)).cuda())
+        out2 = project(plan, f2, torch.from_numpy(v2).cuda())
+        loss = (out1 * torch.from_numpy(gy1).cuda()).sum() + (out2 * torch.from_numpy(gy2).cuda()).sum()
+        loss.backward()
+        df1, df2 = f1.grad.cpu().numpy(), f2.grad.cpu().numpy()
+        # and the other order of the two backward passes
+        f1.grad, f2.grad = None, None
+        out1 = project(plan, f1, torch.from_numpy(taps.v.astype(np.float32)).cuda())
+        out2 = project(plan, f2, torch.from_numpy(v2).cuda())
+        (out2 * torch.from_numpy(gy2).cuda()).sum().backward()
+        (out1 * torch.from_numpy(gy1).cuda()).sum().backward()
+        df1b, df2b = f1.grad.cpu().numpy(), f2.grad.cpu().numpy()
+        plan.check()
+    H1 = O.BlockH(geom, taps)
+    H2 = O.BlockH(geom, O.with_values(taps, v2.astype(np.float64)))
+    for a, b in ((df1, df1b), (df2, df2b)):
+        assert np.array_equal(a, b)
+    assert floored_rel(df1, H1.adjoint(gy1.ravel())) <= TOL
+    assert floored_rel(df2, H2.adjoint(gy2.ravel())) <= TOL
+
+
 def _fd_grad(geom, taps, g, f0, k, idx, rel_eps=1e-4):
     """Central differences of the oracle's float64 unrolled NLL in tap values."""
     out = np.zeros(len(idx))

@@ -56,6 +56,69 @@ def test_golden_projector_and_em_step():
     assert np.allclose(f2, np.array(em["f2_r_p"]).ravel(), rtol=0, atol=1e-15)
 
 
+def _golden_stats_case():
+    gold = json.load(open(os.path.join(GOLDEN, "hand_worked_a2_alpha2_gamma4_xi3.json")))["projector"]
+    q = np.array(gold["hf_y_x"], dtype=np.float64).ravel()
+    st = gold["stats"]
+    g = np.array(st["g_y_x"], dtype=np.float64).ravel()
+    c2, c3, c0 = st["loglik_ln2_ln3_const"]
+    want = {"flux_hf": st["flux_hf"], "flux_g_covered": st["flux_g_covered"],
+            "loglik": c2 * np.log(2.0) + c3 * np.log(3.0) + c0, "resid2": st["resid2"]}
+    return q, g, want
+
+
+def _matches_golden(got, want):
+    return all(abs(got[k] - want[k]) <= 1e-14 * max(1.0, abs(want[k])) for k in want)
+
+
+def test_golden_statistics():
+    """stats() against the hand-worked sums of Eq. 2's likelihood over the
+    support of H f, with a g > 0 pixel off the support and a g = 0 pixel on it."""
+    gold = json.load(open(os.path.join(GOLDEN, "hand_worked_a2_alpha2_gamma4_xi3.json")))["projector"]
+    p = gold["psf"]
+    geom = _geom(2, 2, 1, 4, 3)
+    psf = (np.array(p["ptr"]), np.array(p["x"]), np.array(p["y"]), np.array(p["val"], np.float32))
+    H = O.build_H(geom, psf)
+    q, g, want = _golden_stats_case()
+    assert np.array_equal(H.forward(np.array(gold["f_r_p"]).ravel()), q)
+    assert _matches_golden(O.stats(q, g), want)
+
+
+def _mutant_stats(q, g, kind):
+    """stats() with one plausible mistake planted."""
+    pos = q > 0
+    out = dict(O.stats(q, g))
+    if kind == "all_pixels_resid":      # residual over every pixel, not the support
+        out["resid2"] = float(np.sum((g - q) ** 2))
+    elif kind == "all_pixels_flux_g":   # covered flux over every pixel
+        out["flux_g_covered"] = float(g.sum())
+    elif kind == "unsquared_resid":
+        out["resid2"] = float(np.sum(np.abs(g[pos] - q[pos])))
+    elif kind == "resid_sign_dropped":  # (g + q)^2
+        out["resid2"] = float(np.sum((g[pos] + q[pos]) ** 2))
+    elif kind == "log10":
+        out["loglik"] = float(np.sum(g[pos] * np.log10(q[pos])) - q[pos].sum())
+    elif kind == "missing_q_term":
+        out["loglik"] = float(np.sum(g[pos] * np.log(q[pos])))
+    elif kind == "g_zero_pixels_dropped":   # a g = 0 pixel still adds -q
+        on = pos & (g > 0)
+        out["loglik"] = float(np.sum(g[on] * np.log(q[on])) - q[on].sum())
+    elif kind == "flux_is_g":
+        out["flux_hf"] = float(g[pos].sum())
+    elif kind == "swapped_log_args":   # q log g - g
+        on = pos & (g > 0)
+        out["loglik"] = float(np.sum(q[on] * np.log(g[on])) - g[pos].sum())
+    return out
+
+
+@pytest.mark.parametrize("kind", ["all_pixels_resid", "all_pixels_flux_g", "unsquared_resid",
+                                  "resid_sign_dropped", "log10", "missing_q_term",
+                                  "g_zero_pixels_dropped", "flux_is_g", "swapped_log_args"])
+def test_planted_statistics_mistakes_are_caught_by_golden_pin(kind):
+    q, g, want = _golden_stats_case()
+    assert not _matches_golden(_mutant_stats(q, g, kind), want)
+
+
 # --- index map and E ------------------------------------------------------------
 
 @pytest.mark.parametrize("dims", [(2, 2, 2, 4, 3), (3, 2, 3, 5, 4), (4, 3, 2, 7, 6), (1, 1, 1, 1, 1)])
