@@ -34,3 +34,22 @@ def test_paper_table1_figures():
     t = bench.PAPER_TABLE1_P4000_S
     assert len(t) == 15 and {w for w, _ in t} == {3, 24, 75}
     assert t[(75, 3100)] == 467.2 and t[(3, 10)] == 0.08 and t[(24, 33)] == 1.6
+
+
+def test_reference_arm_reports_the_work_it_ran():
+    """--impl reference: every step is one full-size oracle EM iteration, so
+    steps x ms_per_step is the timed work, and its config has exactly the keys
+    and values the repo arm prints for the workload."""
+    import subprocess
+    import sys
+    import synth
+    wl = synth.TINY
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", wl.name, "--steps", "3", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1
+    assert abs(line["value"] - 1e3 / line["ms_per_step"]) <= 1e-9 * line["value"]
+    assert line["config"] == bench.bench_config(wl, wl.k, 1)
+    assert line["e2e"]["value"] == line["value"] and line["cpu_baseline"]["value"] == line["value"]
