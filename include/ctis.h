@@ -270,7 +270,7 @@ int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, do
                            int* n_adj);
 
 /* H f like ctis_forward, but with the projection's scratch (the x-shifted
- * copies of f, chunk partial sums, tile tickets and counters) taken from a
+ * copies of f, chunk partial sums and tile tickets) taken from a
  * fixed array inside the library instead of the plan's workspace. The paper
  * has no counterpart; this exists for callers that cannot call cudaMalloc
  * when they project (allocation-free real-time loops, code whose device
@@ -288,8 +288,8 @@ int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, do
  *     call's contents (each call clears what must start at zero). Calls whose
  *     executions overlap on the GPU (other streams, other threads, other
  *     plans) race on it: serialise them.
- *   - A device-side wait that gives up is not reported by ctis_plan_check
- *     for this call. */
+ *   - A device-side wait that gives up is reported by ctis_plan_check, as
+ *     for ctis_forward (the error flag is the plan's own). */
 #define CTIS_STATIC_SCRATCH_BYTES (64u << 20)
 int ctis_forward_static_scratch(const ctis_plan* plan, const void* f_dev, float* hf_dev,
                                 void* stream);

@@ -27,7 +27,7 @@
 //    padding of the forward projector;
 //  * each lane keeps an R x C block of outputs in registers and slides down
 //    the window one input row at a time, so every staged value feeds up to
-//    K*K packed FMAs;
+//    K*K FMAs;
 //  * epilogues are fused and selected at compile time: the EM ratio
 //    u = g / (H f) with float64 statistics, and the multiplicative update
 //    f <- f * (H^T u) / h.
@@ -260,34 +260,33 @@ __device__ __forceinline__ void load_row_elems(const TIn* rowp, float (&raw)[G::
 // acc[o][c] += sum_{dy,dx} w[dy][dx] * win[o + dy][c + dx]
 // `win` points at this lane's first element (window row ty*R, column tx*C).
 // Windows are chunk-aligned (shifted copies), so each row is a few aligned
-// loads (load_row_elems); the even-offset operand pairs of the packed FMAs
-// come straight from them and the odd-offset pairs are formed once per row.
+// loads (load_row_elems). The multiply-adds are scalar FFMAs: packed FFMA2
+// pairs would need the odd-offset operand pairs rebuilt in registers every
+// row, and on this part the packed form does not raise the FMA pipe's rate
+// (a measured correlation loop ran at 0.71 of the FP32 peak with scalar
+// FFMAs against 0.63 with FFMA2). Both round each product-sum once, so the
+// results are the same bit for bit. acc is kept as float2 pairs (c, c+1)
+// for the item-end code.
 template <class G, typename TIn>
 __device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const TIn* win,
                                           const float2 (&w2)[G::K * G::K]) {
     constexpr int K = G::K, C = G::C, R = G::R;
-    constexpr int NE = C + K - 1;                 // elements used per row (even)
-    constexpr int NP = NE / 2;                    // even-offset pairs
+    constexpr int NE = C + K - 1;                 // elements used per row
 #pragma unroll
     for (int i = 0; i < R + K - 1; ++i) {
         float raw[NE];
         load_row_elems<G, TIn>(win + i * G::BXW, raw);
-        float2 ev[NP], od[NP - 1];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
-#pragma unroll
-        for (int k = 0; k + 1 < NP; ++k) od[k] = make_float2(raw[2 * k + 1], raw[2 * k + 2]);
 #pragma unroll
         for (int dx = 0; dx < K; ++dx) {
 #pragma unroll
             for (int dy = 0; dy < K; ++dy) {
                 const int o = i - dy;
                 if (o >= 0 && o < R) {
+                    const float wv = w2[dy * K + dx].x;
 #pragma unroll
                     for (int c2 = 0; c2 < C / 2; ++c2) {
-                        // outputs (2c2, 2c2+1) need elements 2c2+dx, 2c2+dx+1
-                        const float2 x2 = (dx & 1) ? od[c2 + dx / 2] : ev[c2 + dx / 2];
-                        acc[o][c2] = __ffma2_rn(x2, w2[dy * K + dx], acc[o][c2]);
+                        acc[o][c2].x = fmaf(raw[2 * c2 + dx], wv, acc[o][c2].x);
+                        acc[o][c2].y = fmaf(raw[2 * c2 + 1 + dx], wv, acc[o][c2].y);
                     }
                 }
             }
@@ -305,16 +304,10 @@ __device__ __forceinline__ void correlate_grad(float2 (&acc)[G::K * G::K], const
                                                const float2 (&fp)[G::R][G::C / 2]) {
     constexpr int K = G::K, C = G::C, R = G::R;
     constexpr int NE = C + K - 1;
-    constexpr int NP = NE / 2;
 #pragma unroll
     for (int i = 0; i < R + K - 1; ++i) {
         float raw[NE];
         load_row_elems<G, TIn>(win + i * G::BXW, raw);
-        float2 ev[NP], od[NP - 1];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) ev[k] = make_float2(raw[2 * k], raw[2 * k + 1]);
-#pragma unroll
-        for (int k = 0; k + 1 < NP; ++k) od[k] = make_float2(raw[2 * k + 1], raw[2 * k + 2]);
 #pragma unroll
         for (int dx = 0; dx < K; ++dx) {
 #pragma unroll
@@ -323,8 +316,8 @@ __device__ __forceinline__ void correlate_grad(float2 (&acc)[G::K * G::K], const
                 if (o >= 0 && o < R) {
 #pragma unroll
                     for (int c2 = 0; c2 < C / 2; ++c2) {
-                        const float2 x2 = (dx & 1) ? od[c2 + dx / 2] : ev[c2 + dx / 2];
-                        acc[dy * K + dx] = __ffma2_rn(x2, fp[o][c2], acc[dy * K + dx]);
+                        acc[dy * K + dx].x = fmaf(raw[2 * c2 + dx], fp[o][c2].x, acc[dy * K + dx].x);
+                        acc[dy * K + dx].y = fmaf(raw[2 * c2 + 1 + dx], fp[o][c2].y, acc[dy * K + dx].y);
                     }
                 }
             }

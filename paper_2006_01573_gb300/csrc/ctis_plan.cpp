@@ -2264,8 +2264,9 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     int rc = check_plan(P);
     if (rc) return rc;
     if (!f_dev || !hf_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
-    // Pieces of the static array, each 256-byte aligned: counters, tile
-    // tickets, chunk partial sums, the x-shifted copies of f.
+    // Pieces of the static array, each 256-byte aligned: tile tickets, chunk
+    // partial sums, the x-shifted copies of f. The bounded waits' error flag
+    // stays the plan's own (ctis_plan_check reports it).
     const size_t es = P->dtype == kDtypeBF16 ? 2 : 4;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -2273,7 +2274,6 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
         off = static_cast<size_t>(round_up(static_cast<int64_t>(off + bytes), 256));
         return o;
     };
-    const size_t o_counters = take(8 * sizeof(int));
     const size_t o_tickets = take(P->fwd.tiles.size() * sizeof(int));
     const size_t o_partials = take(sizeof(float) * static_cast<size_t>(P->fwd.scratch_slots) *
                                    P->fwd.tile_w * P->fwd.tile_h);
@@ -2288,10 +2288,24 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     CTIS_CUDA(static_scratch_ptr(&base_v));
     unsigned char* base = static_cast<unsigned char*>(base_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // The array keeps the previous call's contents: counters and tickets must
-    // start at zero, and so must the copies (their unwritten ends are read).
-    CTIS_CUDA(cudaMemsetAsync(base + o_counters, 0, o_partials - o_counters, st));
-    CTIS_CUDA(cudaMemsetAsync(base + o_copies, 0, copies_bytes, st));
+    // The array keeps the previous call's contents. The tile tickets must
+    // start at zero (the kernel leaves them at zero, but a call whose waits
+    // gave up may not have), and so must the columns of each copy that the
+    // scatter below leaves unwritten and the window map still reads: copy q
+    // holds f at columns [q, a + q) of its rows, so [0, q) and the row's rest
+    // from a + q on are cleared (every row of a copy is a_pitch apart, across
+    // the planes too).
+    CTIS_CUDA(cudaMemsetAsync(base + o_tickets, 0, o_partials - o_tickets, st));
+    const size_t rows = static_cast<size_t>(P->alpha) * P->w;
+    const size_t pitch_b = es * static_cast<size_t>(P->a_pitch);
+    for (int q = 0; q < P->f_copies; ++q) {
+        unsigned char* cq = base + o_copies + es * static_cast<size_t>(P->f_copy_stride) * q;
+        if (q > 0) CTIS_CUDA(cudaMemset2DAsync(cq, pitch_b, 0, es * q, rows, st));
+        const size_t right = static_cast<size_t>(P->a_pitch - P->a - q);
+        if (right > 0)
+            CTIS_CUDA(cudaMemset2DAsync(cq + es * static_cast<size_t>(P->a + q), pitch_b, 0,
+                                        es * right, rows, st));
+    }
     void* copies = base + o_copies;
     const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
     CTIS_CUDA(launch_scatter_copies(P->dtype, copies, P->f_copy_stride, P->f_copies, P->a_pitch,
@@ -2306,7 +2320,6 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     GatherParams p = base_params(P, P->fwd);
     p.scratch = reinterpret_cast<float*>(base + o_partials);
     p.tickets = reinterpret_cast<int*>(base + o_tickets);
-    p.counters = reinterpret_cast<int*>(base + o_counters);
     p.tile_stats = nullptr;
     p.mode = kEpiRaw;
     p.out_w = P->gamma;
