@@ -48,7 +48,6 @@ def parse_args():
     ap.add_argument("--workload", default="realistic_128x128x64_fpa1024")
     ap.add_argument("--k", type=int, default=None, help="EM iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and autograd forms")
     ap.add_argument("--schedule", default=None,
                     help="skip the autotuner and use these schedules, 'FWD,ADJ' with each "
@@ -59,6 +58,9 @@ def parse_args():
                          "89x80, 2048x2048 FPA, w = 3, 24, 75, K = 10..3100) on a synthetic PSF, "
                          "gather and FFT-form reconstruction times beside the paper's P4000 "
                          "times; writes OUT_JSON and prints a one-line summary")
+    ap.add_argument("--fma-peak", action="store_true",
+                    help="instead of the bench line: the FP32 FMA-pipe microbenchmark alone "
+                         "(one JSON line)")
     ap.add_argument("--crossover", default=None, metavar="OUT_JSON",
                     help="instead of the bench line: sweep the spot size on the realistic "
                          "geometry, time the gather and the FFT form per EM iteration, write "
@@ -175,6 +177,21 @@ def ncu_traffic(kernel: str, workload: str, units_scale: float = 1.0):
     return None if entry is None else entry["dram_bytes_per_launch"] * units_scale
 
 
+def measure_fma_peak():
+    """The FP32 FMA-pipe microbenchmark (ctis_fma_peak): TFLOP/s with scalar
+    FFMA and with FFMA2 pairs, at 64 warps per SM and at the projectors' 16."""
+    from paper_2006_01573_gb300 import fma_peak
+    out = {}
+    for packed in (False, True):
+        for bps, thr in ((8, 256), (4, 128)):
+            key = f"{'ffma2' if packed else 'ffma'}_{bps * thr // 32}_warps_per_sm"
+            out[key] = fma_peak(packed=packed, blocks_per_sm=bps, threads=thr)
+    out["best_tflops"] = max(out.values())
+    out["nominal_tflops"] = FP32_PEAK_TFLOPS
+    out["kernel"] = "ctis_fma_peak: 8 independent chains x 4 FMAs per iteration per thread"
+    return out
+
+
 def problem(wl, seed):
     import numpy as np  # noqa: F401
     import synth
@@ -220,18 +237,50 @@ def oracle_iterations(wl, n_iter: int):
     return secs
 
 
-def oracle_baseline(wl, budget_s: float):
-    """The cpu_baseline leg: full-size oracle EM iterations for about
-    budget_s seconds (at least 2), one host thread."""
-    _, _, _, build_s = oracle_problem(wl)
-    secs = oracle_iterations(wl, 1)
-    n = max(2, int(budget_s / max(secs[0], 1e-3)))
-    secs += oracle_iterations(wl, n - 1)
-    value = len(secs) / sum(secs)
-    desc = (f"{wl.name}: {len(secs)} full-size EM iterations of the float64 oracle (scipy CSR "
-            f"sparse H of every wavelength block, 1 thread) in {sum(secs):.1f} s, from ones; "
-            f"H built once in {build_s:.1f} s, not timed")
-    return value, len(secs), sum(secs), desc
+def oracle_reconstruction(wl, k: int):
+    """The benchmarked reconstruction done by the FP64 oracle: k EM updates
+    (Eq. 2) of the full workload from ones on the oracle's own measurement,
+    each timed. Returns (f, seconds per update, seconds to build H)."""
+    import numpy as np
+
+    import oracle as O
+    H, h, g, build_s = oracle_problem(wl)
+    f = np.ones(H.geom.m)
+    secs = []
+    for _ in range(k):
+        t0 = time.perf_counter()
+        f = O.em_update(f, H.adjoint(O.ratio(g, H.forward(f))), h)
+        secs.append(time.perf_counter() - t0)
+    return f, secs, build_s
+
+
+def accuracy_vs_oracle(wl, k, f_ref):
+    """The GPU reconstruction of the benchmarked workload against the FP64
+    oracle's (same input: the oracle's measurement), for the float32 plan and
+    the bfloat16-storage plan, both autotuned as in the timed runs: max
+    floored-relative error (floor 1e-6 of the maximum) and relative L2 over
+    every voxel after k updates from ones."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2006_01573_gb300 import Plan
+    _, _, g, _ = oracle_problem(wl)
+    gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma).astype(np.float32)).cuda()
+    out = {}
+    for dtype in ("f32", "bf16"):
+        plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), dtype=dtype)
+        plan.autotune(gt)
+        f, _ = plan.reconstruct(gt, k, init="ones")
+        plan.check()
+        a = f.double().cpu().numpy().ravel()
+        plan.close()
+        floor = 1e-6 * np.abs(f_ref).max()
+        out[dtype] = {"max_floored_rel": float(np.max(np.abs(a - f_ref) / np.maximum(np.abs(f_ref), floor))),
+                      "rel_l2": float(np.linalg.norm(a - f_ref) / np.linalg.norm(f_ref))}
+    out["reference"] = (f"float64 oracle, {k} EM updates from ones on every voxel of the "
+                        f"{wl.name} workload, the oracle's own noisy measurement")
+    return out
 
 
 def run_reference(args, wl, k):
@@ -286,6 +335,9 @@ def run_ours(args, wl, k):
     from paper_2006_01573_gb300 import Plan
 
     rank, world, local = dist_env()
+    # the batched form's oracle frames run in spawned workers meanwhile
+    oracle_job = (start_batched_oracle() if world == 1 and not args.no_forms and
+                  not args.no_cpu_baseline else None)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
@@ -398,17 +450,27 @@ def run_ours(args, wl, k):
     value, e2e_value, total_ms, total_e2e = aggregate_over_ranks(
         sum(step_ms), sum(e2e_ms), args.steps, k, world, dist, dev)
 
-    # ---- roofline of the dominant kernel (per-launch, from the timed steps)
+    # ---- roofline of the dominant kernel: its average device time per launch
+    # over back-to-back launches of that kernel alone (no event between the
+    # launches), L2 flushed first; the event pairs around every launch of the
+    # profiled steps above give the kernels' shares of a step
     nnz_h = info["nnz"] * wl.a * wl.alpha          # nonzeros of H = FMAs per projection
     flops = 2.0 * nnz_h
+    reps = 50
+    flush.fill_(0.5)
+    b2b = plan.time_launches(g, reps)
+    b2b_ms = {"forward": b2b[0], "adjoint": b2b[1]}
     kernels = {"forward": (fwd_ms, n_fwd), "adjoint": (adj_ms, n_adj)}
-    dom = max(kernels, key=lambda n: kernels[n][0])
-    avg_ms = kernels[dom][0] / max(1, kernels[dom][1])
+    dom = max(b2b_ms, key=lambda n: b2b_ms[n])
+    avg_ms = b2b_ms[dom]
     achieved = flops / (avg_ms * 1e-3) / 1e12
-    per_kernel = {n: {"launches": c, "avg_us": 1e3 * t / max(1, c),
-                      "tflops": flops / (t / max(1, c) * 1e-3) / 1e12 if c else None,
+    per_kernel = {n: {"launches_profiled": c,
+                      "avg_us_back_to_back": 1e3 * b2b_ms[n],
+                      "tflops_back_to_back": flops / (b2b_ms[n] * 1e-3) / 1e12,
+                      "avg_us_with_event_nodes": 1e3 * t / max(1, c),
                       "share_of_step": t / prof_ms if prof_ms else None}
                   for n, (t, c) in kernels.items()}
+    fma = measure_fma_peak() if rank == 0 else None
     if world > 1:
         per_kernel = {n: v for n, v in per_kernel.items()}   # rank 0's view
 
@@ -434,9 +496,13 @@ def run_ours(args, wl, k):
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": ncu_traffic(dom, wl.name),
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2070 MHz (max SM clock)",
-                     "timing": "CUDA event pair around every launch on its stream, over K steps "
-                               "run right after the timed region (same workload and L2 flush)",
+                     "measured_fma_peak": fma["best_tflops"],
+                     "frac_of_measured_fma_peak": achieved / fma["best_tflops"],
+                     "timing": f"CUDA events around {reps} back-to-back EM launches of the kernel "
+                               "(ctis_plan_time_launches, no event between launches), after the "
+                               "timed region on the same workload",
                      "algorithmic_flops_per_launch": flops},
+        "fma_peak": fma,
         "kernels": per_kernel,
         "e2e": {"value": e2e_value, "unit": "it/s",
                 "h2d_bytes_per_step": g_pin.numel() * 4,
@@ -451,14 +517,22 @@ def run_ours(args, wl, k):
                      "solvers": solver_forms(args, wl, k, plan, g, flush, stream, value)}
     if world == 1 and not args.no_forms:
         line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
-        line["forms"]["batched"] = batched_form(args, flush, stream)
+        line["forms"]["batched"] = batched_form(args, flush, stream, oracle_job=oracle_job)
         line["forms"]["large"] = large_form(args, flush, stream)
         line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
-        v, iters_cpu, el, desc = oracle_baseline(wl, args.cpu_budget)
+        f_ref, secs, build_s = oracle_reconstruction(wl, k)
+        v = len(secs) / sum(secs)
+        desc = (f"{wl.name}: the whole benchmarked reconstruction, {len(secs)} full-size EM "
+                f"updates of the float64 oracle (scipy CSR sparse H of every wavelength block, "
+                f"1 thread) in {sum(secs):.1f} s, from ones; H built once in {build_s:.1f} s, "
+                f"not timed")
         line["cpu_baseline"] = {"value": v, "unit": "it/s", "cores": 1, "kind": "oracle",
                                 "sample": desc, "host_cpus": os.cpu_count()}
+        line["accuracy_vs_fp64_oracle"] = accuracy_vs_oracle(wl, k, f_ref)
+        if "forms" in line and "bf16" in line["forms"]:
+            line["forms"]["bf16"]["vs_fp64_oracle_after_k"] = line["accuracy_vs_fp64_oracle"]["bf16"]
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -565,54 +639,120 @@ def _timed_steps(fn, steps, flush, stream):
     return total
 
 
-def batched_form(args, flush, stream, nframes=256, k=100):
+def _oracle_frame(args):
+    """One sampled frame of the batched form, done by the FP64 oracle (run in
+    a spawned worker process): the frame's scene imaged by the oracle, its
+    Poisson counts (seed 1000 + i), and k EM updates from ones."""
+    name, i, k = args
+    import numpy as np
+
+    import oracle as O
+    import synth
+    wl = synth.WORKLOADS[name]
+    geom = O.Geometry(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi)
+    H = O.build_H(geom, synth.make_psf(wl))
+    g, _ = synth.make_measurement(H.forward(synth.make_scene(wl, 1000 + (1000 + i) % 8).ravel()),
+                                  wl.peak, 1000 + i)
+    f, _ = O.mlem(H, g, k)
+    return i, np.asarray(g, dtype=np.float32), f
+
+
+# frames of the 256-frame mix whose error against the FP64 oracle is reported
+# (plan A when i % 4 != 3, plan B otherwise)
+BATCH_SAMPLE_FRAMES = (0, 1, 2, 4, 3, 7)
+
+
+def start_batched_oracle(k=100):
+    """Starts the oracle's sampled frames in a spawned process pool (one
+    worker per frame); returns (pool, async result)."""
+    import multiprocessing as mp
+    import synth
+    jobs = [((synth.MODEL_B if i % 4 == 3 else synth.MODEL_A).name, i, k) for i in BATCH_SAMPLE_FRAMES]
+    pool = mp.get_context("spawn").Pool(len(jobs))
+    return pool, pool.map_async(_oracle_frame, jobs)
+
+
+def batched_form(args, flush, stream, nframes=256, k=100, oracle_job=None):
     """The batched form: 256 frames, 3:1 of the 64x64x32 -> 512^2 and the
     128x128x64 -> 1024^2 geometry, k EM iterations with per-frame statistics,
-    one ctis_reconstruct_batched call per step. Frame i: plan B when
-    i % 4 == 3, else A; scene (1000 + i) % 8 of its geometry (8 scenes each,
-    cycled), Poisson counts of H f scaled to the workload's peak drawn on the
-    GPU with seed 1000 + i."""
+    one ctis_reconstruct_batched call per step, timed with float32 and with
+    bfloat16 storage. Frame i: plan B when i % 4 == 3, else A; scene
+    (1000 + i) % 8 of its geometry (8 scenes each, cycled), Poisson counts of
+    H f scaled to the workload's peak drawn on the GPU with seed 1000 + i.
+    With oracle_job (start_batched_oracle): per-frame error against the FP64
+    oracle on the sampled frames, whose inputs are then the oracle's own
+    measurements (frames are bit-identical to their single-frame runs in any
+    batch, so the sample's errors are those of the same frames in the
+    256-frame batch)."""
+    import numpy as np
     import torch
     import synth
     from paper_2006_01573_gb300 import Plan, reconstruct_batched
     wls = [synth.MODEL_A, synth.MODEL_B]
-    plans = [Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl)) for wl in wls]
     plan_idx = [1 if i % 4 == 3 else 0 for i in range(nframes)]
-    scenes = [[torch.from_numpy(synth.make_scene(wl, 1000 + j)).cuda() for j in range(8)]
-              for wl in wls]
-    gs = []
-    for i, p in enumerate(plan_idx):
-        hf = plans[p].forward(scenes[p][(1000 + i) % 8])
-        gen = torch.Generator(device="cuda").manual_seed(1000 + i)
-        gs.append(torch.poisson(hf * (wls[p].peak / hf.max()), generator=gen))
-    del scenes
-    for p in range(len(plans)):                   # tune each plan on one of its frames
-        plans[p].autotune(gs[plan_idx.index(p)])
-    fs = [torch.empty((wls[p].w, wls[p].alpha, wls[p].a), device="cuda") for p in plan_idx]
-    stats = torch.empty((nframes, k + 1, 4), device="cuda", dtype=torch.float64)
+    out = {"frames": nframes, "mix": "192 x 64x64x32->512^2 + 64 x 128x128x64->1024^2", "k": k}
+    gs = None
+    for dtype in ("f32", "bf16"):
+        plans = [Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), dtype=dtype)
+                 for wl in wls]
+        if gs is None:
+            scenes = [[torch.from_numpy(synth.make_scene(wl, 1000 + j)).cuda() for j in range(8)]
+                      for wl in wls]
+            gs = []
+            for i, p in enumerate(plan_idx):
+                hf = plans[p].forward(scenes[p][(1000 + i) % 8].to(plans[p]._f_dtype()))
+                gen = torch.Generator(device="cuda").manual_seed(1000 + i)
+                gs.append(torch.poisson(hf * (wls[p].peak / hf.max()), generator=gen))
+            del scenes
+        for p in range(len(plans)):                   # tune each plan on one of its frames
+            plans[p].autotune(gs[plan_idx.index(p)])
+        tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+        fs = [torch.empty((wls[p].w, wls[p].alpha, wls[p].a), device="cuda", dtype=tdt)
+              for p in plan_idx]
+        stats = torch.empty((nframes, k + 1, 4), device="cuda", dtype=torch.float64)
 
-    def step():
-        reconstruct_batched(plans, plan_idx, gs, k, fs=fs, init="ones", stats=stats)
+        def step():
+            reconstruct_batched(plans, plan_idx, gs, k, fs=fs, init="ones", stats=stats)
 
-    for _ in range(max(1, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 3))
-    total = _timed_steps(step, steps, flush, stream)
-    for p in plans:
-        p.check()
-    voxels = sum(wls[p].m for p in plan_idx)
-    secs = total / 1e3
-    out = {"frames": nframes, "mix": "192 x 64x64x32->512^2 + 64 x 128x128x64->1024^2",
-           "k": k, "steps": steps, "ms_per_step": total / steps,
-           "frame_iterations_per_s": steps * nframes * k / secs,
-           "voxel_updates_per_s": steps * voxels * k / secs,
-           # per plan: g gather, f scatter, k + 1 forwards, k adjoints, f out, the last
-           # forward's statistics reduction, statistics rows
-           "launches_per_step": len(plans) * (2 * k + 6),
-           "data": "8 scenes per geometry cycled, per-frame Poisson noise on the GPU"}
-    for p in plans:
-        p.close()
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        steps = max(1, min(args.steps, 3))
+        total = _timed_steps(step, steps, flush, stream)
+        for p in plans:
+            p.check()
+        voxels = sum(wls[p].m for p in plan_idx)
+        secs = total / 1e3
+        out[dtype] = {"steps": steps, "ms_per_step": total / steps,
+                      "frame_iterations_per_s": steps * nframes * k / secs,
+                      "voxel_updates_per_s": steps * voxels * k / secs}
+        if oracle_job is not None:
+            res = oracle_job[1].get(timeout=900)
+            sub_idx = [plan_idx[i] for i, _, _ in res]
+            sub_g = [torch.from_numpy(g.reshape(wls[plan_idx[i]].xi, wls[plan_idx[i]].gamma)).cuda()
+                     for i, g, _ in res]
+            sub_f, _ = reconstruct_batched(plans, sub_idx, sub_g, k, init="ones")
+            per = {}
+            for (i, _, f_ref), f in zip(res, sub_f):
+                a = f.double().cpu().numpy().ravel()
+                floor = 1e-6 * np.abs(f_ref).max()
+                per[str(i)] = {"plan": "B" if plan_idx[i] else "A",
+                               "max_floored_rel": float(np.max(np.abs(a - f_ref) /
+                                                               np.maximum(np.abs(f_ref), floor))),
+                               "rel_l2": float(np.linalg.norm(a - f_ref) / np.linalg.norm(f_ref))}
+            out[dtype]["vs_fp64_oracle_sampled_frames"] = per
+        for p in plans:
+            p.close()
+        del fs, stats
+    out["bf16_vs_f32"] = out["bf16"]["frame_iterations_per_s"] / out["f32"]["frame_iterations_per_s"]
+    # per plan: g gather, f scatter, k + 1 forwards, k adjoints, f out, the last
+    # forward's statistics reduction, statistics rows
+    out["launches_per_step"] = len(wls) * (2 * k + 6)
+    out["data"] = ("8 scenes per geometry cycled, per-frame Poisson noise on the GPU; error "
+                   "sample: frames " + ", ".join(map(str, BATCH_SAMPLE_FRAMES)) +
+                   " with the oracle's own measurements, the oracle in a spawned process pool")
+    if oracle_job is not None:
+        oracle_job[0].close()
     return out
 
 
@@ -819,6 +959,11 @@ def run_crossover(args, spots=CROSSOVER_SPOTS, k_gather=20, k_fft=5):
 def main():
     args = parse_args()
     import synth
+    if args.fma_peak:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_fma_peak()), flush=True)
+        return
     if args.crossover:
         run_crossover(args)
         return

@@ -269,6 +269,59 @@ int ctis_plan_set_debug(ctis_plan* plan, int flags);
 int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,
                            int* n_adj);
 
+/* Wavelength-sharded EM reconstruction (Eqs. 2, 3 and 8). H f is the sum over
+ * wavelength blocks of H_s f_s, so the ranks of a job that each own a
+ * contiguous slice of the wavelengths can run one reconstruction together:
+ * every rank creates a plan for its slice alone (the slice's wavelengths,
+ * their calibration images, psf_ptr rebased to 0) and calls this with its
+ * part of the datacube. Each iteration, the rank forms its slice's partial
+ * image q_r = sum over its s of H_s f_s into a plan-owned device buffer of n
+ * float32 and calls reduce(q, n, reduce_ctx, stream), which must replace q,
+ * stream-ordered on `stream`, with the sum over the ranks (an all-reduce, for
+ * instance NCCL's on the caller's communicator; every rank must add in the
+ * same order so that all hold the same sum); then u = g / q (0 where q = 0)
+ * and the statistics of q, and the slice's adjoint and multiplicative update,
+ * are local. The reduction is the only exchange: n floats per iteration
+ * (k + 1 with statistics, the last for the final iterate). reduce may be
+ * NULL: the slice's own image is then the whole H f (a single rank with the
+ * whole datacube, or a test). g_dev (n float32, the whole measurement, on
+ * every rank), f_dev (the slice's datacube, m_slice elements of the plan's
+ * dtype; the initial guess unless CTIS_INIT_ONES), stats_dev (NULL or
+ * float64[(k + 1) * CTIS_NSTATS], identical on every rank) as in
+ * ctis_reconstruct (CTIS_INIT_HTG gives the slice's own columns of H^T g,
+ * local to the rank). Not captured in a CUDA graph (the callback runs on the
+ * host between launches); EM only. Returns what the launches return, or
+ * CTIS_ERR_CUDA when reduce returns nonzero. */
+typedef int (*ctis_reduce_fn)(float* q_dev, int64_t n, void* reduce_ctx, void* stream);
+int ctis_reconstruct_sharded(ctis_plan* plan, const float* g_dev, void* f_dev, int k, int flags,
+                             double* stats_dev, ctis_reduce_fn reduce, void* reduce_ctx,
+                             void* stream);
+
+/* Average device time of one EM launch of each projector, from CUDA events
+ * around `reps` back-to-back launches on `stream` (after two warm-up
+ * launches): the forward with the ratio epilogue and float64 tile statistics
+ * (g_dev the measurement, as in ctis_reconstruct), and the adjoint with the
+ * multiplicative update, on the plan's current schedules; milliseconds per
+ * launch in *fwd_ms and *adj_ms. No event sits between the launches, so the
+ * figures carry no event-record overhead (the profiled reconstruction's
+ * per-launch events of ctis_plan_kernel_times do). The plan's internal
+ * datacube and FPA copies are overwritten; no caller buffer is written.
+ * Synchronous. The paper has no counterpart (a measurement utility). */
+int ctis_plan_time_launches(ctis_plan* plan, const float* g_dev, int reps, double* fwd_ms,
+                            double* adj_ms, void* stream);
+
+/* FP32 FMA-pipe microbenchmark (the measured ceiling of the projectors'
+ * roofline; the paper has no counterpart): `blocks` CTAs of `threads`
+ * threads, each thread advancing 8 independent chains by 4 fused
+ * multiply-adds per iteration for `iters` iterations (scalar FFMA, or FFMA2
+ * pairs when `packed`): blocks * threads * iters * 32 FMAs (twice that when
+ * packed), 2 FLOP each. Writes one float per thread to out_dev (device,
+ * blocks * threads floats) so the chains are kept. Asynchronous on `stream`;
+ * the caller times it. Returns CTIS_ERR_INVALID_ARG for sizes out of range
+ * (threads a multiple of 32 in [32, 1024]), CTIS_ERR_CUDA if the launch
+ * fails. */
+int ctis_fma_peak(int packed, int blocks, int threads, int iters, float* out_dev, void* stream);
+
 /* H f like ctis_forward, but with the projection's scratch (the x-shifted
  * copies of f, chunk partial sums and tile tickets) taken from a
  * fixed array inside the library instead of the plan's workspace. The paper

@@ -46,6 +46,12 @@ are promoted exactly. Readings of points the paper leaves open:
 * duplicate PSF entries at one FPA position add up (H is a sum of responses);
 * ``k`` iterations means ``k`` EM updates from the initial guess.
 
+The shifted-sum projectors (:func:`forward_shifts`, :func:`adjoint_shifts`,
+:func:`mlem_shifts`, :func:`unrolled_nll_shifts`) apply the same H without
+building it (Sec. 2's columns pasted tap by tap), for the workloads whose
+sparse H would not fit in host memory; they are pinned to the sparse and
+dense forms.
+
 Pins (tests/test_oracle_*.py): every function here is checked against something
 other than itself - a dense H assembled literally from Eqs. 5-7, the FFT form of
 Eqs. 13/17 through numpy's FFT, the adjoint identity, 2-D convolution from SciPy
@@ -429,6 +435,74 @@ def adjoint_at(geom: Geometry, taps: Taps, u: np.ndarray, s_idx, ps, rs) -> np.n
     return out
 
 
+# --- whole projections as shifted sums (for problems too large for BlockH) ---
+
+def _paste(geom: Geometry, x: int, y: int):
+    """FPA rows/columns that the field stop shifted by tap (x, y) covers, and
+    the matching field-stop rows/columns (the parts off the FPA dropped, as
+    the clip reading does; under the reject reading nothing is dropped)."""
+    x0, x1 = max(x, 0), min(x + geom.a, geom.gamma)
+    y0, y1 = max(y, 0), min(y + geom.alpha, geom.xi)
+    if x0 >= x1 or y0 >= y1:   # the shifted field stop misses the FPA
+        return None
+    return (slice(y0, y1), slice(x0, x1)), (slice(y0 - y, y1 - y), slice(x0 - x, x1 - x))
+
+
+def forward_shifts(geom: Geometry, taps: Taps, f: np.ndarray) -> np.ndarray:
+    """``H f`` (Eq. 1) straight from Sec. 2's columns: every tap (x, y, v) of
+    wavelength s adds v times the field-stop image f_s pasted at (x, y). The
+    same operator as :class:`BlockH` without building the matrix (memory O(m
+    + n)), for the large workloads; the wrap reading is not supported."""
+    if taps.wrap:
+        raise ValueError("forward_shifts: the wrap reading needs BlockH")
+    f = np.asarray(f, dtype=np.float64).reshape(geom.w, geom.alpha, geom.a)
+    out = np.zeros((geom.xi, geom.gamma))
+    for s in range(geom.w):
+        for x, y, v in zip(*taps.of(s)):
+            cut = _paste(geom, int(x), int(y))
+            if cut is not None:
+                (fy, fx), (sy, sx) = cut
+                out[fy, fx] += v * f[s, sy, sx]
+    return out.ravel()
+
+
+def adjoint_shifts(geom: Geometry, taps: Taps, u: np.ndarray) -> np.ndarray:
+    """``H^T u`` as the transpose of :func:`forward_shifts`: voxel (p, r, s)
+    collects, for every tap (x, y, v) of s, v times u at (x + p, y + r)."""
+    if taps.wrap:
+        raise ValueError("adjoint_shifts: the wrap reading needs BlockH")
+    u = np.asarray(u, dtype=np.float64).reshape(geom.xi, geom.gamma)
+    out = np.zeros((geom.w, geom.alpha, geom.a))
+    for s in range(geom.w):
+        for x, y, v in zip(*taps.of(s)):
+            cut = _paste(geom, int(x), int(y))
+            if cut is not None:
+                (fy, fx), (sy, sx) = cut
+                out[s, sy, sx] += v * u[fy, fx]
+    return out.ravel()
+
+
+def h_shifts(geom: Geometry, taps: Taps) -> np.ndarray:
+    """``h = H^T 1`` (Eq. 2) through :func:`adjoint_shifts`."""
+    return adjoint_shifts(geom, taps, np.ones(geom.n))
+
+
+def mlem_shifts(geom: Geometry, taps: Taps, g: np.ndarray, k: int,
+                f0: np.ndarray | None = None):
+    """:func:`mlem` (Eq. 2, Algorithm 1's loop) with the shifted-sum
+    projectors. Returns ``(f, history)`` like :func:`mlem`."""
+    g64 = np.asarray(g, dtype=np.float64).ravel()
+    f = np.ones(geom.m) if f0 is None else np.asarray(f0, dtype=np.float64).ravel().copy()
+    h = h_shifts(geom, taps)
+    history = []
+    for _ in range(k):
+        q = forward_shifts(geom, taps, f)
+        history.append(stats(q, g64))
+        f = em_update(f, adjoint_shifts(geom, taps, ratio(g64, q)), h)
+    history.append(stats(forward_shifts(geom, taps, f), g64))
+    return f, history
+
+
 # --- the paper's own formulations, used as independent cross-checks ------------
 
 def dense_H(geom: Geometry, psf) -> np.ndarray:
@@ -553,6 +627,13 @@ def poisson_nll(q: np.ndarray, g: np.ndarray) -> float:
 
 def with_values(taps: Taps, v: np.ndarray) -> Taps:
     return Taps(taps.s, taps.x, taps.y, np.asarray(v, dtype=np.float64), taps.ptr, taps.wrap)
+
+
+def unrolled_nll_shifts(geom: Geometry, taps: Taps, g: np.ndarray, f0: np.ndarray, k: int) -> float:
+    """:func:`unrolled_nll` with the shifted-sum projectors (no matrix: for the
+    full-size workloads)."""
+    _, hist = mlem_shifts(geom, taps, g, k, f0)
+    return -hist[k]["loglik"]
 
 
 def unrolled_nll(geom: Geometry, taps: Taps, g: np.ndarray, f0: np.ndarray, k: int) -> float:

@@ -26,6 +26,10 @@ STAT_NAMES = ("flux_hf", "flux_g", "loglik", "resid2")
 
 _lib = None
 
+# int reduce(float* q_dev, int64_t n, void* ctx, void* stream) (ctis_reduce_fn)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_void_p)
+
 # Every symbol include/ctis.h declares, for the ABI export test.
 EXPORTED = (
     "ctis_plan_create", "ctis_plan_create_ex", "ctis_plan_destroy", "ctis_plan_get_info", "ctis_plan_export_taps",
@@ -34,8 +38,9 @@ EXPORTED = (
     "ctis_plan_set_values", "ctis_psf_grad", "ctis_unrolled_nll_grad", "ctis_reconstruct_batched",
     "ctis_plan_autotune", "ctis_plan_set_schedule", "ctis_tables_inspect",
     "ctis_fft_forward", "ctis_fft_adjoint", "ctis_fft_reconstruct", "ctis_reconstruct_solver",
-    "ctis_plan_set_debug", "ctis_reconstruct_batched_solver",
-    "ctis_status_string", "ctis_last_error",
+    "ctis_plan_set_debug", "ctis_reconstruct_batched_solver", "ctis_plan_time_launches",
+    "ctis_reconstruct_sharded",
+    "ctis_fma_peak", "ctis_status_string", "ctis_last_error",
 )
 
 
@@ -112,6 +117,10 @@ def load(path: str = LIB_PATH):
         "ctis_tables_inspect": (I, [I, I, I, I, I, i32p, i32p, i32p, f32p, I,
                                     ctypes.POINTER(PlanOptions), I, I, i32p,
                                     ctypes.POINTER(TablesInfo)] + [i32p] * 8),
+        "ctis_plan_time_launches": (I, [P, VP, I, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), VP]),
+        "ctis_fma_peak": (I, [I, I, I, I, VP, VP]),
+        "ctis_reconstruct_sharded": (I, [P, VP, VP, I, I, VP, REDUCE_FN, VP, VP]),
         "ctis_status_string": (ctypes.c_char_p, [I]),
         "ctis_last_error": (ctypes.c_char_p, []),
     }
@@ -352,6 +361,48 @@ class Plan:
                                              ctypes.byref(am), ctypes.byref(an)))
         return {"forward": (fm.value, fn.value), "adjoint": (am.value, an.value)}
 
+    def reconstruct_sharded(self, g, k: int, f=None, init: str = "ones", stats: bool = False,
+                            reduce=None, stream=None):
+        """k EM updates of this plan's wavelength slice (ctis_reconstruct_sharded):
+        ``reduce(q)`` gets the slice's partial image q (a CUDA float32 tensor
+        of the FPA's shape, a view of the plan's buffer) each iteration and
+        must leave the sum over the ranks in it, on the current stream; None:
+        the slice is the whole problem. Returns ``(f, stats or None)``."""
+        import torch
+        self._check_fpa(g)
+        if f is None:
+            f = torch.empty((self.w, self.alpha, self.a), device=g.device, dtype=self._f_dtype())
+        self._check_cube(f)
+        flags = {"ones": CTIS_INIT_ONES, "htg": CTIS_INIT_HTG, "given": 0}[init]
+        st = torch.empty((k + 1, NSTATS), device=g.device, dtype=torch.float64) if stats else None
+        cb = None
+        if reduce is not None:
+            shape = (self.xi, self.gamma)
+
+            def _cb(q_ptr, n, ctx, strm):
+                try:
+                    q = _wrap_device_floats(q_ptr, int(n), g.device).view(shape)
+                    reduce(q)
+                    return 0
+                except Exception:   # reported to the library as a failed reduction
+                    return 1
+            cb = REDUCE_FN(_cb)
+        _check(load().ctis_reconstruct_sharded(
+            self._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(f.data_ptr()), int(k), flags,
+            ctypes.c_void_p(st.data_ptr() if st is not None else 0),
+            cb if cb is not None else REDUCE_FN(), None, _stream(stream)))
+        return f, st
+
+    def time_launches(self, g, reps: int = 20, stream=None):
+        """Average milliseconds per EM launch ``(forward, adjoint)`` over
+        ``reps`` back-to-back launches of each (ctis_plan_time_launches; no
+        event between the launches). Overwrites the plan's internal copies."""
+        self._check_fpa(g)
+        fm, am = ctypes.c_double(), ctypes.c_double()
+        _check(load().ctis_plan_time_launches(self._h, ctypes.c_void_p(g.data_ptr()), int(reps),
+                                              ctypes.byref(fm), ctypes.byref(am), _stream(stream)))
+        return fm.value, am.value
+
     def check(self, stream=None):
         """Synchronise the stream and raise if a kernel reported a device-side failure."""
         _check(load().ctis_plan_check(self._h, _stream(stream)))
@@ -509,3 +560,64 @@ def reconstruct_batched(plans, plan_idx, gs, k: int, fs=None, init: str | None =
         hp, len(plans), nframes, idx, gp, fp, int(k), flags, _SOLVER[solver], float(relax),
         ctypes.c_void_p(st.data_ptr() if st is not None else 0), _stream(stream)))
     return fs, st
+
+
+def fma_peak(packed: bool = False, blocks_per_sm: int = 8, threads: int = 256, iters: int = 4096,
+             sms: int | None = None, reps: int = 5):
+    """FP32 FMA rate of this GPU (ctis_fma_peak): TFLOP/s of the best of
+    ``reps`` timed launches of ``blocks_per_sm`` CTAs of ``threads`` threads
+    per SM, with the FLOP count the header states."""
+    import torch
+    dev = torch.cuda.current_device()
+    if sms is None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * blocks_per_sm
+    out = torch.empty(blocks * threads, device="cuda", dtype=torch.float32)
+    st = torch.cuda.current_stream()
+    lib = load()
+    run = lambda: _check(lib.ctis_fma_peak(1 if packed else 0, blocks, threads, iters,
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(st.cuda_stream)))
+    run()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        run()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    flops = 2.0 * blocks * threads * iters * 32 * (2 if packed else 1)
+    return flops / (best * 1e-3) / 1e12
+
+
+def _wrap_device_floats(ptr: int, n: int, device):
+    """A torch float32 tensor viewing n floats of device memory the library
+    owns (no copy); valid only during the callback that received it."""
+    import torch
+
+    class _Cuda:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (int(ptr), False),
+                                    "version": 3}
+    return torch.as_tensor(_Cuda(), device=device)
+
+
+def shard_wavelengths(w: int, world: int, rank: int):
+    """Contiguous wavelength slice [s0, s1) of rank `rank` among `world`
+    ranks: sizes differ by at most one, lower ranks get the larger ones."""
+    if not (0 <= rank < world) or w < world:
+        raise ValueError(f"{world} ranks cannot each own wavelengths of w = {w}")
+    base, extra = divmod(w, world)
+    s0 = rank * base + min(rank, extra)
+    return s0, s0 + base + (1 if rank < extra else 0)
+
+
+def slice_psf(psf, s0: int, s1: int):
+    """The calibration images of wavelengths [s0, s1) as a PSF of its own
+    (psf_ptr rebased to 0): the input of a slice's plan."""
+    ptr = np.asarray(psf[0], dtype=np.int64)
+    lo, hi = int(ptr[s0]), int(ptr[s1])
+    return ((ptr[s0:s1 + 1] - lo).astype(np.int32), np.asarray(psf[1])[lo:hi],
+            np.asarray(psf[2])[lo:hi], np.asarray(psf[3])[lo:hi])

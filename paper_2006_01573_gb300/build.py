@@ -15,7 +15,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libctis.so")
 
 SOURCES = ["ctis_gather_fwd.cu", "ctis_gather_adj.cu", "ctis_gather_grad.cu", "ctis_gather.cu",
-           "ctis_plan.cpp", "ctis_static_scratch.cu", "ctis_fft.cu"]
+           "ctis_plan.cpp", "ctis_static_scratch.cu", "ctis_fft.cu", "ctis_fma_peak.cu",
+           "ctis_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

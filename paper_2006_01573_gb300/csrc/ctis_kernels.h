@@ -29,6 +29,15 @@ cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm);
 cudaError_t gather_launch(bool forward, int K, int dtype, const CUtensorMap& win,
                           const GatherParams& p, cudaStream_t stream);
 
+// The ratio step of a wavelength-sharded EM iteration (ctis_shard.cu): u = g
+// / q (0 where q = 0) into the FPA copies; with stats_out, the four
+// statistics of (q, g) over q > 0 into stats_out[0..3] through `part`
+// ([shard_ratio_blocks()][kNumStats] float64 scratch), in a fixed order.
+int shard_ratio_blocks();
+cudaError_t launch_shard_ratio(float* copies, long long copy_stride, int ncopies, int pitch,
+                               const float* q, const float* g, int width, int height, double* part,
+                               double* stats_out, cudaStream_t stream);
+
 // Writes the x-shifted copies (copy q, element x + q = src[x]) of a plane
 // stack from `src` (any pitch; src_dtype float32 or the copies' dtype), or of
 // the constant `value` when src is null.

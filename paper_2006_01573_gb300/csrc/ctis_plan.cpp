@@ -204,6 +204,8 @@ struct ctis_plan {
     bool drop_copies = false;         // CTIS_DEBUG_DROP_COPIES (test hook)
     FftForm* fft = nullptr;           // the paper's FFT form, built on first use
     float* d_fft_u = nullptr;         // its EM ratio [n]
+    float* d_shard_q = nullptr;       // wavelength-sharded EM: the summed H f [n]
+    double* d_shard_part = nullptr;   // its statistics' block sums
     std::vector<cudaEvent_t> events;                  // pool, pairs (start, stop)
     std::vector<std::pair<int, int>> prof_fwd, prof_adj;   // event index pairs of the last call
 };
@@ -266,6 +268,8 @@ void destroy(ctis_plan* P) {
     cudaFree(P->d_rowsum);
     fft_form_destroy(P->fft);
     cudaFree(P->d_fft_u);
+    cudaFree(P->d_shard_q);
+    cudaFree(P->d_shard_part);
     cudaFree(P->d_tap_slot);
     cudaFree(P->d_tap_s);
     cudaFree(P->d_grad_part);
@@ -2841,6 +2845,136 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
     if (result) return result;
     CTIS_CUDA(cudaStreamSynchronize(st));
     return CTIS_OK;
+}
+
+int ctis_reconstruct_sharded(ctis_plan* P, const float* g_dev, void* f_dev, int k, int flags,
+                             double* stats_dev, ctis_reduce_fn reduce, void* reduce_ctx,
+                             void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!g_dev || !f_dev) return fail(CTIS_ERR_INVALID_ARG, "NULL device pointer");
+    if (k < 0) return fail(CTIS_ERR_INVALID_ARG, "k must be >= 0");
+    if ((flags & CTIS_INIT_ONES) && (flags & CTIS_INIT_HTG))
+        return fail(CTIS_ERR_INVALID_ARG, "CTIS_INIT_ONES and CTIS_INIT_HTG are exclusive");
+    if (flags & ~(CTIS_INIT_ONES | CTIS_INIT_HTG))
+        return fail(CTIS_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!P->d_shard_q) {
+        rc = dmalloc(P, reinterpret_cast<void**>(&P->d_shard_q), sizeof(float) * static_cast<size_t>(P->n));
+        if (!rc)
+            rc = dmalloc(P, reinterpret_cast<void**>(&P->d_shard_part),
+                         sizeof(double) * kNumStats * shard_ratio_blocks());
+        if (rc) return rc;
+    }
+    rc = zero_u(P, st);
+    if (rc) return rc;
+    if (flags & CTIS_INIT_ONES) {
+        rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
+    } else if (flags & CTIS_INIT_HTG) {
+        rc = scatter_u(P, g_dev, st);
+        if (rc) return rc;
+        GatherParams p = base_params(P, P->adj);
+        p.mode = kEpiSet;
+        p.out_w = P->a;
+        p.out_h = P->alpha;
+        set_f_copies(P, p);
+        rc = enqueue_adjoint(P, p, st);
+    } else {
+        rc = scatter_f(P, f_dev, P->dtype, 0.f, st);
+    }
+    if (rc) return rc;
+    GatherParams pq = base_params(P, P->fwd);   // the slice's partial image
+    pq.mode = kEpiRaw;
+    pq.out_w = P->gamma;
+    pq.out_h = P->xi;
+    pq.out_f32 = P->d_shard_q;
+    pq.out_pitch = P->gamma;
+    pq.out_plane_stride = 0;
+    GatherParams pa = base_params(P, P->adj);
+    pa.mode = kEpiUpdate;
+    pa.out_w = P->a;
+    pa.out_h = P->alpha;
+    set_f_copies(P, pa);
+    for (int it = 0; it <= k; ++it) {
+        if (it == k && !stats_dev) break;
+        rc = enqueue_forward(P, pq, st);
+        if (rc) return rc;
+        if (reduce) {
+            const int r = reduce(P->d_shard_q, P->n, reduce_ctx, stream);
+            if (r != 0)
+                return fail(CTIS_ERR_CUDA, "the reduction callback returned %d at iteration %d", r, it);
+        }
+        CTIS_CUDA(launch_shard_ratio(P->d_u, P->u_copy_stride, P->u_copies, P->g_pitch,
+                                     P->d_shard_q, g_dev, P->gamma, P->xi, P->d_shard_part,
+                                     stats_dev ? stats_dev + static_cast<int64_t>(it) * kNumStats
+                                               : nullptr,
+                                     st));
+        if (it == k) break;
+        rc = enqueue_adjoint(P, pa, st);
+        if (rc) return rc;
+    }
+    CTIS_CUDA(launch_gather_copy0(P->dtype, f_dev, P->d_fwork, P->a_pitch,
+                                  static_cast<int64_t>(P->a_pitch) * P->alpha, P->a, P->alpha,
+                                  P->w, st));
+    return CTIS_OK;
+}
+
+int ctis_plan_time_launches(ctis_plan* P, const float* g_dev, int reps, double* fwd_ms,
+                            double* adj_ms, void* stream) {
+    int rc = check_plan(P);
+    if (rc) return rc;
+    if (!g_dev || reps < 1 || !fwd_ms || !adj_ms)
+        return fail(CTIS_ERR_INVALID_ARG, "g_dev, fwd_ms or adj_ms is NULL, or reps < 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CTIS_CUDA(cudaStreamSynchronize(st));
+    // the EM loop's operands: f = 1 in the datacube copies, u from g
+    rc = scatter_f(P, nullptr, P->dtype, 1.0f, st);
+    if (!rc) rc = zero_u(P, st);
+    if (!rc) rc = scatter_u(P, g_dev, st);
+    if (rc) return rc;
+    auto launch = [&](bool forward) -> int {
+        if (forward) {
+            GatherParams p = base_params(P, P->fwd);
+            p.mode = kEpiRatio;
+            p.out_w = P->gamma;
+            p.out_h = P->xi;
+            p.out_f32 = P->d_u;
+            p.out_pitch = P->g_pitch;
+            p.out_copy_stride = P->u_copy_stride;
+            p.out_copies = P->u_copies;
+            p.g = g_dev;
+            p.g_pitch = P->gamma;
+            p.with_stats = 1;   // tile statistics, as inside the EM loop
+            return enqueue_forward(P, p, st);
+        }
+        GatherParams p = base_params(P, P->adj);
+        p.mode = kEpiUpdate;
+        p.out_w = P->a;
+        p.out_h = P->alpha;
+        set_f_copies(P, p);
+        return enqueue_adjoint(P, p, st);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CTIS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(CTIS_ERR_CUDA, "cudaEventCreate failed");
+    }
+    for (int side = 0; side < 2 && !rc; ++side) {
+        const bool forward = side == 0;
+        for (int r = 0; r < 2 && !rc; ++r) rc = launch(forward);   // warm-up
+        cudaError_t e = rc ? cudaSuccess : cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = launch(forward);
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "timing back-to-back launches");
+        (forward ? *fwd_ms : *adj_ms) = static_cast<double>(ms) / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int ctis_plan_check(const ctis_plan* P, void* stream) {

@@ -118,41 +118,3 @@ def test_noiseless_single_delta_recovers_scene_exactly():
     with Plan(a, al, w, ga, xi, psf) as plan:
         f, _ = plan.reconstruct(torch.from_numpy(g.reshape(xi, ga)).cuda(), k=1)
     assert np.array_equal(f.cpu().numpy(), f_true)
-
-
-def test_full_size_first_iteration_sampled():
-    """Realistic workload, one EM step from ones in the benchmark's launch
-    configuration; sampled voxels evaluated one by one by the oracle."""
-    wl = synth.REALISTIC
-    geom = geometry(wl)
-    psf = synth.make_psf(wl)
-    taps = O.merge_psf(geom, psf)
-    f_true = synth.make_scene(wl)
-    rng = np.random.default_rng(1)
-    # the measurement of the scene's first 8 wavelengths, imaged by the
-    # oracle's own wavelength blocks (the GPU path supplies no input here)
-    f_part = f_true.copy()
-    f_part[8:] = 0.0
-    hf_part = O.BlockH(geom, taps, range(8)).forward(f_part.ravel())
-    g, _ = synth.make_measurement(hf_part, wl.peak, wl.seed)
-    g = g.reshape(wl.xi, wl.gamma)
-    with _plan(wl, psf) as plan:
-        gt = torch.from_numpy(g).cuda()
-        f1, st = plan.reconstruct(gt, k=1, init="ones", stats=True)
-        plan.check()
-        f1 = f1.cpu().numpy()
-    ss = rng.integers(0, wl.w, 40)
-    ps = rng.integers(0, wl.a, 40)
-    rs = rng.integers(0, wl.alpha, 40)
-    ones = np.ones(geom.m)
-    got, ref = [], []
-    for s, p, r in zip(ss, ps, rs):
-        tx, ty, tv = taps.of(int(s))
-        xs, ys = tx + p, ty + r
-        q = O.forward_at(geom, taps, ones, xs, ys)
-        u = np.where(q > 0, g[ys, xs] / np.where(q > 0, q, 1), 0.0)
-        zeta = float(np.dot(tv, u))
-        h = float(tv.sum())
-        ref.append(zeta / h)
-        got.append(f1[s, r, p])
-    assert floored_rel(got, ref) <= 1e-5

@@ -633,3 +633,55 @@ def test_wrap_em_invariants():
         assert np.all(f_next >= 0)
         assert abs(np.dot(h, f_next) - g[q > 0].sum()) <= 1e-9 * g.sum()
         f = f_next
+
+
+# --- the shifted-sum projectors (large workloads) -----------------------------------
+
+@pytest.mark.parametrize("boundary,shift", [("reject", (0, 0)), ("clip", (-5, 4)), ("clip", (9, -7))])
+def test_shifted_sum_projectors_equal_the_sparse_and_dense_H(boundary, shift):
+    """forward_shifts / adjoint_shifts (pasting the field stop per tap) against
+    the sparse BlockH (indices of Sec. 2's shifted columns) and, under the
+    reject reading, the dense C_s E of Eqs. 5-7; random PSFs with duplicates."""
+    for seed, dims in ((3, (4, 3, 2, 10, 9)), (4, (5, 6, 3, 17, 13)), (5, (7, 2, 4, 12, 20))):
+        geom = _geom(*dims)
+        ptr, x, y, v = _tiny_psf(geom, 5, seed, dup=2)
+        psf = (ptr, (x + shift[0]).astype(np.int32), (y + shift[1]).astype(np.int32), v)
+        taps = O.merge_psf(geom, psf, boundary)
+        H = O.BlockH(geom, taps)
+        f = synth.random_positive(geom.m, seed + 10).astype(np.float64)
+        u = synth.random_positive(geom.n, seed + 20).astype(np.float64)
+        np.testing.assert_allclose(O.forward_shifts(geom, taps, f), H.forward(f), rtol=1e-14, atol=0)
+        np.testing.assert_allclose(O.adjoint_shifts(geom, taps, u), H.adjoint(u), rtol=1e-14, atol=0)
+        np.testing.assert_allclose(O.h_shifts(geom, taps), H.h(), rtol=1e-14, atol=0)
+        if boundary == "reject":
+            D = O.dense_H(geom, psf)
+            np.testing.assert_allclose(O.forward_shifts(geom, taps, f), D @ f, rtol=1e-13, atol=1e-13)
+
+
+def test_shifted_sum_em_equals_sparse_em():
+    geom, H, g, _ = _tiny_problem(noisy=True)
+    taps = H.taps
+    f1, h1 = O.mlem(H, g, 7)
+    f2, h2 = O.mlem_shifts(geom, taps, g, 7)
+    np.testing.assert_allclose(f2, f1, rtol=1e-12, atol=0)
+    for a, b in zip(h1, h2):
+        for key in a:
+            assert b[key] == pytest.approx(a[key], rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["transposed_shift", "flipped_psf", "wrong_wavelength"])
+def test_planted_mistakes_fail_the_shifted_sum_pin(kind):
+    geom = _geom(4, 3, 2, 10, 9)
+    psf = _tiny_psf(geom, 5, 41)
+    taps = O.merge_psf(geom, psf)
+    f = synth.random_positive(geom.m, 12).astype(np.float64)
+    assert not np.allclose(_mutant_forward(geom, taps, f, kind), O.forward_shifts(geom, taps, f),
+                           rtol=1e-6)
+
+
+def test_unrolled_nll_shifts_equals_unrolled_nll():
+    geom, H, g, _ = _tiny_problem(noisy=True)
+    f0 = synth.random_positive(geom.m, 9).astype(np.float64)
+    for k in (0, 1, 4):
+        assert O.unrolled_nll_shifts(geom, H.taps, g, f0, k) == pytest.approx(
+            O.unrolled_nll(geom, H.taps, g, f0, k), rel=1e-12)
