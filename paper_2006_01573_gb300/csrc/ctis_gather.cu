@@ -196,8 +196,13 @@ int gather_box_w(bool forward, int K, int dtype) {
 int gather_weight_pad(bool forward, int K, int dtype) {
     return with_geo(forward, K, dtype, [](auto g) { return decltype(g)::WPAD; });
 }
+// x-shifted copies of a projector's input: 4 (float32: 16-byte alignment;
+// bfloat16: 8-byte alignment, the lanes taking the remaining shift of 0 or 4
+// elements inside a 16-byte aligned box)
 int gather_input_copies(bool forward, int dtype) {
-    return forward && dtype == kDtypeBF16 ? 8 : 4;
+    (void)forward;
+    (void)dtype;
+    return 4;
 }
 
 cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm) {

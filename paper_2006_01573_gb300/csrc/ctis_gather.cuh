@@ -207,10 +207,18 @@ struct Geo {
     static constexpr int TX = LX * C, TY = LY * R;
     static constexpr int ES = int(sizeof(TIn));
     static constexpr int EPC = Elem<TIn>::kPerChunk;
-    static_assert(C % EPC == 0, "a lane's columns must be whole 16-byte chunks");
+    // a lane's first column is 16-byte aligned (float32: C = 4) or 8-byte
+    // aligned (bfloat16 with C = 4, read with 8- and 4-byte loads)
+    static_assert(C % EPC == 0 || (ES == 2 && C == 4), "a lane's columns: whole 16-byte chunks, "
+                                                       "or 4 bfloat16");
     static_assert(LX >= 8, "a quarter warp must span 8 consecutive chunks of a row");
     // window row: TX + K - 1 elements from a chunk-aligned origin
-    static constexpr int BXW = (TX + K - 1 + EPC - 1) / EPC * EPC;
+    // bfloat16 inputs come in 4 x-shifted copies (8-byte alignment) while a
+    // TMA box must start 16-byte aligned: the box starts at the 16-byte
+    // boundary at or below the window, and the lanes start MS elements in
+    // (0 or 4, the task's shift); the box is MSLACK elements wider for it
+    static constexpr int MSLACK = ES == 2 ? 4 : 0;
+    static constexpr int BXW = (TX + K - 1 + MSLACK + EPC - 1) / EPC * EPC;
     static constexpr int ROWS = TY + K - 1;           // TMA box height
     static_assert((BXW * ES) % 16 == 0 && BXW <= 256 && ROWS <= 256, "TMA box");
     static constexpr int WINDOW_BYTES = ROWS * BXW * ES;
@@ -232,7 +240,8 @@ struct Geo {
     static constexpr int FLAG_OFF = RED_OFF + RED_BYTES;
     static constexpr int TSTAT_OFF = FLAG_OFF + 16;       // [NW][4] float64 tile statistics
     static constexpr int BAR_OFF = TSTAT_OFF + NW * 4 * 8;
-    static constexpr int SMEM_BYTES = BAR_OFF + NW * NS * 8;
+    static constexpr int SHIFT_OFF = BAR_OFF + NW * NS * 8;     // [NW][NS] lane shift per stage
+    static constexpr int SMEM_BYTES = SHIFT_OFF + (NW * NS * 4 + 15) / 16 * 16;
     static constexpr int ER = R / NW;   // epilogue rows of each lane's block per warp
     static_assert(R % NW == 0, "the epilogue splits a lane's rows evenly over the warps");
     // resident CTAs per SM the register budget must allow (4 x 4 warps = 16
@@ -267,6 +276,59 @@ __device__ __forceinline__ void load_row_elems(const TIn* rowp, float (&raw)[G::
 // FFMAs against 0.63 with FFMA2). Both round each product-sum once, so the
 // results are the same bit for bit. acc is kept as float2 pairs (c, c+1)
 // for the item-end code.
+// bfloat16 windows (the storage form; the lane starts 0 or 4 elements into
+// the box, so 8-byte aligned): the elements stay 16-bit and feed
+// fma.rn.f32.bf16, which widens both bfloat16 operands exactly and rounds the
+// float32 product-sum once, as the float32 path does after widening them
+// itself (same bits), without spending issue slots on the widening. The
+// lane's C + K - 1 elements start 8-byte aligned: 8-byte loads, then a 4-byte
+// one. wh[q] holds tap q's weight in its low 16 bits.
+template <class G>
+__device__ __forceinline__ void correlate_bf16(float2 (&acc)[G::R][G::C / 2], const __nv_bfloat16* win,
+                                               const uint32_t (&wh)[G::K * G::K]) {
+    constexpr int K = G::K, C = G::C, R = G::R;
+    constexpr int NE = C + K - 1;
+    static_assert(NE % 2 == 0, "whole bfloat16 pairs");
+#pragma unroll
+    for (int i = 0; i < R + K - 1; ++i) {
+        const uint16_t* rp = reinterpret_cast<const uint16_t*>(win + i * G::BXW);
+        uint16_t h[NE];
+#pragma unroll
+        for (int q = 0; q + 4 <= NE; q += 4) {
+            const uint2 v = *reinterpret_cast<const uint2*>(rp + q);
+            h[q] = uint16_t(v.x & 0xffffu);
+            h[q + 1] = uint16_t(v.x >> 16);
+            h[q + 2] = uint16_t(v.y & 0xffffu);
+            h[q + 3] = uint16_t(v.y >> 16);
+        }
+        if constexpr (NE % 4 == 2) {
+            const uint32_t v = *reinterpret_cast<const uint32_t*>(rp + NE - 2);
+            h[NE - 2] = uint16_t(v & 0xffffu);
+            h[NE - 1] = uint16_t(v >> 16);
+        }
+#pragma unroll
+        for (int dx = 0; dx < K; ++dx) {
+#pragma unroll
+            for (int dy = 0; dy < K; ++dy) {
+                const int o = i - dy;
+                if (o >= 0 && o < R) {
+                    const uint16_t wq = uint16_t(wh[dy * K + dx] & 0xffffu);
+#pragma unroll
+                    for (int c2 = 0; c2 < C / 2; ++c2) {
+                        float d0, d1;
+                        asm("fma.rn.f32.bf16 %0, %1, %2, %3;"
+                            : "=f"(d0) : "h"(h[2 * c2 + dx]), "h"(wq), "f"(acc[o][c2].x));
+                        asm("fma.rn.f32.bf16 %0, %1, %2, %3;"
+                            : "=f"(d1) : "h"(h[2 * c2 + 1 + dx]), "h"(wq), "f"(acc[o][c2].y));
+                        acc[o][c2].x = d0;
+                        acc[o][c2].y = d1;
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <class G, typename TIn>
 __device__ __forceinline__ void correlate(float2 (&acc)[G::R][G::C / 2], const TIn* win,
                                           const float2 (&w2)[G::K * G::K]) {
@@ -841,6 +903,7 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     const int tx = lane % G::LX, ty = lane / G::LX;
     unsigned char* my_stages = smem_raw + warp * G::NS * G::STAGE_BYTES;
     uint64_t* my_bars = bars + warp * G::NS;
+    int* my_shift = reinterpret_cast<int*>(smem_raw + G::SHIFT_OFF) + warp * G::NS;
     if (lane == 0) {
         for (int s = 0; s < G::NS; ++s) mbar_init(&my_bars[s], 1);
         fence_mbar_init();
@@ -864,9 +927,13 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         if (lane == 0) {
             unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
             uint64_t* bar = &my_bars[issue_stage];
+            // the lanes' shift inside the box (bfloat16: wx is a multiple of
+            // 4, the box starts at a multiple of 8), published before the
+            // arrival that releases the stage to the warp
+            my_shift[issue_stage] = nxt.wx & (G::EPC - 1);
             mbar_arrive_expect_tx(bar, G::TX_BYTES);
             if (!p.drop_copies) {
-                tma_load_3d(stage, &tm_win, nxt.wx, nxt.wy, nxt.plane, bar);
+                tma_load_3d(stage, &tm_win, nxt.wx & ~(G::EPC - 1), nxt.wy, nxt.plane, bar);
                 bulk_load(stage + G::WOFF,
                           static_cast<const unsigned char*>(p.weights) +
                               (long long)nxt.cluster * G::WBYTES,
@@ -961,6 +1028,12 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                         const float sum = warp_sum_f(gacc[q].x + gacc[q].y);
                         if (lane == 0) dst[q] = sum;
                     }
+                } else if constexpr (std::is_same_v<TIn, __nv_bfloat16>) {
+                    uint32_t wh[G::K * G::K];
+#pragma unroll
+                    for (int q = 0; q < G::K * G::K; ++q) wh[q] = ws[q];
+                    correlate_bf16<G>(acc, reinterpret_cast<const TIn*>(stage) + lane_off +
+                                               my_shift[cons_stage], wh);
                 } else {
                     float2 w2[G::K * G::K];
 #pragma unroll
@@ -1135,15 +1208,15 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     __syncwarp();
 }
 
-// A lane owns whole 16-byte chunks: C = 4 float32 or 8 bfloat16 columns; the
-// rows per lane shrink with the element size so a lane keeps the same number
-// of accumulators.
+// Every instantiation has 32 x 32 tiles: C = 4 columns x R = 8 rows per lane.
+// The forward of a bfloat16 plan reads bfloat16 windows, half the bytes of a
+// float32 window, and spends the freed shared memory on a third TMA stage
+// per warp (a deeper look-ahead on the window stream at the same 4 CTAs per
+// SM).
 template <bool FWD, typename TIn>
 constexpr GatherShape shape_of() {
     GatherShape s = FWD ? kShapeFwd : kShapeAdj;
-    const int c = 16 / int(sizeof(TIn));
-    s.R = s.R * s.C / c;
-    s.C = c;
+    if (FWD && sizeof(TIn) == 2) s.NS = CTIS_FWD_NS_BF16;
     return s;
 }
 

@@ -49,12 +49,13 @@ struct WorkItem {
     int task_begin, task_end;
 };
 
-// Input planes are kept as NC x-shifted copies (NC = elements per 16 bytes:
-// 4 for float32, 8 for bfloat16): copy q holds plane[x - q] at x (rows are
-// NC - 1 elements wider than the plane; the rest is zero). A window whose
-// origin x0 is not 16-byte aligned is read from copy q = (-x0) mod NC at the
-// aligned x0 + q, so every TMA box and every shared-memory load is aligned
-// and the kernel has a single code path.
+// Input planes are kept as NC = 4 x-shifted copies: copy q holds plane[x - q]
+// at x (rows are NC - 1 elements wider than the plane; the rest is zero). A
+// window whose origin x0 is not a multiple of 4 is read from copy
+// q = (-x0) mod 4 at x0 + q, a multiple of 4: 16-byte aligned for float32, so
+// every TMA box and shared-memory load is aligned and the kernel has a single
+// code path; 8-byte aligned for bfloat16, whose box then starts at the 16-byte
+// boundary below and whose lanes start 0 or 4 elements into it.
 struct TaskDesc {        // 16 bytes
     int wx;              // aligned window origin x inside the chosen copy
     int wy;              // window origin y (any integer; TMA zero-fills outside)
@@ -163,6 +164,9 @@ struct GatherShape {
 #endif
 #ifndef CTIS_FWD_NS
 #define CTIS_FWD_NS 2
+#endif
+#ifndef CTIS_FWD_NS_BF16
+#define CTIS_FWD_NS_BF16 3
 #endif
 #ifndef CTIS_ADJ_R
 #define CTIS_ADJ_R 8

@@ -156,7 +156,6 @@ struct ctis_plan {
     int a = 0, alpha = 0, w = 0, gamma = 0, xi = 0, dtype = 0;
     int64_t m = 0, n = 0;
     int device = 0, num_sms = 0, K = 1;
-    int f_epc = 4;        // datacube elements per 16 bytes (= number of f copies)
     int a_pitch = 0;      // row pitch of the internal datacube copies (elements)
     int g_pitch = 0;      // row pitch of the internal FPA copies (elements)
     int f_copies = 4, u_copies = 4;
@@ -1869,7 +1868,6 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     P->dtype = dtype;
     P->m = (int64_t)a * alpha * w;
     P->n = (int64_t)gamma * xi;
-    P->f_epc = dtype == CTIS_BF16 ? 8 : 4;
     P->f_copies = gather_input_copies(true, dtype);
     P->u_copies = gather_input_copies(false, dtype);
     P->forced_per_item = forced_per_item;
@@ -1878,7 +1876,8 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     P->clip = boundary != CTIS_BOUNDARY_REJECT;
     P->wrap = boundary == CTIS_BOUNDARY_WRAP;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
-    P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, P->f_copies));
+    // (a multiple of 16 bytes: the window map's row stride)
+    P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, dtype == CTIS_BF16 ? 8 : 4));
     P->g_pitch = static_cast<int>(round_up(gamma + P->u_copies - 1, 4));
     *out = P;
     return CTIS_OK;
