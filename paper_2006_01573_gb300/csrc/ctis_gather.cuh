@@ -898,7 +898,24 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         }
     }
     if (gw >= p.n_warps) return;
-    const int ib = p.warp_begin[gw], ie = p.warp_begin[gw + 1];
+    // the warp's start: lanes 0..5 load its 96-byte head at once, then the
+    // fields go to every lane by shuffles
+    int4 hv = make_int4(0, 0, 0, 0);
+    if (lane < 6) hv = __ldg(reinterpret_cast<const int4*>(p.heads + gw) + lane);
+    auto from = [&](int src, int4& d) {
+        d.x = __shfl_sync(0xffffffffu, hv.x, src);
+        d.y = __shfl_sync(0xffffffffu, hv.y, src);
+        d.z = __shfl_sync(0xffffffffu, hv.z, src);
+        d.w = __shfl_sync(0xffffffffu, hv.w, src);
+    };
+    int4 h0, f0, f1, f2, i0, i1;
+    from(0, h0);
+    from(1, f0);
+    from(2, f1);
+    from(3, f2);
+    from(4, i0);
+    from(5, i1);
+    const int ib = h0.x, ie = h0.y;
     if (ib >= ie) return;   // nothing issued, nothing to drain
     const int tx = lane % G::LX, ty = lane / G::LX;
     unsigned char* my_stages = smem_raw + warp * G::NS * G::STAGE_BYTES;
@@ -911,16 +928,18 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     __syncwarp();
 
     const int lane_off = ty * G::R * G::BXW + tx * G::C;   // this lane's first element
-    WorkItem next_it = p.items[ib];
-    const int task_end = p.items[ie - 1].task_end;         // end of the warp's task range
-    int issue_task = next_it.task_begin;                    // next task to issue (uniform)
+    WorkItem next_it{i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+    const int task_end = h0.w;                              // end of the warp's task range
+    int issue_task = h0.z;                                  // next task to issue (uniform)
     int issue_stage = 0;
     int cons_stage = 0;
     uint32_t cons_phase = 0;
     int outstanding = 0;                                    // copies issued, not yet waited for
     bool failed = false;                                    // warp-uniform
-    TaskDesc nxt{};                                         // lane 0: descriptor of issue_task
-    if (lane == 0 && issue_task < task_end) nxt = p.tasks[issue_task];
+    // lane 0: descriptor of issue_task; the first three come with the head,
+    // the later ones are loaded one issue ahead
+    TaskDesc nxt{f0.x, f0.y, f0.z, f0.w};
+    const int head_end = issue_task + 3;
 
     auto issue_next = [&]() {
         if (issue_task >= task_end || failed) return;
@@ -939,7 +958,12 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                               (long long)nxt.cluster * G::WBYTES,
                           G::WBYTES, bar);
             }
-            if (issue_task + 1 < task_end) nxt = p.tasks[issue_task + 1];
+            const int t1 = issue_task + 1;
+            if (t1 < task_end) {
+                if (t1 == head_end - 2) nxt = TaskDesc{f1.x, f1.y, f1.z, f1.w};
+                else if (t1 == head_end - 1) nxt = TaskDesc{f2.x, f2.y, f2.z, f2.w};
+                else nxt = p.tasks[t1];
+            }
         }
         ++issue_task;
         ++outstanding;

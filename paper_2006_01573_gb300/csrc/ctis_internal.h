@@ -63,6 +63,17 @@ struct TaskDesc {        // 16 bytes
     int cluster;         // weight set index
 };
 
+// A warp's start, read in one round of independent loads instead of a chain
+// (item range -> first item -> first task -> next task): its items and tasks,
+// its first item and its first three task descriptors (fewer are valid when
+// it has fewer tasks). 96 bytes.
+struct WarpHead {
+    int ib, ie;                  // range in the item list
+    int task_begin, task_end;    // the warp's tasks
+    TaskDesc first[3];
+    WorkItem item0;
+};
+
 enum Epilogue : int {
     kEpiRaw = 0,     // out_f32 = value                      (ctis_forward / ctis_adjoint)
     kEpiRatio = 1,   // u copies = g / value, 0 where value == 0  (forward inside EM)
@@ -83,6 +94,7 @@ enum Solver : int {
 struct GatherParams {
     const WorkItem* items;     // grouped by warp, in processing order
     const int* warp_begin;     // [n_warps + 1] range of each warp in items
+    const WarpHead* heads;     // [n_warps] each warp's start
     const TaskDesc* tasks;     // in item order: each warp's tasks are contiguous
     const void* weights;       // [clusters][padded K*K] in the plan's storage type
     int n_warps;

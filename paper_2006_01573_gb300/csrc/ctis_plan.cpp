@@ -88,6 +88,7 @@ struct ProjTables {
     std::vector<TaskDesc> tile_tasks;       // tile order, the input of schedule()
     std::vector<int> tile_task_begin;       // [tiles + 1]
     std::vector<int> warp_begin;   // [n_warps + 1]
+    std::vector<WarpHead> heads;   // [n_warps] each warp's start (warp_begin, first item/tasks)
     std::vector<int> cta_begin;    // [CTAs + 1]
     std::vector<int> cta_items;    // item indices, grouped by CTA
     int nw = 4;                    // warps per CTA of the projector's kernel
@@ -103,6 +104,7 @@ struct ProjTables {
     double max_warp_load = 0.0;    // LPT estimate of the busiest CTA, tasks per warp
     TaskDesc* d_tasks = nullptr;
     int* d_warp_begin = nullptr;
+    WarpHead* d_heads = nullptr;
     WorkItem* d_witems = nullptr;
     void* d_weights = nullptr;
     int blocks_per_sm = 0;
@@ -234,6 +236,8 @@ int upload(ctis_plan* P, T** dst, const std::vector<T>& src) {
 void free_tables(ProjTables& t) {
     cudaFree(t.d_tasks);
     cudaFree(t.d_warp_begin);
+    cudaFree(t.d_heads);
+    t.d_heads = nullptr;
     cudaFree(t.d_weights);
     cudaFree(t.d_witems);
     t.d_tasks = nullptr;
@@ -601,6 +605,18 @@ void layout_warps(ProjTables& T) {
             T.warp_begin.push_back(static_cast<int>(T.witems.size()));
         }
     T.tasks = std::move(wt);
+    T.heads.assign(T.warp_begin.size() - 1, WarpHead{});
+    for (size_t w = 0; w + 1 < T.warp_begin.size(); ++w) {
+        WarpHead& h = T.heads[w];
+        h.ib = T.warp_begin[w];
+        h.ie = T.warp_begin[w + 1];
+        if (h.ib >= h.ie) continue;
+        h.task_begin = T.witems[h.ib].task_begin;
+        h.task_end = T.witems[h.ie - 1].task_end;
+        for (int j = 0; j < 3 && h.task_begin + j < h.task_end; ++j)
+            h.first[j] = T.tasks[h.task_begin + j];
+        h.item0 = T.witems[h.ib];
+    }
 }
 
 // h = H^T 1 (Eq. 2): under the on-FPA rule every voxel of wavelength s sees
@@ -963,6 +979,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     for (ProjTables* T : {&P->fwd, &P->adj}) {
         int rc = upload(P, &T->d_tasks, T->tasks);
         if (!rc) rc = upload(P, &T->d_warp_begin, T->warp_begin);
+        if (!rc) rc = upload(P, &T->d_heads, T->heads);
         if (!rc) rc = upload(P, &T->d_witems, T->witems);
         if (rc) return rc;
     }
@@ -1023,12 +1040,15 @@ void drop_table_users(ctis_plan* P) {
 int reupload_tables(ctis_plan* P, ProjTables& T) {
     cudaFree(T.d_tasks);
     cudaFree(T.d_warp_begin);
+    cudaFree(T.d_heads);
     cudaFree(T.d_witems);
     T.d_tasks = nullptr;
     T.d_warp_begin = nullptr;
+    T.d_heads = nullptr;
     T.d_witems = nullptr;
     int r = upload(P, &T.d_tasks, T.tasks);
     if (!r) r = upload(P, &T.d_warp_begin, T.warp_begin);
+    if (!r) r = upload(P, &T.d_heads, T.heads);
     if (!r) r = upload(P, &T.d_witems, T.witems);
     if (r) return r;
     const int64_t need = T.scratch_slots * T.tile_w * T.tile_h;
@@ -1086,6 +1106,7 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.tasks = T.d_tasks;
     p.weights = T.d_weights;
     p.warp_begin = T.d_warp_begin;
+    p.heads = T.d_heads;
     p.n_warps = T.n_warps;
     p.n_tiles = static_cast<int>(T.tiles.size());
     p.scratch = P->d_scratch;
@@ -1398,6 +1419,7 @@ struct BatchTables {
     WorkItem* d_witems = nullptr;
     TaskDesc* d_tasks = nullptr;
     int* d_warp_begin = nullptr;
+    WarpHead* d_heads = nullptr;
     int n_warps = 0;
     int n_tiles = 0;
     int64_t scratch_slots = 0;   // chunk partial-sum slots of the joint schedule
@@ -1426,6 +1448,7 @@ void free_tables(BatchTables& t) {
     cudaFree(t.d_witems);
     cudaFree(t.d_tasks);
     cudaFree(t.d_warp_begin);
+    cudaFree(t.d_heads);
     t = BatchTables{};
 }
 
@@ -1512,6 +1535,7 @@ int replicate(ctis_plan* P, const ProjTables& T, bool forward, int F, BatchTable
     int rc = upload(P, &B.d_witems, J.witems);
     if (!rc) rc = upload(P, &B.d_tasks, J.tasks);
     if (!rc) rc = upload(P, &B.d_warp_begin, J.warp_begin);
+    if (!rc) rc = upload(P, &B.d_heads, J.heads);
     return rc;
 }
 
@@ -1584,6 +1608,7 @@ GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward)
     GatherParams p{};
     p.items = BT.d_witems;
     p.warp_begin = BT.d_warp_begin;
+    p.heads = BT.d_heads;
     p.tasks = BT.d_tasks;
     p.weights = T.d_weights;
     p.n_warps = BT.n_warps;
