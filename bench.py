@@ -52,7 +52,8 @@ def parse_args():
     ap.add_argument("--schedule", default=None,
                     help="skip the autotuner and use these schedules, 'FWD,ADJ' with each "
                          "'chunk:TASKS:SKEW' or 'split:OVERHEAD_Q:SKEW' (SKEW in permille), "
-                         "e.g. a bench line's config.schedule.spec")
+                         "FWD optionally led by its tile shape ('32x16:chunk:64:0'), "
+                         "e.g. a bench line's schedule.spec")
     ap.add_argument("--paper-table", default=None, metavar="OUT_JSON",
                     help="instead of the bench line: the paper's Table 1 grid (field stop "
                          "89x80, 2048x2048 FPA, w = 3, 24, 75, K = 10..3100) on a synthetic PSF, "
@@ -348,12 +349,16 @@ def run_ours(args, wl, k):
     seed = wl.seed + rank
     psf = synth.make_psf(wl)
     f_true = synth.make_scene(wl, seed)
-    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
+    specs = args.schedule.split(",") if args.schedule else None
+    tile = "32x32"
+    if specs and specs[0].count(":") == 3:        # the forward's spec led by its tile shape
+        tile, specs[0] = specs[0].split(":", 1)
+    plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, forward_tile=tile)
     hf = plan.forward(torch.from_numpy(f_true).to(dev))
     g_host, _ = synth.make_measurement(hf.cpu().numpy(), wl.peak, seed)
     g = torch.from_numpy(g_host).to(dev)
-    if args.schedule:                             # a given schedule (e.g. to profile one)
-        for forward, spec in zip((True, False), args.schedule.split(",")):
+    if specs:                                     # a given schedule (e.g. to profile one)
+        for forward, spec in zip((True, False), specs):
             kind, value, skew = spec.split(":")
             plan.set_schedule(forward, (kind, int(value), int(skew)))
         tuned = plan.schedules()
@@ -488,8 +493,10 @@ def run_ours(args, wl, k):
         "config": bench_config(wl, k, world),
         # the work schedule the plan ran (kept out of config, which both arms
         # print identically)
-        "schedule": {"forward": schedule_name(tuned[0]), "adjoint": schedule_name(tuned[1]),
-                     "spec": ",".join(f"{k}:{v}:{sk}" for k, v, sk in tuned),
+        "schedule": {"forward": f"{plan.forward_tile()} tiles, " + schedule_name(tuned[0]),
+                     "adjoint": schedule_name(tuned[1]),
+                     "spec": plan.forward_tile() + ":" +
+                             ",".join(f"{k}:{v}:{sk}" for k, v, sk in tuned),
                      "chosen_by": "--schedule" if args.schedule else "ctis_plan_autotune"},
         "voxel_updates_per_s": value * wl.m,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,

@@ -123,8 +123,16 @@ typedef struct {
     int boundary;          /* CTIS_BOUNDARY_REJECT (0), _CLIP or _WRAP; CLIP
                               accepts PSF coordinates in [-2^24, 2^24), WRAP
                               those on the FPA                                  */
-    int reserved[3];       /* must be 0                                          */
+    int forward_tile;      /* CTIS_TILE_32X32 (0, default) or CTIS_TILE_32X16:
+                              the forward's output tiles until ctis_plan_autotune
+                              picks the faster shape                            */
+    int reserved[2];       /* must be 0                                          */
 } ctis_plan_options;
+
+/* Forward tile shapes (FPA pixels, columns x rows). 32 x 16 tiles waste less
+ * of the footprints of small field stops (a footprint covers whole tiles)
+ * but carry each window's fixed costs over half the outputs. */
+enum { CTIS_TILE_32X32 = 0, CTIS_TILE_32X16 = 1 };
 
 /* ctis_plan_create with options; opt may be NULL (all defaults). */
 int ctis_plan_create_ex(ctis_plan** out, int a, int alpha, int w, int gamma, int xi,
@@ -191,6 +199,8 @@ typedef struct {
                                               quarter tasks; 0 = chunk schedule */
     int64_t fwd_skew_pm, adj_skew_pm;      /* CTA priority skew of the schedule  */
     int64_t boundary;                      /* CTIS_BOUNDARY_*                    */
+    int64_t fwd_tile_w, fwd_tile_h;        /* the forward's tile shape (FPA pixels;
+                                              ctis_plan_autotune may change it)  */
 } ctis_plan_info;
 
 int ctis_plan_get_info(const ctis_plan* plan, ctis_plan_info* info);
@@ -417,10 +427,14 @@ int ctis_unrolled_nll_grad(ctis_plan* plan, const float* g_dev, const float* f0_
  * at most 16..192 cluster tasks assigned longest first, and the balanced
  * split with item overheads of 2..24 quarter tasks, some of them also with
  * CTA priority skews of 100..300 permille (ctis_plan_options); the four
- * fastest of a first pass are timed again, interleaved, before the choice. Synchronous; overwrites the plan's internal copies
- * and drops its cached graphs (the next ctis_reconstruct re-captures).
- * Results stay deterministic for a given schedule but may differ in the last
- * bits between schedules (partial sums are grouped differently). */
+ * fastest of a first pass are timed again, interleaved, before the choice.
+ * The forward is tuned once per tile shape (CTIS_TILE_*), and the shapes'
+ * winners are timed against each other, interleaved, over three rounds: the
+ * plan keeps the faster shape with its schedule (ctis_plan_get_info reports
+ * both). Synchronous; overwrites the plan's internal copies and drops its
+ * cached graphs (the next ctis_reconstruct re-captures). Results stay
+ * deterministic for a given shape and schedule but may differ in the last
+ * bits between them (partial sums are grouped differently). */
 int ctis_plan_autotune(ctis_plan* plan, const float* g_dev, void* stream);
 
 /* Reschedules one projector's work lists (forward != 0: the forward) as the

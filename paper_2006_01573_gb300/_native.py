@@ -21,6 +21,8 @@ _SOLVER = {"em": CTIS_SOLVER_EM, "sart": CTIS_SOLVER_SART, "smart": CTIS_SOLVER_
 _BOUNDARY = {"reject": CTIS_BOUNDARY_REJECT, "clip": CTIS_BOUNDARY_CLIP,
              "wrap": CTIS_BOUNDARY_WRAP}
 CTIS_INIT_ONES, CTIS_INIT_HTG = 1, 2
+CTIS_TILE_32X32, CTIS_TILE_32X16 = 0, 1
+_TILE = {"32x32": CTIS_TILE_32X32, "32x16": CTIS_TILE_32X16}
 NSTATS = 4
 STAT_NAMES = ("flux_hf", "flux_g", "loglik", "resid2")
 
@@ -56,7 +58,7 @@ class PlanInfo(ctypes.Structure):
         "fwd_tiles", "fwd_tasks", "fwd_items", "adj_tiles", "adj_tasks", "adj_items",
         "scratch_bytes", "dtype", "fwd_warps", "adj_warps", "fwd_chunk", "adj_chunk",
         "fwd_load_milli", "adj_load_milli", "fwd_split_q", "adj_split_q", "fwd_skew_pm",
-        "adj_skew_pm", "boundary")]
+        "adj_skew_pm", "boundary", "fwd_tile_w", "fwd_tile_h")]
 
 
 class TablesInfo(ctypes.Structure):
@@ -68,7 +70,8 @@ class TablesInfo(ctypes.Structure):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("tasks_per_item", ctypes.c_int),
                 ("item_overhead_q", ctypes.c_int), ("cta_skew_permille", ctypes.c_int),
-                ("boundary", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("boundary", ctypes.c_int), ("forward_tile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 def load(path: str = LIB_PATH):
@@ -153,7 +156,8 @@ def _stream(stream):
 
 def tables_inspect(a, alpha, w, gamma, xi, psf, forward: bool, n_ctas: int, dtype: str = "f32",
                    block_sm=None, tasks_per_item: int = 0, item_overhead_q: int = 0,
-                   cta_skew_permille: int = 0, boundary: str = "reject") -> dict:
+                   cta_skew_permille: int = 0, boundary: str = "reject",
+                   forward_tile: str = "32x32") -> dict:
     """Host-only view of one projector's work lists and schedule
     (ctis_tables_inspect; no device needed). Returns the info fields and the
     arrays as numpy int32 arrays."""
@@ -164,7 +168,7 @@ def tables_inspect(a, alpha, w, gamma, xi, psf, forward: bool, n_ctas: int, dtyp
     v, _ = _arr(psf[3], np.float32)
     i32 = lambda arr: None if arr is None else arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
-                      int(cta_skew_permille), _BOUNDARY[boundary])
+                      int(cta_skew_permille), _BOUNDARY[boundary], _TILE[forward_tile])
     bsm = None if block_sm is None else np.ascontiguousarray(block_sm, dtype=np.int32)
     dt = {"f32": CTIS_F32, "bf16": CTIS_BF16}[dtype]
     info = TablesInfo(ctypes.sizeof(TablesInfo))
@@ -200,7 +204,8 @@ class Plan:
     """
 
     def __init__(self, a, alpha, w, gamma, xi, psf, dtype: str = "f32", tasks_per_item: int = 0,
-                 item_overhead_q: int = 0, cta_skew_permille: int = 0, boundary: str = "reject"):
+                 item_overhead_q: int = 0, cta_skew_permille: int = 0, boundary: str = "reject",
+                 forward_tile: str = "32x32"):
         lib = load()
         ptr, _ = _arr(psf[0], np.int32)
         x, _ = _arr(psf[1], np.int32)
@@ -212,7 +217,7 @@ class Plan:
         handle = ctypes.c_void_p()
         i32 = lambda arr: arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         opt = PlanOptions(ctypes.sizeof(PlanOptions), int(tasks_per_item), int(item_overhead_q),
-                          int(cta_skew_permille), _BOUNDARY[boundary])
+                          int(cta_skew_permille), _BOUNDARY[boundary], _TILE[forward_tile])
         _check(lib.ctis_plan_create_ex(ctypes.byref(handle), a, alpha, w, gamma, xi, i32(ptr),
                                        i32(x), i32(y),
                                        v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
@@ -408,9 +413,10 @@ class Plan:
         _check(load().ctis_plan_check(self._h, _stream(stream)))
 
     def autotune(self, g, stream=None):
-        """Time the EM launches over candidate work schedules with ``g`` as the
-        measurement and keep the fastest (synchronous). Returns the chosen
-        schedules ``(forward, adjoint)`` (see ``schedules``)."""
+        """Time the EM launches over candidate work schedules (and, for the
+        forward, both tile shapes) with ``g`` as the measurement and keep the
+        fastest (synchronous). Returns the chosen schedules ``(forward,
+        adjoint)`` (see ``schedules``; ``forward_tile`` gives the shape)."""
         self._check_fpa(g)
         _check(load().ctis_plan_autotune(self._h, ctypes.c_void_p(g.data_ptr()), _stream(stream)))
         return self.schedules()
@@ -459,6 +465,12 @@ class Plan:
             raise ValueError(f"schedule kind must be 'chunk' or 'split', got {kind!r}")
         chunk, split = (int(value), 0) if kind == "chunk" else (0, int(value))
         _check(load().ctis_plan_set_schedule(self._h, 1 if forward else 0, chunk, split, int(skew)))
+
+    def forward_tile(self) -> str:
+        """The forward's output tile shape, ``"32x32"`` or ``"32x16"`` (the
+        plan's option until ``autotune`` picks the faster one)."""
+        i = self.info()
+        return f"{int(i['fwd_tile_w'])}x{int(i['fwd_tile_h'])}"
 
     def schedules(self):
         """The projectors' work schedules ``(forward, adjoint)``, each

@@ -5,9 +5,9 @@
 
 namespace ctis {
 
-cudaError_t gather_prepare_fwd(int K, int dtype, int* blocks_per_sm);
-cudaError_t gather_launch_fwd(int K, int dtype, const CUtensorMap& win, const GatherParams& p,
-                              cudaStream_t stream);
+cudaError_t gather_prepare_fwd(int K, int dtype, int shape, int* blocks_per_sm);
+cudaError_t gather_launch_fwd(int K, int dtype, int shape, const CUtensorMap& win,
+                              const GatherParams& p, cudaStream_t stream);
 cudaError_t gather_prepare_adj(int K, int dtype, int* blocks_per_sm);
 cudaError_t gather_launch_adj(int K, int dtype, const CUtensorMap& win, const GatherParams& p,
                               cudaStream_t stream);
@@ -151,17 +151,23 @@ __global__ void index_map_kernel(long long* out, int a, int alpha, int w, int ga
     }
 }
 
-// Calls fn(G{}) for the geometry serving (direction, K, dtype).
+// Calls fn(G{}) for the geometry serving (direction, K, dtype, forward tile
+// shape; the adjoint has shape 0 only).
 template <class Fn>
-int with_geo(bool forward, int K, int dtype, Fn&& fn) {
+int with_geo(bool forward, int K, int dtype, int shape, Fn&& fn) {
+    if (shape < 0 || shape >= kFwdShapes || (!forward && shape != 0)) return -1;
     auto by_k = [&](auto tin, auto tf, auto fwd) -> int {
         using TIn = decltype(tin);
         using TF = decltype(tf);
         constexpr bool F = decltype(fwd)::value;
+        auto by_shape = [&](auto kc) -> int {
+            constexpr int KK = decltype(kc)::value;
+            return shape == 1 ? fn(GeoOf<KK, TIn, TF, F, 1>{}) : fn(GeoOf<KK, TIn, TF, F, 0>{});
+        };
         switch (K) {
-            case 1: return fn(GeoOf<1, TIn, TF, F>{});
-            case 3: return fn(GeoOf<3, TIn, TF, F>{});
-            case 5: return fn(GeoOf<5, TIn, TF, F>{});
+            case 1: return by_shape(std::integral_constant<int, 1>{});
+            case 3: return by_shape(std::integral_constant<int, 3>{});
+            case 5: return by_shape(std::integral_constant<int, 5>{});
             default: return -1;
         }
     };
@@ -180,22 +186,23 @@ int with_geo(bool forward, int K, int dtype, Fn&& fn) {
 // ---------------------------------------------------------------------------
 // host entry points used by the plan / API code
 // ---------------------------------------------------------------------------
-int gather_tile_w(bool forward, int dtype) {
-    return with_geo(forward, 1, dtype, [](auto g) { return decltype(g)::TX; });
+int gather_tile_w(bool forward, int dtype, int shape) {
+    return with_geo(forward, 1, dtype, shape, [](auto g) { return decltype(g)::TX; });
 }
-int gather_tile_h(bool forward, int dtype) {
-    return with_geo(forward, 1, dtype, [](auto g) { return decltype(g)::TY; });
+int gather_tile_h(bool forward, int dtype, int shape) {
+    return with_geo(forward, 1, dtype, shape, [](auto g) { return decltype(g)::TY; });
 }
-int gather_window_rows(bool forward, int K, int dtype) {
-    return gather_tile_h(forward, dtype) + K - 1;
+int gather_window_rows(bool forward, int K, int dtype, int shape) {
+    return gather_tile_h(forward, dtype, shape) + K - 1;
 }
 int gather_warps_per_cta(bool forward) { return forward ? kShapeFwd.NW : kShapeAdj.NW; }
-int gather_box_w(bool forward, int K, int dtype) {
-    return with_geo(forward, K, dtype, [](auto g) { return decltype(g)::BXW; });
+int gather_box_w(bool forward, int K, int dtype, int shape) {
+    return with_geo(forward, K, dtype, shape, [](auto g) { return decltype(g)::BXW; });
 }
 int gather_weight_pad(bool forward, int K, int dtype) {
-    return with_geo(forward, K, dtype, [](auto g) { return decltype(g)::WPAD; });
+    return with_geo(forward, K, dtype, 0, [](auto g) { return decltype(g)::WPAD; });
 }
+int gather_fwd_shapes() { return kFwdShapes; }
 // x-shifted copies of a projector's input: 4 (float32: 16-byte alignment;
 // bfloat16: 8-byte alignment, the lanes taking the remaining shift of 0 or 4
 // elements inside a 16-byte aligned box)
@@ -205,14 +212,14 @@ int gather_input_copies(bool forward, int dtype) {
     return 4;
 }
 
-cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm) {
-    return forward ? gather_prepare_fwd(K, dtype, blocks_per_sm)
+cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm, int shape) {
+    return forward ? gather_prepare_fwd(K, dtype, shape, blocks_per_sm)
                    : gather_prepare_adj(K, dtype, blocks_per_sm);
 }
 
 cudaError_t gather_launch(bool forward, int K, int dtype, const CUtensorMap& win,
-                          const GatherParams& p, cudaStream_t stream) {
-    return forward ? gather_launch_fwd(K, dtype, win, p, stream)
+                          const GatherParams& p, cudaStream_t stream, int shape) {
+    return forward ? gather_launch_fwd(K, dtype, shape, win, p, stream)
                    : gather_launch_adj(K, dtype, win, p, stream);
 }
 

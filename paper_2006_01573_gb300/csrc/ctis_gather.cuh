@@ -241,7 +241,8 @@ struct Geo {
     static constexpr int TSTAT_OFF = FLAG_OFF + 16;       // [NW][4] float64 tile statistics
     static constexpr int BAR_OFF = TSTAT_OFF + NW * 4 * 8;
     static constexpr int SHIFT_OFF = BAR_OFF + NW * NS * 8;     // [NW][NS] lane shift per stage
-    static constexpr int SMEM_BYTES = SHIFT_OFF + (NW * NS * 4 + 15) / 16 * 16;
+    static constexpr int HEAD_OFF = SHIFT_OFF + (NW * NS * 4 + 15) / 16 * 16;   // [NW][3] first tasks
+    static constexpr int SMEM_BYTES = HEAD_OFF + NW * 3 * 16;
     static constexpr int ER = R / NW;   // epilogue rows of each lane's block per warp
     static_assert(R % NW == 0, "the epilogue splits a lane's rows evenly over the warps");
     // resident CTAs per SM the register budget must allow (4 x 4 warps = 16
@@ -908,15 +909,16 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         d.z = __shfl_sync(0xffffffffu, hv.z, src);
         d.w = __shfl_sync(0xffffffffu, hv.w, src);
     };
-    int4 h0, f0, f1, f2, i0, i1;
+    int4 h0, i0, i1;
     from(0, h0);
-    from(1, f0);
-    from(2, f1);
-    from(3, f2);
     from(4, i0);
     from(5, i1);
     const int ib = h0.x, ie = h0.y;
     if (ib >= ie) return;   // nothing issued, nothing to drain
+    // the first three task descriptors wait in shared memory for lane 0
+    int4* my_head = reinterpret_cast<int4*>(smem_raw + G::HEAD_OFF) + warp * 3;
+    if (lane >= 1 && lane <= 3) my_head[lane - 1] = hv;
+    __syncwarp();
     const int tx = lane % G::LX, ty = lane / G::LX;
     unsigned char* my_stages = smem_raw + warp * G::NS * G::STAGE_BYTES;
     uint64_t* my_bars = bars + warp * G::NS;
@@ -938,7 +940,11 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     bool failed = false;                                    // warp-uniform
     // lane 0: descriptor of issue_task; the first three come with the head,
     // the later ones are loaded one issue ahead
-    TaskDesc nxt{f0.x, f0.y, f0.z, f0.w};
+    TaskDesc nxt{};
+    if (lane == 0) {
+        const int4 f0 = my_head[0];
+        nxt = TaskDesc{f0.x, f0.y, f0.z, f0.w};
+    }
     const int head_end = issue_task + 3;
 
     auto issue_next = [&]() {
@@ -960,9 +966,12 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             }
             const int t1 = issue_task + 1;
             if (t1 < task_end) {
-                if (t1 == head_end - 2) nxt = TaskDesc{f1.x, f1.y, f1.z, f1.w};
-                else if (t1 == head_end - 1) nxt = TaskDesc{f2.x, f2.y, f2.z, f2.w};
-                else nxt = p.tasks[t1];
+                if (t1 < head_end) {
+                    const int4 f = my_head[t1 - (head_end - 3)];
+                    nxt = TaskDesc{f.x, f.y, f.z, f.w};
+                } else {
+                    nxt = p.tasks[t1];
+                }
             }
         }
         ++issue_task;
@@ -1232,21 +1241,31 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     __syncwarp();
 }
 
-// Every instantiation has 32 x 32 tiles: C = 4 columns x R = 8 rows per lane.
-// The forward of a bfloat16 plan reads bfloat16 windows, half the bytes of a
-// float32 window, and spends the freed shared memory on a third TMA stage
-// per warp (a deeper look-ahead on the window stream at the same 4 CTAs per
-// SM).
-template <bool FWD, typename TIn>
+// Tile shapes: C = 4 columns per lane, 8 lanes across (32 columns). Shape 0
+// (every adjoint, and the forward by default): R = 8 rows per lane, 32 x 32
+// tiles. Shape 1 (a forward alternative for small field stops, whose
+// footprints waste less of 16-row tiles): R = 4, 32 x 16 tiles, whose windows
+// are half as tall, so a third TMA stage fits. The forward of a bfloat16 plan
+// reads bfloat16 windows, half the bytes of a float32 window, and spends the
+// freed shared memory on a third TMA stage per warp (a deeper look-ahead on
+// the window stream at the same 4 CTAs per SM).
+constexpr int kFwdShapes = 2;
+
+template <bool FWD, typename TIn, int SHAPE>
 constexpr GatherShape shape_of() {
     GatherShape s = FWD ? kShapeFwd : kShapeAdj;
+    if (FWD && SHAPE == 1) {
+        s.R = 4;
+        s.NS = 3;
+    }
     if (FWD && sizeof(TIn) == 2) s.NS = CTIS_FWD_NS_BF16;
     return s;
 }
 
-template <int K, typename TIn, typename TF, bool FWD>
-using GeoOf = Geo<K, shape_of<FWD, TIn>().C, shape_of<FWD, TIn>().R, shape_of<FWD, TIn>().LX,
-                  shape_of<FWD, TIn>().NW, shape_of<FWD, TIn>().NS, TIn, TF>;
+template <int K, typename TIn, typename TF, bool FWD, int SHAPE = 0>
+using GeoOf = Geo<K, shape_of<FWD, TIn, SHAPE>().C, shape_of<FWD, TIn, SHAPE>().R,
+                  shape_of<FWD, TIn, SHAPE>().LX, shape_of<FWD, TIn, SHAPE>().NW,
+                  shape_of<FWD, TIn, SHAPE>().NS, TIn, TF>;
 
 template <class G, class Kern>
 cudaError_t prepare_kernel(Kern kern, int* blocks_per_sm) {

@@ -13,9 +13,10 @@ __global__ void __launch_bounds__(G::THREADS, G::MIN_BLOCKS)
     gather_body<G, TIn, TF, MODE>(tm_win, p);
 }
 
-// Calls fn(kernel, G{}) for the instantiation serving (K, dtype, mode).
+// Calls fn(kernel, G{}) for the instantiation serving (K, dtype, mode, tile
+// shape).
 template <class Fn>
-cudaError_t dispatch_fwd(int K, int dtype, int mode, Fn&& fn) {
+cudaError_t dispatch_fwd(int K, int dtype, int mode, int shape, Fn&& fn) {
     auto by_k = [&](auto tin, auto tf) -> cudaError_t {
         using TIn = decltype(tin);
         using TF = decltype(tf);
@@ -25,10 +26,16 @@ cudaError_t dispatch_fwd(int K, int dtype, int mode, Fn&& fn) {
             if (mode == kEpiRaw) return fn(forward_kernel<G, TIn, TF, kEpiRaw>, geo);
             return cudaErrorInvalidValue;
         };
+        auto by_shape = [&](auto kc) -> cudaError_t {
+            constexpr int KK = decltype(kc)::value;
+            if (shape == 1) return by_mode(GeoOf<KK, TIn, TF, true, 1>{});
+            if (shape == 0) return by_mode(GeoOf<KK, TIn, TF, true, 0>{});
+            return cudaErrorInvalidValue;
+        };
         switch (K) {
-            case 1: return by_mode(GeoOf<1, TIn, TF, true>{});
-            case 3: return by_mode(GeoOf<3, TIn, TF, true>{});
-            case 5: return by_mode(GeoOf<5, TIn, TF, true>{});
+            case 1: return by_shape(std::integral_constant<int, 1>{});
+            case 3: return by_shape(std::integral_constant<int, 3>{});
+            case 5: return by_shape(std::integral_constant<int, 5>{});
             default: return cudaErrorInvalidValue;
         }
     };
@@ -38,11 +45,11 @@ cudaError_t dispatch_fwd(int K, int dtype, int mode, Fn&& fn) {
 
 }  // namespace
 
-cudaError_t gather_prepare_fwd(int K, int dtype, int* blocks_per_sm) {
+cudaError_t gather_prepare_fwd(int K, int dtype, int shape, int* blocks_per_sm) {
     int lo = 1 << 30;
     for (int mode : {kEpiRaw, kEpiRatio}) {
         int b = 0;
-        const cudaError_t e = dispatch_fwd(K, dtype, mode, [&](auto kern, auto geo) {
+        const cudaError_t e = dispatch_fwd(K, dtype, mode, shape, [&](auto kern, auto geo) {
             return prepare_kernel<decltype(geo)>(kern, &b);
         });
         if (e != cudaSuccess) return e;
@@ -52,9 +59,9 @@ cudaError_t gather_prepare_fwd(int K, int dtype, int* blocks_per_sm) {
     return cudaSuccess;
 }
 
-cudaError_t gather_launch_fwd(int K, int dtype, const CUtensorMap& win, const GatherParams& p,
-                              cudaStream_t stream) {
-    return dispatch_fwd(K, dtype, p.mode, [&](auto kern, auto geo) {
+cudaError_t gather_launch_fwd(int K, int dtype, int shape, const CUtensorMap& win,
+                              const GatherParams& p, cudaStream_t stream) {
+    return dispatch_fwd(K, dtype, p.mode, shape, [&](auto kern, auto geo) {
         return launch_kernel<decltype(geo)>(kern, win, p, stream);
     });
 }

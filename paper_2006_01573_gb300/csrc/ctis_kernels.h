@@ -11,23 +11,26 @@ namespace ctis {
 constexpr int kDtypeF32 = 0;
 constexpr int kDtypeBF16 = 1;
 
-// Geometry of the instantiations serving each direction (forward = true).
-int gather_tile_w(bool forward, int dtype);         // output tile columns
-int gather_tile_h(bool forward, int dtype);         // output tile rows
-int gather_window_rows(bool forward, int K, int dtype);   // TMA box height (tile rows + K - 1)
+// Geometry of the instantiations serving each direction (forward = true) and,
+// for the forward, tile shape (0: 32 x 32 tiles, 1: 32 x 16; the adjoint has
+// shape 0 only). Invalid combinations return -1.
+int gather_tile_w(bool forward, int dtype, int shape = 0);   // output tile columns
+int gather_tile_h(bool forward, int dtype, int shape = 0);   // output tile rows
+int gather_window_rows(bool forward, int K, int dtype, int shape = 0);   // TMA box height
 int gather_warps_per_cta(bool forward);
-int gather_box_w(bool forward, int K, int dtype);   // TMA box width (elements)
+int gather_box_w(bool forward, int K, int dtype, int shape = 0);   // TMA box width (elements)
 int gather_weight_pad(bool forward, int K, int dtype);  // weight pairs per cluster, padded
 int gather_input_copies(bool forward, int dtype);       // x-shifted copies of the input
+int gather_fwd_shapes();                                // forward tile shapes built
 
 // Sets kernel attributes and returns the number of resident CTAs per SM for
-// the instantiation serving (direction, K, dtype). Call before capture.
-cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm);
+// the instantiation serving (direction, K, dtype, shape). Call before capture.
+cudaError_t gather_prepare(bool forward, int K, int dtype, int* blocks_per_sm, int shape = 0);
 
 // Enqueues one projector pass over p.n_warps independent warps. `win` is the
 // tensor map of the input copies with box (box_w, window_rows, 1).
 cudaError_t gather_launch(bool forward, int K, int dtype, const CUtensorMap& win,
-                          const GatherParams& p, cudaStream_t stream);
+                          const GatherParams& p, cudaStream_t stream, int shape = 0);
 
 // The ratio step of a wavelength-sharded EM iteration (ctis_shard.cu): u = g
 // / q (0 where q = 0) into the FPA copies; with stats_out, the four

@@ -168,6 +168,7 @@ struct ctis_plan {
     std::vector<Cluster> clusters;
     std::vector<int32_t> tap_slot;   // cluster * K*K + dy*K + dx of every stored tap
     ProjTables fwd, adj;
+    int fwd_shape = 0;               // forward tile shape (0: 32 x 32, 1: 32 x 16)
     int adj_tiles_per_plane = 0;
     int* d_tap_slot = nullptr;
     int* d_tap_s = nullptr;
@@ -184,8 +185,10 @@ struct ctis_plan {
     float* d_scratch = nullptr;
     int64_t scratch_capacity = 0;    // float elements of d_scratch
     int* d_tickets = nullptr;
+    size_t tickets_capacity = 0;      // ints in d_tickets
     int* d_counters = nullptr;   // [3] error flag, [8] the frame reduction's ticket
     double* d_tile_stats = nullptr;
+    size_t tile_stats_capacity = 0;   // forward tiles d_tile_stats holds
     double* d_red_part = nullptr;   // [kStatSlices][kNumStats] frame reduction slices
     int64_t device_bytes = 0;
     cudaStream_t cap_stream = nullptr;
@@ -730,6 +733,69 @@ int64_t pos_key(int64_t x, int64_t y) {
     return static_cast<int64_t>((static_cast<uint64_t>(y) << 32) ^ static_cast<uint32_t>(x));
 }
 
+// Forward work lists (FPA tiles of the plan's forward tile shape x clusters
+// whose footprint meets them) and their schedule over warps_fwd warps.
+void build_forward_lists(ctis_plan* P, int warps_fwd) {
+    const int K = P->K, a = P->a, al = P->alpha, w = P->w, ga = P->gamma, xi = P->xi;
+    const int64_t ncl = static_cast<int64_t>(P->clusters.size());
+    ProjTables& T = P->fwd;
+    T.tiles.clear();
+    T.items.clear();
+    T.tile_tasks.clear();
+    const int TX = T.tile_w = gather_tile_w(true, P->dtype, P->fwd_shape);
+    const int TY = T.tile_h = gather_tile_h(true, P->dtype, P->fwd_shape);
+    T.nw = gather_warps_per_cta(true);
+    const int ntx = (ga + TX - 1) / TX, nty = (xi + TY - 1) / TY;
+    const int fw = a + K - 1, fh = al + K - 1;   // footprint of one cluster
+    std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
+    for (int64_t c = 0; c < ncl; ++c) {
+        const Cluster& cl = P->clusters[c];
+        // the tiles that the footprint's part on the FPA meets (under
+        // clipping the footprint may reach past any edge, or miss the FPA
+        // altogether; a cluster box may also reach past its last tap)
+        const int64_t fx0 = std::max<int64_t>(0, cl.X);
+        const int64_t fx1 = std::min<int64_t>(ga, int64_t{cl.X} + fw);
+        const int64_t fy0 = std::max<int64_t>(0, cl.Y);
+        const int64_t fy1 = std::min<int64_t>(xi, int64_t{cl.Y} + fh);
+        if (fx0 >= fx1 || fy0 >= fy1) continue;
+        const int64_t tx0 = fx0 / TX, tx1 = (fx1 - 1) / TX;
+        const int64_t ty0 = fy0 / TY, ty1 = (fy1 - 1) / TY;
+        for (int64_t ty = ty0; ty <= ty1; ++ty)
+            for (int64_t tx = tx0; tx <= tx1; ++tx)
+                per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));
+    }
+    // Tiles no footprint meets hold H f = 0 whatever f is: they are left out
+    // of the lists (the raw forward zeroes its output first; the ratio's
+    // u copies and the tile statistics are zero there).
+    std::vector<int> begin{0};
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            if (per_tile[static_cast<size_t>(ty) * ntx + tx].empty()) continue;
+            TileDesc td{};
+            td.x0 = tx * TX;
+            td.y0 = ty * TY;
+            td.plane = 0;
+            T.tiles.push_back(td);
+            std::vector<TaskDesc> tl;
+            for (int c : per_tile[static_cast<size_t>(ty) * ntx + tx]) {
+                const Cluster& cl = P->clusters[c];
+                const int64_t px = static_cast<int64_t>(td.x0) - cl.X - (K - 1);
+                const int64_t py = static_cast<int64_t>(td.y0) - cl.Y - (K - 1);
+                const int64_t q = floor_mod(-px, P->f_copies);   // copy holding px aligned
+                TaskDesc t;
+                t.wx = static_cast<int>(px + q);
+                t.wy = static_cast<int>(py);
+                t.plane = static_cast<int>(q) * w + cl.s;   // copy * w + s
+                t.cluster = c;
+                tl.push_back(t);
+            }
+            T.tile_tasks.insert(T.tile_tasks.end(), tl.begin(), tl.end());
+            begin.push_back(static_cast<int>(T.tile_tasks.size()));
+        }
+    T.tile_task_begin = std::move(begin);
+    schedule(T, warps_fwd, P->forced_per_item, P->forced_split_q, P->forced_skew_pm);
+}
+
 int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int32_t* psf_y,
           const float* psf_val) {
     const int a = P->a, al = P->alpha, w = P->w, ga = P->gamma, xi = P->xi;
@@ -866,7 +932,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     int warps_fwd = P->host_ctas * gather_warps_per_cta(true);
     int warps_adj = P->host_ctas * gather_warps_per_cta(false);
     if (P->host_ctas == 0) {
-        CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm));
+        CTIS_CUDA(gather_prepare(true, K, P->dtype, &P->fwd.blocks_per_sm, P->fwd_shape));
         CTIS_CUDA(gather_prepare(false, K, P->dtype, &P->adj.blocks_per_sm));
         int grad_blocks = 0;   // runs on the adjoint's work lists and warp count
         CTIS_CUDA(psf_grad_prepare(K, P->dtype, &grad_blocks));
@@ -874,61 +940,7 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
         warps_adj = P->num_sms * P->adj.blocks_per_sm * gather_warps_per_cta(false);
     }
 
-    // ---- forward work lists: FPA tiles x clusters whose footprint meets them
-    {
-        ProjTables& T = P->fwd;
-        const int TX = T.tile_w = gather_tile_w(true, P->dtype), TY = T.tile_h = gather_tile_h(true, P->dtype);
-        T.nw = gather_warps_per_cta(true);
-        const int ntx = (ga + TX - 1) / TX, nty = (xi + TY - 1) / TY;
-        const int fw = a + K - 1, fh = al + K - 1;   // footprint of one cluster
-        std::vector<std::vector<int>> per_tile(static_cast<size_t>(ntx) * nty);
-        for (int64_t c = 0; c < ncl; ++c) {
-            const Cluster& cl = P->clusters[c];
-            // the tiles that the footprint's part on the FPA meets (under
-            // clipping the footprint may reach past any edge, or miss the FPA
-            // altogether; a cluster box may also reach past its last tap)
-            const int64_t fx0 = std::max<int64_t>(0, cl.X);
-            const int64_t fx1 = std::min<int64_t>(ga, int64_t{cl.X} + fw);
-            const int64_t fy0 = std::max<int64_t>(0, cl.Y);
-            const int64_t fy1 = std::min<int64_t>(xi, int64_t{cl.Y} + fh);
-            if (fx0 >= fx1 || fy0 >= fy1) continue;
-            const int64_t tx0 = fx0 / TX, tx1 = (fx1 - 1) / TX;
-            const int64_t ty0 = fy0 / TY, ty1 = (fy1 - 1) / TY;
-            for (int64_t ty = ty0; ty <= ty1; ++ty)
-                for (int64_t tx = tx0; tx <= tx1; ++tx)
-                    per_tile[static_cast<size_t>(ty) * ntx + tx].push_back(static_cast<int>(c));
-        }
-        // Tiles no footprint meets hold H f = 0 whatever f is: they are left out
-        // of the lists (the raw forward zeroes its output first; the ratio's
-        // u copies and the tile statistics are zero there).
-        std::vector<int> begin{0};
-        for (int ty = 0; ty < nty; ++ty)
-            for (int tx = 0; tx < ntx; ++tx) {
-                if (per_tile[static_cast<size_t>(ty) * ntx + tx].empty()) continue;
-                TileDesc td{};
-                td.x0 = tx * TX;
-                td.y0 = ty * TY;
-                td.plane = 0;
-                T.tiles.push_back(td);
-                std::vector<TaskDesc> tl;
-                for (int c : per_tile[static_cast<size_t>(ty) * ntx + tx]) {
-                    const Cluster& cl = P->clusters[c];
-                    const int64_t px = static_cast<int64_t>(td.x0) - cl.X - (K - 1);
-                    const int64_t py = static_cast<int64_t>(td.y0) - cl.Y - (K - 1);
-                    const int64_t q = floor_mod(-px, P->f_copies);   // copy holding px aligned
-                    TaskDesc t;
-                    t.wx = static_cast<int>(px + q);
-                    t.wy = static_cast<int>(py);
-                    t.plane = static_cast<int>(q) * w + cl.s;   // copy * w + s
-                    t.cluster = c;
-                    tl.push_back(t);
-                }
-                T.tile_tasks.insert(T.tile_tasks.end(), tl.begin(), tl.end());
-                begin.push_back(static_cast<int>(T.tile_tasks.size()));
-            }
-        T.tile_task_begin = std::move(begin);
-        schedule(T, warps_fwd, P->forced_per_item, P->forced_split_q, P->forced_skew_pm);
-    }
+    build_forward_lists(P, warps_fwd);
 
     // ---- adjoint work lists: voxel tiles of wavelength s x clusters of s
     {
@@ -1008,6 +1020,8 @@ int build(ctis_plan* P, const int32_t* psf_ptr, const int32_t* psf_x, const int3
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_counters), sizeof(int) * 16);
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
                           sizeof(double) * kNumStats * P->fwd.tiles.size());
+    P->tickets_capacity = ntiles;
+    P->tile_stats_capacity = P->fwd.tiles.size();
     if (!rc) rc = dmalloc(P, reinterpret_cast<void**>(&P->d_red_part),
                           sizeof(double) * kNumStats * kStatSlices);
     if (rc) return rc;
@@ -1138,10 +1152,10 @@ int enqueue_forward(const ctis_plan* P, GatherParams p, cudaStream_t st) {
     CUtensorMap win;
     const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
     int rc = make_map(&win, P->d_fwork, P->dtype, P->a + P->f_copies - 1, P->alpha,
-                      P->w * P->f_copies, P->a_pitch, plane, gather_box_w(true, P->K, P->dtype),
-                      gather_window_rows(true, P->K, P->dtype));
+                      P->w * P->f_copies, P->a_pitch, plane, gather_box_w(true, P->K, P->dtype, P->fwd_shape),
+                      gather_window_rows(true, P->K, P->dtype, P->fwd_shape));
     if (rc) return rc;
-    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st, P->fwd_shape));
     return CTIS_OK;
 }
 
@@ -1179,6 +1193,42 @@ void probe_placement(ctis_plan* P, ProjTables& T, bool forward) {
     }
     cudaGetLastError();
     cudaFree(d);
+}
+
+// Switches the forward projector to tile shape `shape`: its kernel's launch
+// resources, its work lists (same schedule parameters), the tile tickets and
+// statistics grown to the new tile count, and its probed placement. The
+// caller has synchronised the device and dropped the tables' users.
+int set_forward_shape(ctis_plan* P, int shape) {
+    P->fwd_shape = shape;
+    CTIS_CUDA(gather_prepare(true, P->K, P->dtype, &P->fwd.blocks_per_sm, shape));
+    P->fwd.block_sm.clear();
+    build_forward_lists(P, P->num_sms * P->fwd.blocks_per_sm * gather_warps_per_cta(true));
+    const size_t ntiles = std::max(P->fwd.tiles.size(), P->adj.tiles.size());
+    if (ntiles > P->tickets_capacity) {
+        cudaFree(P->d_tickets);
+        P->d_tickets = nullptr;
+        P->tickets_capacity = 0;
+        const int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tickets), sizeof(int) * ntiles);
+        if (rc) return rc;
+        CTIS_CUDA(cudaMemset(P->d_tickets, 0, sizeof(int) * ntiles));
+        P->tickets_capacity = ntiles;
+    }
+    if (P->fwd.tiles.size() > P->tile_stats_capacity) {
+        cudaFree(P->d_tile_stats);
+        P->d_tile_stats = nullptr;
+        P->tile_stats_capacity = 0;
+        const int rc = dmalloc(P, reinterpret_cast<void**>(&P->d_tile_stats),
+                               sizeof(double) * kNumStats * P->fwd.tiles.size());
+        if (rc) return rc;
+        P->tile_stats_capacity = P->fwd.tiles.size();
+    }
+    int rc = reupload_tables(P, P->fwd);
+    if (rc) return rc;
+    probe_placement(P, P->fwd, true);
+    if (P->fwd.block_sm.empty()) return CTIS_OK;
+    schedule(P->fwd, P->fwd.n_warps, P->fwd.per_item, P->fwd.split_q, P->fwd.skew_pm);
+    return reupload_tables(P, P->fwd);
 }
 
 // Probes both projectors' placements and, when the maps came back, lays the
@@ -1629,9 +1679,9 @@ int batch_forward(const ctis_plan* P, const BatchState* B, GatherParams p, cudaS
     const int64_t plane = static_cast<int64_t>(P->a_pitch) * P->alpha;
     int rc = make_map(&win, B->d_fwork, P->dtype, P->a + P->f_copies - 1, P->alpha,
                       P->w * B->F * P->f_copies, P->a_pitch, plane,
-                      gather_box_w(true, P->K, P->dtype), gather_window_rows(true, P->K, P->dtype));
+                      gather_box_w(true, P->K, P->dtype, P->fwd_shape), gather_window_rows(true, P->K, P->dtype, P->fwd_shape));
     if (rc) return rc;
-    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st, P->fwd_shape));
     return CTIS_OK;
 }
 
@@ -1834,6 +1884,7 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
              const ctis_plan_options* opt) {
     if (!out) return fail(CTIS_ERR_INVALID_ARG, "out is NULL");
     int forced_per_item = 0, forced_split_q = 0, forced_skew_pm = 0, boundary = 0;
+    int forward_tile = CTIS_TILE_32X32;
     if (opt) {
         if (opt->struct_size != static_cast<int>(sizeof(ctis_plan_options)))
             return fail(CTIS_ERR_INVALID_ARG, "ctis_plan_options.struct_size mismatch");
@@ -1851,6 +1902,9 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
             opt->boundary != CTIS_BOUNDARY_WRAP)
             return fail(CTIS_ERR_INVALID_ARG,
                         "boundary must be CTIS_BOUNDARY_REJECT, _CLIP or _WRAP");
+        if (opt->forward_tile != CTIS_TILE_32X32 && opt->forward_tile != CTIS_TILE_32X16)
+            return fail(CTIS_ERR_INVALID_ARG, "forward_tile must be CTIS_TILE_32X32 or CTIS_TILE_32X16");
+        forward_tile = opt->forward_tile;
         boundary = opt->boundary;
         forced_per_item = opt->tasks_per_item;
         forced_split_q = opt->item_overhead_q;
@@ -1900,6 +1954,7 @@ int new_plan(ctis_plan** out, int a, int alpha, int w, int gamma, int xi, const 
     P->forced_skew_pm = forced_skew_pm;
     P->clip = boundary != CTIS_BOUNDARY_REJECT;
     P->wrap = boundary == CTIS_BOUNDARY_WRAP;
+    P->fwd_shape = forward_tile;
     // copies are NC - 1 elements wider than the plane (see TaskDesc)
     // (a multiple of 16 bytes: the window map's row stride)
     P->a_pitch = static_cast<int>(round_up(a + P->f_copies - 1, dtype == CTIS_BF16 ? 8 : 4));
@@ -2106,6 +2161,8 @@ int ctis_plan_get_info(const ctis_plan* P, ctis_plan_info* info) {
     info->adj_skew_pm = P->adj.skew_pm;
     info->boundary = P->wrap ? CTIS_BOUNDARY_WRAP
                              : (P->clip ? CTIS_BOUNDARY_CLIP : CTIS_BOUNDARY_REJECT);
+    info->fwd_tile_w = P->fwd.tile_w;
+    info->fwd_tile_h = P->fwd.tile_h;
     return CTIS_OK;
 }
 
@@ -2342,8 +2399,8 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
                                     0.f, st));
     CUtensorMap win;
     rc = make_map(&win, copies, P->dtype, P->a + P->f_copies - 1, P->alpha, P->w * P->f_copies,
-                  P->a_pitch, plane, gather_box_w(true, P->K, P->dtype),
-                  gather_window_rows(true, P->K, P->dtype));
+                  P->a_pitch, plane, gather_box_w(true, P->K, P->dtype, P->fwd_shape),
+                  gather_window_rows(true, P->K, P->dtype, P->fwd_shape));
     if (rc) return rc;
     GatherParams p = base_params(P, P->fwd);
     p.scratch = reinterpret_cast<float*>(base + o_partials);
@@ -2357,7 +2414,7 @@ int ctis_forward_static_scratch(const ctis_plan* P, const void* f_dev, float* hf
     p.out_plane_stride = 0;
     rc = zero_raw_output(p, st);
     if (rc) return rc;
-    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st));
+    CTIS_CUDA(gather_launch(true, P->K, P->dtype, win, p, st, P->fwd_shape));
     return CTIS_OK;
 }
 
@@ -2819,50 +2876,83 @@ int ctis_plan_autotune(ctis_plan* P, const float* g_dev, void* stream) {
         for (int q : {12, 16, 20}) cands.push_back({0, q, skew});
     }
     int result = CTIS_OK;
-    for (ProjTables* T : {&P->fwd, &P->adj}) {
-        const bool forward = T == &P->fwd;
-        // milliseconds per launch of candidate c over `reps` launches (after
-        // two warm-up launches); < 0 when something failed (result is set)
-        auto time_cand = [&](const Cand& c, int reps) -> float {
-            schedule(*T, T->n_warps, c.chunk, c.split_q, c.skew_pm);
-            result = reupload(*T);
-            for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
-            cudaError_t e = result ? cudaSuccess : cudaEventRecord(e0, st);
-            for (int r = 0; r < reps && !result && e == cudaSuccess; ++r) result = run(forward);
-            if (!result && e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (!result && e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (!result && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (!result && e != cudaSuccess) result = cuda_fail(e, "timing a candidate schedule");
-            return result ? -1.f : ms / reps;
-        };
-        // a first pass over all candidates, then the four fastest again,
-        // interleaved over three rounds of 10 launches, to keep the timing
-        // noise out of the choice
+    // milliseconds per launch of the projector's current tables over `reps`
+    // launches (after two warm-up launches); < 0 when something failed
+    // (result is set)
+    auto time_now = [&](bool forward, int reps) -> float {
+        for (int r = 0; r < 2 && !result; ++r) result = run(forward);   // warm-up
+        cudaError_t e = result ? cudaSuccess : cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !result && e == cudaSuccess; ++r) result = run(forward);
+        if (!result && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!result && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (!result && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (!result && e != cudaSuccess) result = cuda_fail(e, "timing a candidate schedule");
+        return result ? -1.f : ms / reps;
+    };
+    auto time_cand = [&](ProjTables* T, const Cand& c, int reps) -> float {
+        schedule(*T, T->n_warps, c.chunk, c.split_q, c.skew_pm);
+        result = reupload(*T);
+        return result ? -1.f : time_now(T == &P->fwd, reps);
+    };
+    // The best schedule of the projector's current tables: a first pass over
+    // all candidates, then the four fastest again, interleaved over three
+    // rounds of 10 launches, to keep the timing noise out of the choice.
+    auto tune = [&](ProjTables* T) -> Cand {
         std::vector<std::pair<float, Cand>> timed;
         for (const Cand& c : cands) {
-            const float ms = time_cand(c, 5);
+            const float ms = time_cand(T, c, 5);
             if (ms < 0.f) break;
             timed.push_back({ms, {T->per_item, T->split_q, T->skew_pm}});
         }
-        if (result) break;
+        if (result) return Cand{};
         std::stable_sort(timed.begin(), timed.end(),
                          [](const auto& x, const auto& y) { return x.first < y.first; });
         timed.resize(std::min<size_t>(timed.size(), 4));
         std::vector<float> total(timed.size(), 0.f);
         for (int round = 0; round < 3 && !result; ++round)
             for (size_t i = 0; i < timed.size() && !result; ++i) {
-                const float ms = time_cand(timed[i].second, 10);
+                const float ms = time_cand(T, timed[i].second, 10);
                 if (ms >= 0.f) total[i] += ms;
             }
-        if (result) break;
         size_t bi = 0;
         for (size_t i = 1; i < timed.size(); ++i)
             if (total[i] < total[bi]) bi = i;
-        const Cand best = timed[bi].second;
-        schedule(*T, T->n_warps, best.chunk, best.split_q, best.skew_pm);
-        result = reupload(*T);
-        if (result) break;
+        return timed.empty() ? Cand{} : timed[bi].second;
+    };
+    // Forward: every tile shape with its own best schedule, then the shapes'
+    // winners against each other, interleaved over three rounds.
+    const int nshapes = gather_fwd_shapes();
+    std::vector<Cand> shape_best(nshapes);
+    for (int sh = 0; sh < nshapes && !result; ++sh) {
+        result = set_forward_shape(P, sh);
+        if (!result) shape_best[sh] = tune(&P->fwd);
+    }
+    int best_shape = 0;
+    if (!result && nshapes > 1) {
+        std::vector<float> total(nshapes, 0.f);
+        for (int round = 0; round < 3 && !result; ++round)
+            for (int sh = 0; sh < nshapes && !result; ++sh) {
+                if (P->fwd_shape != sh) result = set_forward_shape(P, sh);
+                const float ms = result ? -1.f : time_cand(&P->fwd, shape_best[sh], 10);
+                if (ms >= 0.f) total[sh] += ms;
+            }
+        for (int sh = 1; sh < nshapes; ++sh)
+            if (total[sh] < total[best_shape]) best_shape = sh;
+    }
+    if (!result && P->fwd_shape != best_shape) result = set_forward_shape(P, best_shape);
+    if (!result) {
+        const Cand& b = shape_best[best_shape];
+        schedule(P->fwd, P->fwd.n_warps, b.chunk, b.split_q, b.skew_pm);
+        result = reupload(P->fwd);
+    }
+    // adjoint: one tile shape
+    if (!result) {
+        const Cand b = tune(&P->adj);
+        if (!result) {
+            schedule(P->adj, P->adj.n_warps, b.chunk, b.split_q, b.skew_pm);
+            result = reupload(P->adj);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

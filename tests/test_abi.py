@@ -104,7 +104,7 @@ def test_header_constants_match_the_binding():
     consts = {name: int(val) for name, val in re.findall(r"\b(CTIS_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
     for name in ("CTIS_F32", "CTIS_BF16", "CTIS_BOUNDARY_REJECT", "CTIS_BOUNDARY_CLIP",
                  "CTIS_BOUNDARY_WRAP", "CTIS_SOLVER_EM", "CTIS_SOLVER_SART", "CTIS_SOLVER_SMART",
-                 "CTIS_INIT_ONES", "CTIS_INIT_HTG"):
+                 "CTIS_INIT_ONES", "CTIS_INIT_HTG", "CTIS_TILE_32X32", "CTIS_TILE_32X16"):
         assert consts[name] == getattr(_native, name), name
     assert consts["CTIS_NSTATS"] == _native.NSTATS
     assert consts["CTIS_DEBUG_DROP_COPIES"] == 1

@@ -63,8 +63,8 @@ def _blob_case():
 CASES["blob_split"] = _blob_case()
 
 
-def _plan(wl, psf, dtype="f32"):
-    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype)
+def _plan(wl, psf, dtype="f32", forward_tile="32x32"):
+    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype, forward_tile=forward_tile)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -104,13 +104,15 @@ def test_delta_psf_forward_is_exact_paste():
     assert np.array_equal(hf, expect)
 
 
+@pytest.mark.parametrize("tile", ["32x32", "32x16"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_forward_parity(name):
+def test_forward_parity(name, tile):
     wl, psf = CASES[name]
     geom = geometry(wl)
     H = O.build_H(geom, psf)
     f = synth.random_positive((wl.w, wl.alpha, wl.a), 11)
-    with _plan(wl, psf) as plan:
+    with _plan(wl, psf, forward_tile=tile) as plan:
+        assert plan.forward_tile() == tile
         hf = plan.forward(torch.from_numpy(f).cuda())
         plan.check()
         hf = hf.cpu().numpy()

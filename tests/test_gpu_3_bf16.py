@@ -49,8 +49,8 @@ def _bf16_H(wl, psf):
     return geom, O.with_values(taps, stored)
 
 
-def _plan(wl, psf):
-    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16")
+def _plan(wl, psf, forward_tile="32x32"):
+    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype="bf16", forward_tile=forward_tile)
 
 
 def _bf16_cube(wl, seed):
@@ -71,13 +71,15 @@ def test_bf16_tables_hold_rounded_values(name):
     np.testing.assert_allclose(h, h_ref, rtol=1.2e-7, atol=0)
 
 
+@pytest.mark.parametrize("tile", ["32x32", "32x16"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_bf16_forward_parity(name):
+def test_bf16_forward_parity(name, tile):
     wl = CASES[name]
     psf = synth.make_psf(wl)
     geom, taps = _bf16_H(wl, psf)
     f, ft = _bf16_cube(wl, 61)
-    with _plan(wl, psf) as plan:
+    with _plan(wl, psf, tile) as plan:
+        assert plan.forward_tile() == tile
         hf = plan.forward(ft)
         plan.check()
         hf = hf.cpu().numpy()

@@ -34,6 +34,7 @@ def test_autotuned_plan_matches_oracle_and_is_reproducible():
         gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
         fc, ac = plan.autotune(gt)
         assert fc in CANDIDATES | {model_choice[0]} and ac in CANDIDATES | {model_choice[1]}
+        assert plan.forward_tile() in ("32x32", "32x16")
         a, _ = plan.reconstruct(gt, k=wl.k, init="ones")
         a = a.clone()
         b, _ = plan.reconstruct(gt, k=wl.k, init="ones")
@@ -123,3 +124,48 @@ def test_set_schedule_reapplies_a_schedule():
         from paper_2006_01573_gb300 import CtisError
         with pytest.raises(CtisError):
             plan.set_schedule(True, ("chunk", 16, 901))
+
+
+STAT_KEYS = ("flux_hf", "flux_g_covered", "loglik", "resid2")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_32x16_forward_tiles_in_em_and_statistics(dtype):
+    """EM on 32 x 16 forward tiles (the fused ratio and the per-tile
+    statistics over twice as many tiles). float32: iterates and statistics
+    within the parity bounds of the oracle. bfloat16: iterates within the
+    bound of the oracle EM that stores every iterate in bfloat16, and the
+    same statistics as the 32 x 32 run up to the rounding of a few iterate
+    elements (the tiles regroup float32 partial sums, so an element may round
+    to the neighbouring bfloat16 value)."""
+    for wl in (synth.TINY, synth.Workload("ragged", 13, 11, 3, 49, 43, 3, 14.0, 1.0, 3, 0.7,
+                                          "mask_spectra", 100.0, 5)):
+        geom, psf, H, _, g = problem(wl)
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        runs = {}
+        for tile in ("32x32", "32x16"):
+            with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype,
+                      forward_tile=tile) as plan:
+                assert plan.forward_tile() == tile
+                got, st = plan.reconstruct(gt, k=wl.k, init="ones", stats=True)
+                plan.check()
+                runs[tile] = (got.float().cpu().numpy().ravel(), st.cpu().numpy())
+        got, st = runs["32x16"]
+        if dtype == "f32":
+            ref, hist = O.mlem(H, g, wl.k)
+            assert floored_rel(got, ref) <= wl.k * 1e-5, wl.name
+            assert rel_l2(got, ref) <= 1e-5 * np.sqrt(wl.k), wl.name
+            for t in range(wl.k + 1):
+                for q, key in enumerate(STAT_KEYS):
+                    assert abs(st[t, q] - hist[t][key]) <= 1e-5 * abs(hist[t][key]), (wl.name, t, key)
+        else:
+            taps = O.merge_psf(geom, psf)
+            stored = O.round_bf16(taps.v.astype(np.float32)).astype(np.float64)
+            Hb = O.BlockH(geom, O.with_values(taps, stored))
+            store = lambda z: O.round_bf16(z.astype(np.float32))   # noqa: E731
+            f_stored = np.ones(geom.m)
+            for _ in range(wl.k):
+                f_stored = O.em_step_stored(Hb, g, f_stored, store)
+            assert rel_l2(got, f_stored) <= 4 * 2.0 ** -8, wl.name
+            base = runs["32x32"][1]
+            assert np.all(np.abs(st - base) <= 1e-3 * np.abs(base)), wl.name

@@ -67,13 +67,16 @@ def test_clusters_cover_every_psf_nonzero(case):
         assert np.any((X <= xs) & (xs < X + K) & (Y <= ys) & (ys < Y + K))
 
 
+@pytest.mark.parametrize("tile", ["32x32", "32x16"])
 @pytest.mark.parametrize("case", CASES, ids=_case_id)
-def test_forward_tasks_are_the_footprint_overlaps(case):
+def test_forward_tasks_are_the_footprint_overlaps(case, tile):
     """A forward task exists exactly when the cluster's footprint meets an FPA
-    tile (under clipping only its part on the FPA counts)."""
+    tile (under clipping only its part on the FPA counts), for either forward
+    tile shape."""
     wl, shift = case
-    t = _inspect(wl, True, 8, shift)
+    t = _inspect(wl, True, 8, shift, forward_tile=tile)
     K, TW, TH = t["cluster_k"], t["tile_w"], t["tile_h"]
+    assert (TW, TH) == ((32, 32) if tile == "32x32" else (32, 16))
     expect = {}
     for c, (s, X, Y) in enumerate(t["cluster_sxy"]):
         # the footprint's part on the FPA: [x0, x1) x [y0, y1)
@@ -348,13 +351,15 @@ def _random_case(seed, boundary):
 
 @pytest.mark.parametrize("seed", range(20))
 @pytest.mark.parametrize("boundary", ["reject", "clip"])
-def test_random_work_lists_follow_their_definitions(seed, boundary):
+@pytest.mark.parametrize("tile", ["32x32", "32x16"])
+def test_random_work_lists_follow_their_definitions(seed, boundary, tile):
     """Random geometries and blob PSFs: forward tasks are exactly the
     (tile, cluster) pairs whose footprint (its part on the FPA) meets the
     tile; adjoint tiles list the clusters of their plane whose window meets
     the FPA; every schedule runs every task once."""
     wl, psf = _random_case(seed, boundary)
-    tf = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 6, boundary=boundary)
+    tf = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 6, boundary=boundary,
+                        forward_tile=tile)
     K, TW, TH = tf["cluster_k"], tf["tile_w"], tf["tile_h"]
     expect = {}
     for c, (s, X, Y) in enumerate(tf["cluster_sxy"]):
