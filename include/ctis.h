@@ -267,14 +267,19 @@ int ctis_reconstruct_solver(const ctis_plan* plan, const float* g_dev, void* f_d
  * number of forward and adjoint launches. Any output pointer may be NULL. */
 int ctis_plan_set_profiling(ctis_plan* plan, int enable);
 
-/* Test hook for the bounded waits. With CTIS_DEBUG_DROP_COPIES the gather
+/* Test and measurement hooks. With CTIS_DEBUG_DROP_COPIES the gather
  * kernels arm each copy's barrier without issuing the copy, so every wait of
  * every warp runs out (after about 2^31 SM cycles, ~1 s), the kernel records
  * the failure, skips its remaining copies and returns; ctis_plan_check then
  * reports CTIS_ERR_TIMEOUT and the context stays usable. Results are
- * undefined while it is set. flags = 0 restores normal operation. Waits for
- * the device and drops the plan's cached graphs. */
-enum { CTIS_DEBUG_DROP_COPIES = 1 };
+ * undefined while it is set. CTIS_DEBUG_SERIAL_LAUNCH launches the projector
+ * kernels as plain launches instead of with programmatic dependent launch
+ * (by default a projector kernel is scheduled as soon as every CTA of the
+ * stream's previous projector has finished its work, and its prologue, which
+ * reads only the plan's work lists, runs while that grid drains and exits;
+ * the results are the same either way). flags = 0 restores normal operation. Waits for the
+ * device and drops the plan's cached graphs. */
+enum { CTIS_DEBUG_DROP_COPIES = 1, CTIS_DEBUG_SERIAL_LAUNCH = 2 };
 int ctis_plan_set_debug(ctis_plan* plan, int flags);
 int ctis_plan_kernel_times(const ctis_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,
                            int* n_adj);

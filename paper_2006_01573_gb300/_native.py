@@ -348,11 +348,14 @@ class Plan:
         _check(load().ctis_index_map(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
 
-    def set_debug(self, drop_copies: bool):
-        """Test hook (ctis_plan_set_debug): with ``drop_copies`` every bounded
-        wait in the gather kernels runs out and ``check()`` raises
-        CTIS_ERR_TIMEOUT."""
-        _check(load().ctis_plan_set_debug(self._h, 1 if drop_copies else 0))
+    def set_debug(self, drop_copies: bool = False, serial_launch: bool = False):
+        """Test and measurement hooks (ctis_plan_set_debug): with
+        ``drop_copies`` every bounded wait in the gather kernels runs out and
+        ``check()`` raises CTIS_ERR_TIMEOUT; with ``serial_launch`` the
+        projectors are plain launches instead of programmatic dependent
+        launches."""
+        _check(load().ctis_plan_set_debug(self._h, (1 if drop_copies else 0) |
+                                          (2 if serial_launch else 0)))
 
     def set_profiling(self, enable: bool):
         _check(load().ctis_plan_set_profiling(self._h, int(bool(enable))))

@@ -115,6 +115,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Programmatic dependent launch. launch_dependents lets the stream's next
+// kernel be scheduled once every CTA of this grid has executed it (its CTAs
+// become resident as this grid's CTAs exit); grid_dependency_wait blocks
+// until the stream's previous kernel has completed and its memory operations
+// are visible (it returns at once when the grid was launched without the
+// programmatic attribute).
+__device__ __forceinline__ void launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+// Pulls a tensor map (a __grid_constant__ kernel parameter) into the
+// descriptor cache before its first TMA.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
                                           uint64_t* bar) {
     asm volatile(
@@ -888,6 +906,22 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * G::NW + warp;
+    const bool has_work = gw < p.n_warps;   // warp-uniform
+    // the warp's start: lanes 0..5 load its 96-byte head at once, then the
+    // fields go to every lane by shuffles. Up to the dependency wait below
+    // the kernel reads only the plan's work lists (written by host copies
+    // before any launch that uses them) and its own parameters: under
+    // programmatic launch this part runs while the previous projector's grid
+    // drains. (That grid lets this one be scheduled only once all its CTAs
+    // have finished their work: scheduled earlier, this grid's CTAs would
+    // take the SM slots in the order the previous CTAs exit, not in the
+    // placement the work lists were balanced for.)
+    int4 hv = make_int4(0, 0, 0, 0);
+    if (has_work && lane < 6) hv = __ldg(reinterpret_cast<const int4*>(p.heads + gw) + lane);
+    if (threadIdx.x == 0) prefetch_tensormap(&tm_win);
+    // the inputs (copies, g, f, statistics) are the previous kernel's outputs
+    // and the outputs may still be its inputs
+    grid_dependency_wait();
     // the previous forward's statistics: slice r of the frames' reduction on
     // warp r / gridDim.x of CTA r % gridDim.x (the CTAs' first warps first)
     if (p.red_out) {
@@ -898,11 +932,7 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                                p.red_tickets, p.red_out + f * p.red_frame_stride, lane);
         }
     }
-    if (gw >= p.n_warps) return;
-    // the warp's start: lanes 0..5 load its 96-byte head at once, then the
-    // fields go to every lane by shuffles
-    int4 hv = make_int4(0, 0, 0, 0);
-    if (lane < 6) hv = __ldg(reinterpret_cast<const int4*>(p.heads + gw) + lane);
+    if (!has_work) return;
     auto from = [&](int src, int4& d) {
         d.x = __shfl_sync(0xffffffffu, hv.x, src);
         d.y = __shfl_sync(0xffffffffu, hv.y, src);
@@ -1226,6 +1256,10 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         }
     }
 
+    // this CTA's work is done: once every CTA is here (or gone) the next
+    // projector of the stream may be scheduled (it waits for this grid
+    // before touching data)
+    launch_dependents();
     // Copies still in flight exist only after a failed wait: give them a
     // bounded chance to land before the warp's shared memory is released.
     if (lane == 0) {
@@ -1282,8 +1316,21 @@ template <class G, class Kern>
 cudaError_t launch_kernel(Kern kern, const CUtensorMap& win, const GatherParams& p,
                           cudaStream_t stream) {
     const int grid = (p.n_warps + G::NW - 1) / G::NW;
-    kern<<<grid, G::THREADS, G::SMEM_BYTES, stream>>>(win, p);
-    return cudaGetLastError();
+    if (!p.overlap_launch) {
+        kern<<<grid, G::THREADS, G::SMEM_BYTES, stream>>>(win, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(G::THREADS);
+    cfg.dynamicSmemBytes = G::SMEM_BYTES;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, win, p);
 }
 
 }  // namespace

@@ -158,6 +158,9 @@ struct GatherParams {
     // issuing the copy, so every wait runs out through its bounded path
     int drop_copies;
     double* tile_stats;        // [n_tiles][kNumStats] written by kEpiRatio with_stats
+    // host side only: launch the projector with programmatic dependent launch
+    // (its prologue overlaps the tail of the stream's previous kernel)
+    int overlap_launch;
 };
 
 // Compile-time configuration of one gather kernel instantiation.

@@ -206,6 +206,7 @@ struct ctis_plan {
     float* d_rowsum = nullptr;        // SART: r = H 1 per pixel [xi][gamma], built on first use
     bool rowsum_valid = false;
     bool drop_copies = false;         // CTIS_DEBUG_DROP_COPIES (test hook)
+    bool overlap_launch = true;       // programmatic dependent launch of the projectors
     FftForm* fft = nullptr;           // the paper's FFT form, built on first use
     float* d_fft_u = nullptr;         // its EM ratio [n]
     float* d_shard_q = nullptr;       // wavelength-sharded EM: the summed H f [n]
@@ -1131,6 +1132,7 @@ GatherParams base_params(const ctis_plan* P, const ProjTables& T) {
     p.h_vox = P->d_hvox;
     p.h_vox_planes = P->w;
     p.drop_copies = P->drop_copies;
+    p.overlap_launch = P->overlap_launch;
     return p;
 }
 
@@ -1671,6 +1673,7 @@ GatherParams batch_params(const ctis_plan* P, const BatchState* B, bool forward)
     p.h_vox = P->d_hvox;
     p.h_vox_planes = P->w;
     p.drop_copies = P->drop_copies;
+    p.overlap_launch = P->overlap_launch;
     return p;
 }
 
@@ -2310,10 +2313,12 @@ int ctis_reconstruct_solver(const ctis_plan* Pc, const float* g_dev, void* f_dev
 
 int ctis_plan_set_debug(ctis_plan* P, int flags) {
     if (!P) return fail(CTIS_ERR_INVALID_ARG, "plan is NULL");
-    if (flags & ~CTIS_DEBUG_DROP_COPIES) return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
+    if (flags & ~(CTIS_DEBUG_DROP_COPIES | CTIS_DEBUG_SERIAL_LAUNCH))
+        return fail(CTIS_ERR_INVALID_ARG, "bad flags 0x%x", flags);
     CTIS_CUDA(cudaDeviceSynchronize());   // cached graphs hold the old parameters
     drop_table_users(P);
     P->drop_copies = (flags & CTIS_DEBUG_DROP_COPIES) != 0;
+    P->overlap_launch = (flags & CTIS_DEBUG_SERIAL_LAUNCH) == 0;
     return CTIS_OK;
 }
 

@@ -108,4 +108,5 @@ def test_header_constants_match_the_binding():
         assert consts[name] == getattr(_native, name), name
     assert consts["CTIS_NSTATS"] == _native.NSTATS
     assert consts["CTIS_DEBUG_DROP_COPIES"] == 1
+    assert consts["CTIS_DEBUG_SERIAL_LAUNCH"] == 2
     assert consts["CTIS_ERR_TIMEOUT"] == -5 and consts["CTIS_ERR_UNSUPPORTED"] == -6

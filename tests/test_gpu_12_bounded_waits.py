@@ -59,5 +59,6 @@ def test_the_hook_takes_only_known_flags():
     with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl)) as plan:
         from paper_2006_01573_gb300 import load
         import ctypes
-        assert load().ctis_plan_set_debug(plan._h, 2) != 0
+        assert load().ctis_plan_set_debug(plan._h, 4) != 0
+        assert load().ctis_plan_set_debug(plan._h, 2) == 0
         assert load().ctis_plan_set_debug(plan._h, 0) == 0
