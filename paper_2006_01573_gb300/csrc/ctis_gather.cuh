@@ -165,9 +165,8 @@ struct Elem<float> {
     }
     __device__ static __forceinline__ float load(const float* p) { return *p; }
     __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
-    // weight stored as a duplicated pair (w, w)
-    using WPair = float2;
-    __device__ static __forceinline__ float2 weight_pair(const WPair& w) { return w; }
+    // weight stored as one float32 word
+    using Weight = float;
 };
 template <>
 struct Elem<__nv_bfloat16> {
@@ -203,11 +202,9 @@ struct Elem<__nv_bfloat16> {
     __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
         *p = __float2bfloat16_rn(v);
     }
-    // weight stored as a duplicated pair of bfloat16 in one 32-bit word
-    using WPair = uint32_t;
-    __device__ static __forceinline__ float2 weight_pair(const WPair& w) {
-        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-    }
+    // weight stored as a bfloat16 duplicated in both halves of a 32-bit word
+    // (fma.rn.f32.bf16 takes the low half)
+    using Weight = uint32_t;
 };
 
 // ---------------------------------------------------------------------------
@@ -240,9 +237,9 @@ struct Geo {
     static constexpr int ROWS = TY + K - 1;           // TMA box height
     static_assert((BXW * ES) % 16 == 0 && BXW <= 256 && ROWS <= 256, "TMA box");
     static constexpr int WINDOW_BYTES = ROWS * BXW * ES;
-    // per-cluster weights (duplicated pairs), padded to a 16-byte multiple,
-    // copied with the window
-    static constexpr int WES = int(sizeof(typename Elem<TF>::WPair));
+    // per-cluster weights (one 32-bit word each), padded to a 16-byte
+    // multiple, copied with the window
+    static constexpr int WES = int(sizeof(typename Elem<TF>::Weight));
     static constexpr int WPAD = (K * K * WES + 15) / 16 * 16 / WES;
     static constexpr int WBYTES = WPAD * WES;
     static constexpr int WOFF = (WINDOW_BYTES + 15) / 16 * 16;   // bytes into the stage
@@ -1075,7 +1072,7 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
             }
             if (!failed) {
                 const unsigned char* stage = my_stages + cons_stage * G::STAGE_BYTES;
-                using WP = typename Elem<TF>::WPair;
+                using WP = typename Elem<TF>::Weight;
                 const WP* ws = reinterpret_cast<const WP*>(stage + G::WOFF);
                 if constexpr (MODE == kEpiGrad) {
                     const int cl = p.tasks[t].cluster;
@@ -1091,17 +1088,32 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
                         const float sum = warp_sum_f(gacc[q].x + gacc[q].y);
                         if (lane == 0) dst[q] = sum;
                     }
-                } else if constexpr (std::is_same_v<TIn, __nv_bfloat16>) {
-                    uint32_t wh[G::K * G::K];
-#pragma unroll
-                    for (int q = 0; q < G::K * G::K; ++q) wh[q] = ws[q];
-                    correlate_bf16<G>(acc, reinterpret_cast<const TIn*>(stage) + lane_off +
-                                               my_shift[cons_stage], wh);
                 } else {
-                    float2 w2[G::K * G::K];
+                    // the task's weights: one 32-bit word each, read 16 bytes
+                    // at a time (the slot is whole 16-byte words)
+                    static_assert(sizeof(WP) == 4 && G::WPAD % 4 == 0, "weight slot of 16-byte words");
+                    uint32_t wq[G::WPAD];
 #pragma unroll
-                    for (int q = 0; q < G::K * G::K; ++q) w2[q] = Elem<TF>::weight_pair(ws[q]);
-                    correlate<G, TIn>(acc, reinterpret_cast<const TIn*>(stage) + lane_off, w2);
+                    for (int i = 0; i < G::WPAD / 4; ++i) {
+                        const uint4 v = reinterpret_cast<const uint4*>(ws)[i];
+                        wq[4 * i] = v.x;
+                        wq[4 * i + 1] = v.y;
+                        wq[4 * i + 2] = v.z;
+                        wq[4 * i + 3] = v.w;
+                    }
+                    if constexpr (std::is_same_v<TIn, __nv_bfloat16>) {
+                        uint32_t wh[G::K * G::K];
+#pragma unroll
+                        for (int q = 0; q < G::K * G::K; ++q) wh[q] = wq[q];
+                        correlate_bf16<G>(acc, reinterpret_cast<const TIn*>(stage) + lane_off +
+                                                   my_shift[cons_stage], wh);
+                    } else {
+                        float2 w2[G::K * G::K];
+#pragma unroll
+                        for (int q = 0; q < G::K * G::K; ++q)   // a bfloat16 weight widened exactly
+                            w2[q].x = __uint_as_float(std::is_same_v<TF, __nv_bfloat16> ? wq[q] << 16 : wq[q]);
+                        correlate<G, TIn>(acc, reinterpret_cast<const TIn*>(stage) + lane_off, w2);
+                    }
                 }
                 // after a failed wait the stage and phase stay at the copy
                 // that did not land, where the final drain resumes

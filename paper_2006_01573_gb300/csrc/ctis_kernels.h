@@ -19,7 +19,7 @@ int gather_tile_h(bool forward, int dtype, int shape = 0);   // output tile rows
 int gather_window_rows(bool forward, int K, int dtype, int shape = 0);   // TMA box height
 int gather_warps_per_cta(bool forward);
 int gather_box_w(bool forward, int K, int dtype, int shape = 0);   // TMA box width (elements)
-int gather_weight_pad(bool forward, int K, int dtype);  // weight pairs per cluster, padded
+int gather_weight_pad(bool forward, int K, int dtype);  // weight words per cluster, padded
 int gather_input_copies(bool forward, int dtype);       // x-shifted copies of the input
 int gather_fwd_shapes();                                // forward tile shapes built
 

@@ -639,8 +639,9 @@ void compute_h(ctis_plan* P) {
 
 // Device image of one projector's weight table: per cluster its K x K values
 // (adjoint orientation: [dy][dx] as on the FPA; forward: flipped, since the
-// forward applies the cluster as a convolution), each as a duplicated pair in
-// the storage type, padded to the kernel's 16-byte weight slot.
+// forward applies the cluster as a convolution), one 32-bit word each (float32,
+// or a bfloat16 duplicated in both halves), padded to the kernel's 16-byte
+// weight slot.
 std::vector<unsigned char> weight_table(const ctis_plan* P, bool forward) {
     const int K = P->K, KK = K * K;
     const int64_t ncl = static_cast<int64_t>(P->clusters.size());
@@ -662,12 +663,9 @@ std::vector<unsigned char> weight_table(const ctis_plan* P, bool forward) {
         out.resize(b.size() * sizeof(uint32_t));
         std::memcpy(out.data(), b.data(), out.size());
     } else {
-        std::vector<float> f(static_cast<size_t>(ncl) * pad * 2, 0.f);
+        std::vector<float> f(static_cast<size_t>(ncl) * pad, 0.f);
         for (int64_t c = 0; c < ncl; ++c)
-            for (int e = 0; e < KK; ++e) {
-                f[(c * pad + e) * 2] = wts[c * KK + e];
-                f[(c * pad + e) * 2 + 1] = wts[c * KK + e];
-            }
+            for (int e = 0; e < KK; ++e) f[c * pad + e] = wts[c * KK + e];
         out.resize(f.size() * sizeof(float));
         std::memcpy(out.data(), f.data(), out.size());
     }

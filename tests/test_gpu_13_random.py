@@ -1,8 +1,9 @@
 """Randomised parity: seeded random geometries (field stops from 1 pixel to
 several tiles with ragged tails, 1-6 wavelengths), random sparse PSFs with
 duplicate entries and random spot blobs (so K = 1, 3 and 5 all occur), under
-the reject, clip and wrap boundaries: projectors and three EM updates against the
-FP64 oracle, with the parity suite's bounds."""
+the reject, clip and wrap boundaries, over both forward tile shapes:
+projectors and three EM updates against the FP64 oracle, with the parity
+suite's bounds."""
 import numpy as np
 import pytest
 import torch
@@ -69,7 +70,9 @@ def test_random_geometry_projectors_and_em(seed):
     f = synth.random_positive((geom.w, geom.alpha, geom.a), 2000 + seed)
     r = synth.random_positive((geom.xi, geom.gamma), 3000 + seed)
     g = (synth.random_positive(geom.n, 4000 + seed) * 50).astype(np.float32)
-    with Plan(geom.a, geom.alpha, geom.w, geom.gamma, geom.xi, psf, boundary=boundary) as plan:
+    tile = ("32x32", "32x16")[seed % 2]   # both forward tile shapes
+    with Plan(geom.a, geom.alpha, geom.w, geom.gamma, geom.xi, psf, boundary=boundary,
+              forward_tile=tile) as plan:
         hf = plan.forward(torch.from_numpy(f).cuda()).cpu().numpy().ravel()
         ht = plan.adjoint(torch.from_numpy(r).cuda()).cpu().numpy().ravel()
         out, _ = plan.reconstruct(torch.from_numpy(g.reshape(geom.xi, geom.gamma)).cuda(), 3,
