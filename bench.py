@@ -525,7 +525,7 @@ def run_ours(args, wl, k):
     if world == 1 and not args.no_forms:
         line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
         line["forms"]["batched"] = batched_form(args, flush, stream, oracle_job=oracle_job)
-        line["forms"]["large"] = large_form(args, flush, stream)
+        line["forms"]["large"] = large_form(args, flush, stream, fma)
         line["forms"]["autograd"] = autograd_form(args, flush, stream)
     plan.close()
     if world == 1 and not args.no_cpu_baseline:
@@ -763,11 +763,12 @@ def batched_form(args, flush, stream, nframes=256, k=100, oracle_job=None):
     return out
 
 
-def large_form(args, flush, stream):
+def large_form(args, flush, stream, fma=None):
     """The large workload (256x256x128 cube, 2048x2048 FPA, 5x5 orders of
     5x5 spots: 625 nonzeros per image, K = 5 clusters), k = 50 EM iterations
     with statistics per step: iterations/s, voxel-updates/s and the FP32
-    FLOP rate of the two projections."""
+    FLOP rate of the two projections; then each projector's EM launch alone
+    (CUDA events around back-to-back launches) against the FP32 peak."""
     import torch
     import synth
     from paper_2006_01573_gb300 import Plan
@@ -777,7 +778,7 @@ def large_form(args, flush, stream):
     plan = Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf)
     hf = plan.forward(torch.from_numpy(synth.make_scene(wl)).cuda())
     g = torch.poisson(hf * (wl.peak / hf.max()), generator=torch.Generator(device="cuda").manual_seed(wl.seed))
-    plan.autotune(g)
+    tuned = plan.autotune(g)
     f = torch.empty((wl.w, wl.alpha, wl.a), device="cuda")
     stats = torch.empty((k + 1, 4), device="cuda", dtype=torch.float64)
     run = lambda: plan.reconstruct(g, k, f=f, init="ones", stats=stats)
@@ -788,12 +789,27 @@ def large_form(args, flush, stream):
     total = _timed_steps(run, steps, flush, stream)
     plan.check()
     info = plan.info()
+    reps = 20
+    fwd_ms, adj_ms = plan.time_launches(g, reps)
+    tile = plan.forward_tile()
     plan.close()
     value = steps * k / (total / 1e3)
     flops = 2 * 2 * int(info["nnz"]) * wl.a * wl.alpha   # two projections, 2 FLOP per FMA
+    one = flops / 2                                       # one projection
+    kernels = {}
+    for name, ms in (("forward", fwd_ms), ("adjoint", adj_ms)):
+        tf = one / (ms * 1e-3) / 1e12
+        kernels[name] = {"avg_us_back_to_back": ms * 1e3, "tflops": tf,
+                         "frac_of_nominal_peak": tf / FP32_PEAK_TFLOPS}
+        if fma:
+            kernels[name]["frac_of_measured_fma_peak"] = tf / fma["best_tflops"]
     return {"workload": wl.name, "k": k, "steps": steps, "value": value, "unit": "it/s",
             "voxel_updates_per_s": value * wl.m, "tflops_two_projections": value * flops / 1e12,
-            "cluster_k": int(info["cluster_k"]),
+            "cluster_k": int(info["cluster_k"]), "forward_tile": tile,
+            "schedule_spec": tile + ":" + ",".join(f"{kd}:{v}:{sk}" for kd, v, sk in tuned),
+            "kernels": kernels,
+            "kernel_timing": f"CUDA events around {reps} back-to-back EM launches of each kernel "
+                             "(ctis_plan_time_launches), after the timed steps",
             "data": "seeded scene, Poisson counts of the GPU image drawn on the GPU"}
 
 
