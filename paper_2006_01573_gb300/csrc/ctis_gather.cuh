@@ -62,12 +62,6 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -106,12 +100,34 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint64_t* bar) {
+// The copy-side operations (the barrier's expected bytes, a tensor-TMA box,
+// a bulk copy), executed only by the lanes whose `on` is set (the warp's
+// lane 0) as predicated instructions: the warp runs one instruction stream
+// instead of branching around a one-lane block.
+__device__ __forceinline__ void mbar_arrive_expect_tx_if(bool on, uint64_t* bar, uint32_t bytes) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes), "r"(int(on))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_if(bool on, void* dst, const CUtensorMap* map, int x,
+                                               int y, int z, uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+        "@p cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n\t}" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar)),
+        "r"(int(on))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load_if(bool on, void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        "\n\t}" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "r"(int(on))
         : "memory");
 }
 
@@ -131,14 +147,6 @@ __device__ __forceinline__ void grid_dependency_wait() {
 // descriptor cache before its first TMA.
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -884,9 +892,9 @@ __device__ __forceinline__ void reduce_frame_slice(const double* tile_stats, int
 // and each warp applies the epilogue to its share of the tile's rows. Each
 // warp's tasks are stored contiguously, so its TMA issue cursor is a plain
 // counter running NS tasks ahead of the compute loop, across item boundaries.
-// Only lane 0 reads task descriptors (it alone issues the copies); it loads
-// the next one right after each issue, so the load's latency overlaps a task
-// of compute.
+// Lane 0 alone issues the copies (predicated instructions, no branch); the
+// warp loads the next task descriptor right after each issue, so the load's
+// latency overlaps a task of compute.
 template <class G, typename TIn, typename TF, int MODE>
 __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const GatherParams& p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -965,40 +973,40 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     uint32_t cons_phase = 0;
     int outstanding = 0;                                    // copies issued, not yet waited for
     bool failed = false;                                    // warp-uniform
-    // lane 0: descriptor of issue_task; the first three come with the head,
-    // the later ones are loaded one issue ahead
-    TaskDesc nxt{};
-    if (lane == 0) {
+    // descriptor of issue_task, held by every lane (same-address loads); the
+    // first three come with the head, the later ones are loaded one issue
+    // ahead
+    TaskDesc nxt;
+    {
         const int4 f0 = my_head[0];
         nxt = TaskDesc{f0.x, f0.y, f0.z, f0.w};
     }
     const int head_end = issue_task + 3;
+    const bool leader = lane == 0;   // issues the copies
 
     auto issue_next = [&]() {
         if (issue_task >= task_end || failed) return;
-        if (lane == 0) {
-            unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
-            uint64_t* bar = &my_bars[issue_stage];
-            // the lanes' shift inside the box (bfloat16: wx is a multiple of
-            // 4, the box starts at a multiple of 8), published before the
-            // arrival that releases the stage to the warp
-            my_shift[issue_stage] = nxt.wx & (G::EPC - 1);
-            mbar_arrive_expect_tx(bar, G::TX_BYTES);
-            if (!p.drop_copies) {
-                tma_load_3d(stage, &tm_win, nxt.wx & ~(G::EPC - 1), nxt.wy, nxt.plane, bar);
-                bulk_load(stage + G::WOFF,
-                          static_cast<const unsigned char*>(p.weights) +
-                              (long long)nxt.cluster * G::WBYTES,
-                          G::WBYTES, bar);
-            }
-            const int t1 = issue_task + 1;
-            if (t1 < task_end) {
-                if (t1 < head_end) {
-                    const int4 f = my_head[t1 - (head_end - 3)];
-                    nxt = TaskDesc{f.x, f.y, f.z, f.w};
-                } else {
-                    nxt = p.tasks[t1];
-                }
+        unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
+        uint64_t* bar = &my_bars[issue_stage];
+        // the lanes' shift inside the box (bfloat16: wx is a multiple of 4,
+        // the box starts at a multiple of 8), published before the arrival
+        // that releases the stage to the warp
+        if (leader) my_shift[issue_stage] = nxt.wx & (G::EPC - 1);
+        mbar_arrive_expect_tx_if(leader, bar, G::TX_BYTES);
+        if (!p.drop_copies) {
+            tma_load_3d_if(leader, stage, &tm_win, nxt.wx & ~(G::EPC - 1), nxt.wy, nxt.plane, bar);
+            bulk_load_if(leader, stage + G::WOFF,
+                         static_cast<const unsigned char*>(p.weights) +
+                             (long long)nxt.cluster * G::WBYTES,
+                         G::WBYTES, bar);
+        }
+        const int t1 = issue_task + 1;
+        if (t1 < task_end) {
+            if (t1 < head_end) {
+                const int4 f = my_head[t1 - (head_end - 3)];
+                nxt = TaskDesc{f.x, f.y, f.z, f.w};
+            } else {
+                nxt = p.tasks[t1];
             }
         }
         ++issue_task;
