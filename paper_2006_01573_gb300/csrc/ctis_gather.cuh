@@ -988,10 +988,12 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         if (issue_task >= task_end || failed) return;
         unsigned char* stage = my_stages + issue_stage * G::STAGE_BYTES;
         uint64_t* bar = &my_bars[issue_stage];
-        // the lanes' shift inside the box (bfloat16: wx is a multiple of 4,
-        // the box starts at a multiple of 8), published before the arrival
-        // that releases the stage to the warp
-        if (leader) my_shift[issue_stage] = nxt.wx & (G::EPC - 1);
+        // bfloat16 windows: the lanes' shift inside the box (wx is a multiple
+        // of 4, the box starts at a multiple of 8), published before the
+        // arrival that releases the stage to the warp (float32 windows start
+        // aligned: no shift)
+        if constexpr (G::EPC > 4)
+            if (leader) my_shift[issue_stage] = nxt.wx & (G::EPC - 1);
         mbar_arrive_expect_tx_if(leader, bar, G::TX_BYTES);
         if (!p.drop_copies) {
             tma_load_3d_if(leader, stage, &tm_win, nxt.wx & ~(G::EPC - 1), nxt.wy, nxt.plane, bar);
