@@ -170,3 +170,33 @@ def test_other_forward_tiles_in_em_and_statistics(dtype, tile):
             assert rel_l2(got, f_stored) <= 4 * 2.0 ** -8, wl.name
             base = runs["32x32"][1]
             assert np.all(np.abs(st - base) <= 1e-3 * np.abs(base)), wl.name
+
+
+def test_autotune_on_a_small_field_stop_keeps_parity():
+    """A 20x20 field stop with many wavelengths, where 32 x 16 forward tiles
+    compute far less of the footprints' empty rows than 32 x 32 ones (the
+    autotuner keeps them on the GPU of this project): after autotuning,
+    whichever shape it kept, the EM iterates and every statistic meet the
+    parity bounds, and the plan's forward tile count is the one its shape's
+    work lists have (switching shape regrows the tile tickets and
+    statistics)."""
+    from paper_2006_01573_gb300._native import tables_inspect
+    wl = synth.Workload("fs20", 20, 20, 24, 192, 192, 5, 30.0, 1.0, 3, 0.8, "segmentation",
+                        2000.0, 6)
+    geom, psf, H, _, g = problem(wl)
+    ref, hist = O.mlem(H, g, wl.k)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf) as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        plan.autotune(gt)
+        tile = plan.forward_tile()
+        assert tile in ("32x32", "32x16")
+        t = tables_inspect(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, True, 608, forward_tile=tile)
+        assert int(plan.info()["fwd_tiles"]) == t["tiles"]
+        got, st = plan.reconstruct(gt, k=wl.k, init="ones", stats=True)
+        plan.check()
+        got, st = got.cpu().numpy().ravel(), st.cpu().numpy()
+    assert floored_rel(got, ref) <= wl.k * 1e-5
+    assert rel_l2(got, ref) <= 1e-5 * np.sqrt(wl.k)
+    for it in range(wl.k + 1):
+        for q, key in enumerate(STAT_KEYS):
+            assert abs(st[it, q] - hist[it][key]) <= 1e-5 * abs(hist[it][key]), (it, key)
