@@ -627,9 +627,32 @@ def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=33):
     avg_rel = float(((a[on] - b[on]).abs() / b[on]).mean())
     plan.close()
     value = steps * k / (total / 1e3)
+    # HBM bytes of one iteration if every pass reads and writes its operands
+    # once: the w-batched R2C and C2R (4 n w real, 8 beta w complex each way),
+    # the spectral multiply-accumulate (X and the PSF spectra D in, S out) and
+    # its adjoint expansion (S and D in, X out); the n- and m-sized passes
+    # (embedding, ratio, single transforms, crop, update) add < 1%
+    n, w = wl.gamma * wl.xi, wl.w
+    beta = n // 2 + 1
+    nbytes = 2 * (4 * n * w + 8 * beta * w) + 2 * (16 * beta * w + 8 * beta)
+    hbm = measured_hbm_gbs()
     return {"value": value, "unit": "it/s", "k": k, "steps": steps, "vs_gather": value / f32_value,
             "rel_l2_vs_gather_after_k": err, "avg_rel_pixel_err_vs_gather_after_k": avg_rel,
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_iteration": nbytes,
+                         "achieved_gbs": nbytes * value / 1e9, "peak_gbs": hbm,
+                         "frac": nbytes * value / 1e9 / hbm,
+                         "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
             "form": "cuFFT R2C/C2R of length n per wavelength + spectral MAC (float32)"}
+
+
+def measured_hbm_gbs():
+    """The machine's measured HBM copy bandwidth in GB/s (MEASURED_PEAKS.json),
+    else the earlier GB300 measurement of 6 800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 def _timed_steps(fn, steps, flush, stream):
