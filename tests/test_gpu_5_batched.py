@@ -27,8 +27,9 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def _plan(wl, dtype="f32"):
-    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), dtype=dtype)
+def _plan(wl, dtype="f32", forward_tile="32x32"):
+    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, synth.make_psf(wl), dtype=dtype,
+                forward_tile=forward_tile)
 
 
 def _frame_g(plan, wl, seed):
@@ -62,6 +63,31 @@ def test_batched_frames_equal_single_frame_reconstructions(init, dtype):
         for n, i in enumerate(plan_idx):
             f1 = f0[n].clone() if init is None else None
             ref, ref_st = plans[i].reconstruct(gs[n], k=k, f=f1, init=init, stats=True)
+            plans[i].check()
+            assert torch.equal(fs[n], ref), f"frame {n}"
+            assert torch.equal(st[n], ref_st), f"frame {n} statistics"
+    finally:
+        for p in plans:
+            p.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_plans_of_different_forward_tiles(dtype):
+    """Plans of one batch may use different forward tile shapes (each plan's
+    frames run on its own launches): every frame equals its single-frame
+    reconstruction bit for bit, statistics included."""
+    wls = [synth.TINY, RAGGED]
+    plans = [_plan(wls[0], dtype, "32x16"), _plan(wls[1], dtype, "32x32")]
+    try:
+        assert [p.forward_tile() for p in plans] == ["32x16", "32x32"]
+        plan_idx = [1, 0, 0, 1, 0]
+        gs = [_frame_g(plans[i], wls[i], 300 + n) for n, i in enumerate(plan_idx)]
+        k = 5
+        fs, st = reconstruct_batched(plans, plan_idx, gs, k, init="ones", stats=True)
+        for p in plans:
+            p.check()
+        for n, i in enumerate(plan_idx):
+            ref, ref_st = plans[i].reconstruct(gs[n], k=k, init="ones", stats=True)
             plans[i].check()
             assert torch.equal(fs[n], ref), f"frame {n}"
             assert torch.equal(st[n], ref_st), f"frame {n} statistics"
