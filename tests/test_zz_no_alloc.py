@@ -65,17 +65,21 @@ def _case(wl, dtype, boundary, seed):
     return psf, O.BlockH(geom, taps), f
 
 
-CASES = [(synth.TINY, "f32", "reject"), (RAGGED, "f32", "reject"), (synth.MODEL_A, "f32", "reject"),
-         (synth.REALISTIC, "f32", "reject"), (RAGGED, "bf16", "reject"), (RAGGED, "f32", "clip"),
-         (synth.TINY, "f32", "wrap"), (RAGGED, "bf16", "clip")]
+CASES = [(synth.TINY, "f32", "reject", "32x32"), (RAGGED, "f32", "reject", "32x32"),
+         (synth.MODEL_A, "f32", "reject", "32x32"), (synth.REALISTIC, "f32", "reject", "32x32"),
+         (RAGGED, "bf16", "reject", "32x32"), (RAGGED, "f32", "clip", "32x32"),
+         (synth.TINY, "f32", "wrap", "32x32"), (RAGGED, "bf16", "clip", "32x32"),
+         (RAGGED, "f32", "reject", "32x16"), (synth.MODEL_A, "bf16", "clip", "32x16")]
 
 
-@pytest.mark.parametrize("wl,dtype,boundary", CASES,
-                         ids=[f"{w.name}-{d}-{b}" for w, d, b in CASES])
-def test_static_scratch_forward_matches_oracle_and_forward_on_consecutive_calls(wl, dtype, boundary):
+@pytest.mark.parametrize("wl,dtype,boundary,tile", CASES,
+                         ids=[f"{w.name}-{d}-{b}-{t}" for w, d, b, t in CASES])
+def test_static_scratch_forward_matches_oracle_and_forward_on_consecutive_calls(wl, dtype, boundary,
+                                                                               tile):
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     psf = _edge_psf(wl, boundary) if boundary != "reject" else synth.make_psf(wl)
-    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype, boundary=boundary) as plan:
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype, boundary=boundary,
+              forward_tile=tile) as plan:
         for seed in (101, 102):   # two calls in a row, different inputs
             _, H, f = _case(wl, dtype, boundary, seed)
             ft = torch.from_numpy(f).to(tdt).cuda()
