@@ -56,7 +56,7 @@ class _PairSum:
         return reduce
 
 
-def _sharded(wl, psf, g, k, world, init="ones", f0=None):
+def _sharded(wl, psf, g, k, world, init="ones", f0=None, forward_tile="32x32"):
     bounds = [shard_wavelengths(wl.w, world, r) for r in range(world)]
     red = _PairSum(world)
     out, errs = [None] * world, []
@@ -66,7 +66,8 @@ def _sharded(wl, psf, g, k, world, init="ones", f0=None):
             s0, s1 = bounds[rank]
             st = torch.cuda.Stream()
             with torch.cuda.stream(st):
-                plan = Plan(wl.a, wl.alpha, s1 - s0, wl.gamma, wl.xi, slice_psf(psf, s0, s1))
+                plan = Plan(wl.a, wl.alpha, s1 - s0, wl.gamma, wl.xi, slice_psf(psf, s0, s1),
+                            forward_tile=forward_tile)
                 gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
                 f = None
                 if f0 is not None:
@@ -90,12 +91,13 @@ def _sharded(wl, psf, g, k, world, init="ones", f0=None):
     return np.concatenate([o[0] for o in out]), [o[1] for o in out]
 
 
-@pytest.mark.parametrize("wl,k", [(synth.TINY, 10), (RAGGED, 6), (synth.MODEL_A, 4)],
-                         ids=["tiny", "ragged", "model_a"])
-def test_two_slices_reconstruct_like_the_whole_plan(wl, k):
+@pytest.mark.parametrize("wl,k,tile", [(synth.TINY, 10, "32x32"), (RAGGED, 6, "32x32"),
+                                       (synth.MODEL_A, 4, "32x32"), (RAGGED, 6, "32x16")],
+                         ids=["tiny", "ragged", "model_a", "ragged-32x16"])
+def test_two_slices_reconstruct_like_the_whole_plan(wl, k, tile):
     geom, psf, H, _, g = problem(wl)
     f_ref, hist = O.mlem(H, g, k)
-    f, stats = _sharded(wl, psf, g, k, 2)
+    f, stats = _sharded(wl, psf, g, k, 2, forward_tile=tile)
     floor = 1e-6 * np.abs(f_ref).max()
     assert np.max(np.abs(f - f_ref) / np.maximum(np.abs(f_ref), floor)) <= k * 1e-5
     assert rel_l2(f, f_ref) <= 1e-5 * math.sqrt(k)
