@@ -688,6 +688,9 @@ int write_values(ctis_plan* P, bool allocate) {
         if (rc) return rc;
     }
     CTIS_CUDA(cudaMemcpy(P->d_h, P->h.data(), sizeof(float) * P->w, cudaMemcpyHostToDevice));
+    // a copy from pageable host memory may still be in flight when cudaMemcpy
+    // returns; kernels on other streams must not read the tables before it lands
+    CTIS_CUDA(cudaDeviceSynchronize());
     return CTIS_OK;
 }
 
@@ -1073,6 +1076,9 @@ int reupload_tables(ctis_plan* P, ProjTables& T) {
         if (r) return r;
         P->scratch_capacity = need;
     }
+    // the uploads above come from pageable host memory and may still be in
+    // flight; the next launch may be on any stream
+    CTIS_CUDA(cudaDeviceSynchronize());
     return CTIS_OK;
 }
 
@@ -1649,6 +1655,9 @@ int ensure_batch(ctis_plan* P, int F, int k) {
     std::vector<float> hx(static_cast<size_t>(P->w) * F);
     for (int f = 0; f < F; ++f) std::copy(P->h.begin(), P->h.end(), hx.begin() + f * P->w);
     CTIS_CUDA(cudaMemcpy(B->d_h, hx.data(), sizeof(float) * hx.size(), cudaMemcpyHostToDevice));
+    // the tables and h come from pageable host memory (copies that may still
+    // be in flight when cudaMemcpy returns); the batch runs on any stream
+    CTIS_CUDA(cudaDeviceSynchronize());
     return CTIS_OK;
 }
 
