@@ -43,8 +43,8 @@ def _cases():
 CASES = _cases()
 
 
-def _plan(wl, psf, dtype="f32"):
-    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype)
+def _plan(wl, psf, dtype="f32", forward_tile="32x32"):
+    return Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, dtype=dtype, forward_tile=forward_tile)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -183,14 +183,14 @@ def _fd_grad(geom, taps, g, f0, k, idx, rel_eps=1e-4):
     return out
 
 
-@pytest.mark.parametrize("k", [0, 1, 3])
-def test_unrolled_nll_gradient_against_oracle_differences(k):
+@pytest.mark.parametrize("k,tile", [(0, "32x32"), (1, "32x32"), (3, "32x32"), (3, "32x16")])
+def test_unrolled_nll_gradient_against_oracle_differences(k, tile):
     wl = synth.TINY
     geom, psf, _, _, g = problem(wl)
     taps = O.merge_psf(geom, psf)
     taps = O.with_values(taps, taps.v.astype(np.float32).astype(np.float64))
     f0 = np.ones(geom.m)
-    with _plan(wl, psf) as plan:
+    with _plan(wl, psf, forward_tile=tile) as plan:
         gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
         nll, dval, df0 = plan.unrolled_nll_grad(gt, k, f0=torch.ones((wl.w, wl.alpha, wl.a),
                                                                      device="cuda"), want_df0=True)
