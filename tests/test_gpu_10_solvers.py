@@ -60,6 +60,21 @@ def test_solver_iterations_and_statistics(wl, solver, lam):
         assert got.min() >= 0.0
 
 
+@pytest.mark.parametrize("wl", [RAGGED, synth.MODEL_A], ids=lambda w: w.name)
+@pytest.mark.parametrize("solver", ["sart", "smart"])
+def test_solvers_on_32x16_forward_tiles(wl, solver):
+    """The solvers' ratio rules (SART's row-sum weighted residual, SMART's
+    log ratio) in the epilogue of the 32 x 16 forward tiles."""
+    geom, psf, H, _, g = problem(wl)
+    ref, hist = O.solve(H, g, K, solver, 1.0)
+    with Plan(wl.a, wl.alpha, wl.w, wl.gamma, wl.xi, psf, forward_tile="32x16") as plan:
+        gt = torch.from_numpy(g.reshape(wl.xi, wl.gamma)).cuda()
+        out, st = plan.reconstruct(gt, K, init="ones", stats=True, solver=solver, relax=1.0)
+        plan.check()
+        got, st = out.cpu().numpy().ravel(), st.cpu().numpy()
+    _check(got, st, ref, hist, K, solver)
+
+
 @pytest.mark.parametrize("boundary", ["clip", "wrap"])
 @pytest.mark.parametrize("solver", ["sart", "smart"])
 def test_solvers_under_the_other_boundaries(boundary, solver):
