@@ -545,6 +545,56 @@ __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int 
     constexpr int NCMAX = 16 / int(sizeof(T));
     constexpr int DMAX = (NCMAX - 1 + C - 1) / C;   // lanes to the left a copy reaches
     const int col0 = tx * C;
+    if constexpr (sizeof(T) == 2 && C == 4) {
+        // A full bfloat16 tile with the 4 copies of the plan (uniform over
+        // the warp): each value is rounded once, the lanes pass packed pairs
+        // to the right, and each copy's 4 elements are two 32-bit words
+        // assembled with byte permutes (the same bits as rounding per copy).
+        if (tile_cols == LX * C && ncopies <= 4) {
+            const uint32_t p0 = pack_bf16x2(v[0], v[1]), p1 = pack_bf16x2(v[2], v[3]);
+            const uint32_t l0 = __shfl_up_sync(0xffffffffu, p0, 1);   // left lane's (e0, e1)
+            const uint32_t l1 = __shfl_up_sync(0xffffffffu, p1, 1);   // left lane's (e2, e3)
+            if (!active) return;
+            // the high half of x and the low half of y: (x.hi, y.lo)
+            auto mid = [](uint32_t x, uint32_t y) { return __byte_perm(x, y, 0x5432); };
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= ncopies) break;
+                uint16_t* dst = reinterpret_cast<uint16_t*>(row + q * copy_stride);
+                // copy q, columns col0 .. col0 + 3: source columns col0 - q ..
+                const uint32_t w0 = q == 0 ? p0 : q == 1 ? mid(l1, p0) : q == 2 ? l1 : mid(l0, l1);
+                const uint32_t w1 = q == 0 ? p1 : q == 1 ? mid(p0, p1) : q == 2 ? p0 : mid(l1, p0);
+                if (q == 0 || tx >= 1) {
+                    DBG_CHECK_RANGE(reinterpret_cast<T*>(dst) + col0, C);
+                    *reinterpret_cast<uint2*>(dst + col0) = make_uint2(w0, w1);
+                } else if (q == 1) {   // left edge: columns 1..3 (e0, e1, e2)
+                    DBG_CHECK_RANGE(reinterpret_cast<T*>(dst) + 1, 3);
+                    dst[1] = uint16_t(w0 >> 16);
+                    *reinterpret_cast<uint32_t*>(dst + 2) = w1;
+                } else if (q == 2) {   // columns 2, 3 (e0, e1)
+                    DBG_CHECK_RANGE(reinterpret_cast<T*>(dst) + 2, 2);
+                    *reinterpret_cast<uint32_t*>(dst + 2) = w1;
+                } else {               // column 3 (e0)
+                    DBG_CHECK_RANGE(reinterpret_cast<T*>(dst) + 3, 1);
+                    dst[3] = uint16_t(w1 >> 16);
+                }
+                // right edge: the last q source columns land past the tile
+                if (q >= 1 && tx == LX - 1) {
+                    uint16_t* sp = dst + LX * C;
+                    DBG_CHECK_RANGE(reinterpret_cast<T*>(sp), q);
+                    if (q == 1) {          // e3
+                        sp[0] = uint16_t(p1 >> 16);
+                    } else if (q == 2) {   // e2, e3
+                        *reinterpret_cast<uint32_t*>(sp) = p1;
+                    } else {               // e1, e2, e3
+                        *reinterpret_cast<uint32_t*>(sp) = mid(p0, p1);
+                        sp[2] = uint16_t(p1 >> 16);
+                    }
+                }
+            }
+            return;
+        }
+    }
     // The values of the DMAX lanes to the left, fetched once for all copies.
     // Every lane runs the shuffles (DMAX is uniform); lanes of rows outside
     // the plane (`active` false) store nothing.
