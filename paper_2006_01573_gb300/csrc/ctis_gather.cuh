@@ -696,16 +696,14 @@ __device__ __forceinline__ void store_copies(T* row, long long copy_stride, int 
 template <class G, typename TF, int MODE, int ER>
 __device__ __forceinline__ void epilogue(const GatherParams& p, const WorkItem& it, int tx,
                                          int ty, int o0, const float (&v)[ER][G::C],
-                                         const float (&ein)[ER][G::C], float (&stat)[kNumStats]) {
+                                         const float (&ein)[ER][G::C], float (&stat)[kNumStats],
+                                         float hs) {
     constexpr int C = G::C;
     const int tile_cols = min(G::TX, p.out_w - it.x0);
     const int col0 = tx * C;
     const int n_valid = tile_cols - col0;
     float rh = 0.f;   // kEpiUpdate: 1 / h_s (0 where h_s == 0: f = 0 there)
-    if constexpr (MODE == kEpiUpdate) {
-        const float hs = p.h[it.plane];
-        rh = hs != 0.f ? 1.0f / hs : 0.f;
-    }
+    if constexpr (MODE == kEpiUpdate) rh = hs != 0.f ? 1.0f / hs : 0.f;
 #pragma unroll
     for (int o = 0; o < ER; ++o) {
         const int y = it.y0 + ty * G::R + o0 + o;
@@ -1075,6 +1073,9 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
     for (int ii = ib; ii < ie; ++ii) {
         const WorkItem it = next_it;
         if (ii + 1 < ie) next_it = p.items[ii + 1];   // prefetch; used next item
+        // kEpiUpdate: h_s of the item's plane, loaded now for its item end
+        float hs_item = 0.f;
+        if constexpr (MODE == kEpiUpdate) hs_item = __ldg(p.h + it.plane);
         // pull the epilogue's inputs toward L1 while the item's tasks run
         if constexpr (MODE == kEpiRatio || MODE == kEpiUpdate) {
             if (MODE == kEpiRatio || p.mode == kEpiUpdate) {
@@ -1312,7 +1313,7 @@ __device__ __forceinline__ void gather_body(const CUtensorMap& tm_win, const Gat
         }
         if (finish) {
             float stat[kNumStats] = {0.f, 0.f, 0.f, 0.f};
-            epilogue<G, TF, MODE, ER>(p, it, tx, ty, warp * ER, ve, ein, stat);
+            epilogue<G, TF, MODE, ER>(p, it, tx, ty, warp * ER, ve, ein, stat, hs_item);
             if constexpr (MODE == kEpiRatio) {
                 if (p.with_stats) {   // uniform over the launch
                     store_tile_stats(stat, warp, lane, tstat);
