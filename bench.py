@@ -523,6 +523,7 @@ def run_ours(args, wl, k):
     line["forms"] = {"bf16": bf16_form(args, wl, k, psf, g, f, flush, stream, value),
                      "solvers": solver_forms(args, wl, k, plan, g, flush, stream, value)}
     if world == 1 and not args.no_forms:
+        line["forms"]["sharded"] = sharded_form(args, wl, k, plan, g, flush, stream, value)
         line["forms"]["fft"] = fft_form(args, wl, psf, g, f, flush, stream, value)
         line["forms"]["batched"] = batched_form(args, flush, stream, oracle_job=oracle_job)
         line["forms"]["large"] = large_form(args, flush, stream, fma)
@@ -600,6 +601,27 @@ def solver_forms(args, wl, k, plan, g, flush, stream, em_value):
         out[solver] = {"value": value, "unit": "it/s", "steps": steps, "vs_em": value / em_value,
                        "relax": 1.0}
     return out
+
+
+def sharded_form(args, wl, k, plan, g, flush, stream, em_value):
+    """The wavelength-sharded EM path (ctis_reconstruct_sharded) with the
+    whole datacube as its one slice and no reduction, on the same plan and g:
+    its iterations/s against the graph-captured EM. One GPU: this measures
+    the path's own cost (its host loop of launches, the partial image and the
+    separate ratio kernel in place of the fused one), not a scaling."""
+    import torch
+    f = torch.empty((wl.w, wl.alpha, wl.a), device=g.device)
+    run = lambda: plan.reconstruct_sharded(g, k, f=f, init="ones", stats=True)
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    total = _timed_steps(run, steps, flush, stream)
+    plan.check()
+    value = steps * k / (total / 1e3)
+    return {"value": value, "unit": "it/s", "steps": steps, "slices": 1, "vs_em_graph": value / em_value,
+            "exchange_bytes_per_iteration_per_rank": 4 * wl.gamma * wl.xi,
+            "note": "one slice, no reduction; multi-GPU scaling unmeasured (one GPU)"}
 
 
 def fft_form(args, wl, psf, g, f32_result, flush, stream, f32_value, k=33):

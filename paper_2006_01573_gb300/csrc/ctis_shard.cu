@@ -66,13 +66,25 @@ __global__ void __launch_bounds__(kRatioThreads)
     }
 }
 
-// out[k] = sum over the blocks, in block order, of part[block][k].
-__global__ void stats_finish_kernel(const double* part, int blocks, double* out) {
-    if (threadIdx.x < kNumStats) {
-        double t = 0.0;
-        for (int b = 0; b < blocks; ++b) t += part[(long long)b * kNumStats + threadIdx.x];
-        out[threadIdx.x] = t;
+constexpr int kFinishThreads = 256;
+constexpr int kFinishGroups = kFinishThreads / kNumStats;   // 64 groups per statistic
+
+// out[k] = sum over the blocks of part[block][k] in a fixed order: group j of
+// statistic k adds blocks j, j + 64, j + 128, ... in turn, then the 64 group
+// sums are added pairwise in a fixed tree (same result on every run).
+__global__ void __launch_bounds__(kFinishThreads)
+    stats_finish_kernel(const double* part, int blocks, double* out) {
+    __shared__ double gs[kFinishGroups][kNumStats];
+    const int k = threadIdx.x % kNumStats, j = threadIdx.x / kNumStats;
+    double t = 0.0;
+    for (int b = j; b < blocks; b += kFinishGroups) t += part[(long long)b * kNumStats + k];
+    gs[j][k] = t;
+    __syncthreads();
+    for (int half = kFinishGroups / 2; half > 0; half >>= 1) {
+        if (j < half) gs[j][k] += gs[j + half][k];
+        __syncthreads();
     }
+    if (j == 0) out[k] = gs[0][k];
 }
 
 }  // namespace
@@ -86,7 +98,7 @@ cudaError_t launch_shard_ratio(float* copies, long long copy_stride, int ncopies
         copies, copy_stride, ncopies, pitch, q, g, width, height, stats_out ? part : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !stats_out) return e;
-    stats_finish_kernel<<<1, 32, 0, stream>>>(part, kRatioBlocks, stats_out);
+    stats_finish_kernel<<<1, kFinishThreads, 0, stream>>>(part, kRatioBlocks, stats_out);
     return cudaGetLastError();
 }
 
